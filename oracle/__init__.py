@@ -1,0 +1,1 @@
+"""Sequential CPU oracle (test infrastructure only; see oracle/oracle.py)."""

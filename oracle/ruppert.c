@@ -1,0 +1,394 @@
+/*
+ * Sequential Ruppert refinement (the oracle for Algorithm 1 of Sec. 4).
+ * TEST INFRASTRUCTURE ONLY.
+ *
+ * Loop (Sec. 4.2 rules, applied one point at a time):
+ *   1. while a subsegment is encroached -- a vertex strictly inside its
+ *      diametral circle -- split it (midpoint, or a concentric-shell point
+ *      next to a small input angle);
+ *   2. otherwise take the worst bad triangle and compute its circumcentre c:
+ *      - if the walk from the triangle to c crosses a subsegment, split that
+ *        subsegment instead (Sec. 4.3, point location);
+ *      - if c would encroach a subsegment on its cavity boundary, split those
+ *        subsegments instead (Sec. 4.2: midpoints take priority over
+ *        circumcentres; such a circumcentre is redundant);
+ *      - else insert c by Bowyer-Watson;
+ *   3. stop when nothing is encroached and no triangle is bad (bad triangles
+ *      whose shortest edge joins two segments meeting at a small input angle
+ *      are accepted, Sec. 4.1).
+ */
+#include "mesh_int.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------- small input angles ---------------- */
+typedef struct {
+    int64_t* off;   /* CSR over input vertices: incident input segments */
+    int32_t* adj;
+} seg_adj;
+
+static void build_adj(const or_mesh* M, seg_adj* A) {
+    A->off = (int64_t*)calloc((size_t)M->n_in + 1, sizeof(int64_t));
+    A->adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * M->nseg + 1));
+    for (int64_t s = 0; s < M->nseg; ++s) {
+        A->off[M->seg[2 * s] + 1]++;
+        A->off[M->seg[2 * s + 1] + 1]++;
+    }
+    for (int64_t v = 0; v < M->n_in; ++v) A->off[v + 1] += A->off[v];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(M->n_in + 1));
+    memcpy(fill, A->off, sizeof(int64_t) * (size_t)(M->n_in + 1));
+    for (int64_t s = 0; s < M->nseg; ++s) {
+        A->adj[fill[M->seg[2 * s]]++] = (int32_t)s;
+        A->adj[fill[M->seg[2 * s + 1]]++] = (int32_t)s;
+    }
+    free(fill);
+}
+
+/* two distinct input segments meeting at a shared endpoint at less than 60 degrees */
+static int small_pair(const or_mesh* M, int64_t s1, int64_t s2) {
+    if (s1 == s2) return 0;
+    const int32_t* a = M->seg + 2 * s1;
+    const int32_t* b = M->seg + 2 * s2;
+    int64_t o = -1, p = -1, q = -1;
+    for (int i = 0; i < 2 && o < 0; ++i)
+        for (int j = 0; j < 2; ++j)
+            if (a[i] == b[j]) { o = a[i]; p = a[1 - i]; q = b[1 - j]; break; }
+    if (o < 0) return 0;
+    double ux = M->x[p] - M->x[o], uy = M->y[p] - M->y[o];
+    double wx = M->x[q] - M->x[o], wy = M->y[q] - M->y[o];
+    double dot = ux * wx + uy * wy;
+    double nn = sqrt(ux * ux + uy * uy) * sqrt(wx * wx + wy * wy);
+    return 2.0 * dot > nn;
+}
+
+/* the segments a vertex lies on: its own segment for a Steiner vertex placed
+ * on one, the incident segments for an input vertex */
+static int segs_of(const or_mesh* M, const seg_adj* A, int64_t v, int32_t* out, int cap) {
+    if (v < M->n_in) {
+        int n = 0;
+        for (int64_t k = A->off[v]; k < A->off[v + 1] && n < cap; ++k) out[n++] = A->adj[k];
+        return n;
+    }
+    if (M->vseg[v] >= 0) { out[0] = M->vseg[v]; return 1; }
+    return 0;
+}
+
+/* C10: a bad triangle is accepted when its shortest edge joins vertices on two
+ * segments that meet at a small input angle */
+static int exempt(const or_mesh* M, const seg_adj* A, int64_t t) {
+    if (M->nseg < 2) return 0;
+    const int32_t* v = M->tv + 3 * t;
+    double best = -1;
+    int be = 0;
+    for (int e = 0; e < 3; ++e) {
+        int64_t a = v[(e + 1) % 3], b = v[(e + 2) % 3];
+        double dx = M->x[b] - M->x[a], dy = M->y[b] - M->y[a];
+        double l = dx * dx + dy * dy;
+        if (best < 0 || l < best) { best = l; be = e; }
+    }
+    int64_t u = v[(be + 1) % 3], w = v[(be + 2) % 3];
+    int32_t su[64], sw[64];
+    int nu = segs_of(M, A, u, su, 64), nw = segs_of(M, A, w, sw, 64);
+    for (int i = 0; i < nu; ++i)
+        for (int j = 0; j < nw; ++j)
+            if (small_pair(M, su[i], sw[j])) return 1;
+    return 0;
+}
+
+/* C6: split point of subsegment (u,v) of input segment s.  If exactly one
+ * endpoint is an input vertex where segments meet at a small angle, the point
+ * sits at the power-of-two distance from it nearest to half the length
+ * (concentric shells); otherwise the midpoint. */
+static void split_point(const or_mesh* M, int64_t u, int64_t v, double* px, double* py) {
+    int au = (u < M->n_in) && M->apex && M->apex[u];
+    int av = (v < M->n_in) && M->apex && M->apex[v];
+    if (au == av) {
+        or_midpoint(M->x[u], M->y[u], M->x[v], M->y[v], px, py);
+        return;
+    }
+    int64_t o = au ? u : v, q = au ? v : u;
+    double dx = M->x[q] - M->x[o], dy = M->y[q] - M->y[o];
+    double L = sqrt(dx * dx + dy * dy);
+    int e;
+    double m = frexp(0.5 * L, &e);           /* 0.5 L = m 2^e, m in [0.5,1) */
+    double d = (m * m < 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+    double r = d / L;
+    *px = M->x[o] + dx * r;
+    *py = M->y[o] + dy * r;
+}
+
+/* ---------------- work queues ---------------- */
+typedef struct { double key; int64_t t; int32_t v[3]; } hent;
+typedef struct { hent* a; int64_t n, cap; } heap;
+
+static void hpush(heap* h, hent e) {
+    if (h->n + 1 > h->cap) {
+        h->cap = h->cap ? 2 * h->cap : 1024;
+        h->a = (hent*)realloc(h->a, sizeof(hent) * (size_t)h->cap);
+    }
+    int64_t i = h->n++;
+    h->a[i] = e;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h->a[p].key >= h->a[i].key) break;
+        hent t = h->a[p];
+        h->a[p] = h->a[i];
+        h->a[i] = t;
+        i = p;
+    }
+}
+
+static hent hpop(heap* h) {
+    hent top = h->a[0];
+    h->a[0] = h->a[--h->n];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < h->n && h->a[l].key > h->a[m].key) m = l;
+        if (r < h->n && h->a[r].key > h->a[m].key) m = r;
+        if (m == i) break;
+        hent t = h->a[m];
+        h->a[m] = h->a[i];
+        h->a[i] = t;
+        i = m;
+    }
+    return top;
+}
+
+typedef struct { int64_t u, v; int forced; } sent;
+typedef struct { sent* a; int64_t head, n, cap; } fifo;
+
+static void qpush(fifo* q, int64_t u, int64_t v, int forced) {
+    if (q->n + 1 > q->cap) {
+        int64_t nc = q->cap ? 2 * q->cap : 1024;
+        sent* na = (sent*)malloc(sizeof(sent) * (size_t)nc);
+        for (int64_t i = 0; i < q->n; ++i) na[i] = q->a[(q->head + i) % q->cap];
+        free(q->a);
+        q->a = na;
+        q->cap = nc;
+        q->head = 0;
+    }
+    q->a[(q->head + q->n) % q->cap] = (sent){u, v, forced};
+    ++q->n;
+}
+
+static sent qpop(fifo* q) {
+    sent s = q->a[q->head];
+    q->head = (q->head + 1) % q->cap;
+    --q->n;
+    return s;
+}
+
+typedef struct {
+    or_mesh* M;
+    seg_adj A;
+    double B2;
+    int order;
+    int64_t seq;
+    heap H;
+    fifo Q;
+    int64_t* nt_buf;
+    int64_t nt_cap;
+} rstate;
+
+static void consider_tri(rstate* S, int64_t t) {
+    or_mesh* M = S->M;
+    const int32_t* v = M->tv + 3 * t;
+    double ax = M->x[v[0]], ay = M->y[v[0]], bx = M->x[v[1]], by = M->y[v[1]];
+    double cx = M->x[v[2]], cy = M->y[v[2]];
+    if (!or_is_bad(ax, ay, bx, by, cx, cy, S->B2)) return;
+    if (exempt(M, &S->A, t)) return;
+    hent e;
+    e.t = t;
+    e.v[0] = v[0];
+    e.v[1] = v[1];
+    e.v[2] = v[2];
+    if (S->order == 0) e.key = or_ratio_key(ax, ay, bx, by, cx, cy);
+    else if (S->order == 1) e.key = -(double)(S->seq++);
+    else e.key = or_tri_measure(ax, ay, bx, by, cx, cy);
+    hpush(&S->H, e);
+}
+
+/* new triangles: queue the bad ones and re-check their subsegments */
+static void after_insert(rstate* S, int64_t nn) {
+    or_mesh* M = S->M;
+    for (int64_t i = 0; i < nn; ++i) {
+        int64_t t = S->nt_buf[i];
+        consider_tri(S, t);
+        const int32_t* v = M->tv + 3 * t;
+        for (int e = 0; e < 3; ++e) {
+            int64_t a = v[(e + 1) % 3], b = v[(e + 2) % 3];
+            if (or_is_sub(M, a, b)) qpush(&S->Q, a, b, 0);
+        }
+    }
+}
+
+/* C2: encroached iff the apex of an adjacent triangle is strictly inside the
+ * diametral circle */
+static int encroached(const or_mesh* M, int64_t u, int64_t v) {
+    int64_t ts[2] = {or_map_get(&M->edges, or_dkey(u, v)), or_map_get(&M->edges, or_dkey(v, u))};
+    for (int k = 0; k < 2; ++k) {
+        int64_t t = ts[k];
+        if (t < 0) continue;
+        const int32_t* tv = M->tv + 3 * t;
+        for (int j = 0; j < 3; ++j) {
+            int64_t w = tv[j];
+            if (w == u || w == v) continue;
+            if (or_dot_sign(M->x[u], M->y[u], M->x[v], M->y[v], M->x[w], M->y[w]) < 0) return 1;
+        }
+    }
+    return 0;
+}
+
+static int split_sub(rstate* S, int64_t u, int64_t v) {
+    or_mesh* M = S->M;
+    double px, py;
+    split_point(M, u, v, &px, &py);
+    int32_t sid = (int32_t)or_map_get(&M->subs, or_ukey(u, v));
+    int64_t p = or_add_vertex(M, px, py, sid);
+    int64_t nn = or_insert_vertex(M, p, -1, u, v, &S->nt_buf, &S->nt_cap);
+    if (nn < 0) { M->nv--; return OR_INTERNAL; }
+    M->n_steiner++;
+    after_insert(S, nn);
+    return OR_OK;
+}
+
+int or_refine(or_mesh* M, double B, int64_t max_steiner, int order) {
+    rstate S;
+    memset(&S, 0, sizeof(S));
+    S.M = M;
+    S.B2 = B * B;
+    S.order = order;
+    build_adj(M, &S.A);
+    int status = OR_OK;
+    for (int64_t i = 0; i < M->subs.cap; ++i) {
+        if (M->subs.keys[i] == UINT64_MAX) continue;
+        qpush(&S.Q, (int64_t)(M->subs.keys[i] >> 32), (int64_t)(M->subs.keys[i] & 0xffffffffu), 0);
+    }
+    for (int64_t t = 0; t < M->nt; ++t)
+        if (M->alive[t]) consider_tri(&S, t);
+    int64_t* ctris = NULL;
+    int64_t ccap = 0, *cbnd = NULL, cbcap = 0;
+    for (;;) {
+        while (S.Q.n > 0) {
+            sent s = qpop(&S.Q);
+            if (!or_is_sub(M, s.u, s.v)) continue;
+            if (!s.forced && !encroached(M, s.u, s.v)) continue;
+            if (M->n_steiner >= max_steiner) { status = OR_LIMIT; goto done; }
+            status = split_sub(&S, s.u, s.v);
+            if (status != OR_OK) goto done;
+        }
+        int64_t t = -1;
+        while (S.H.n > 0) {
+            hent e = hpop(&S.H);
+            const int32_t* v = M->tv + 3 * e.t;
+            if (!M->alive[e.t] || v[0] != e.v[0] || v[1] != e.v[1] || v[2] != e.v[2]) continue;
+            t = e.t;
+            break;
+        }
+        if (t < 0) break;
+        if (M->n_steiner >= max_steiner) { status = OR_LIMIT; goto done; }
+        const int32_t* v = M->tv + 3 * t;
+        double cx, cy;
+        or_circumcenter(M->x[v[0]], M->y[v[0]], M->x[v[1]], M->y[v[1]], M->x[v[2]], M->y[v[2]],
+                        &cx, &cy);
+        int64_t su = -1, sv = -1;
+        int64_t tl = or_locate(M, t, cx, cy, 1, &su, &sv);
+        if (tl == -2) { status = OR_INTERNAL; goto done; }
+        if (tl < 0) {
+            qpush(&S.Q, su, sv, 1);
+            consider_tri(&S, t);
+            continue;
+        }
+        int64_t nb = 0;
+        or_cavity(M, cx, cy, tl, -1, &ctris, &ccap, &cbnd, &nb, &cbcap);
+        int enc = 0;
+        for (int64_t i = 0; i < nb; ++i) {
+            int64_t a = cbnd[2 * i], b = cbnd[2 * i + 1];
+            if (!or_is_sub(M, a, b)) continue;
+            if (or_dot_sign(M->x[a], M->y[a], M->x[b], M->y[b], cx, cy) < 0) {
+                qpush(&S.Q, a, b, 1);
+                enc = 1;
+            }
+        }
+        if (enc) {
+            consider_tri(&S, t);
+            continue;
+        }
+        int64_t p = or_add_vertex(M, cx, cy, -1);
+        int64_t nn = or_insert_vertex(M, p, tl, -1, -1, &S.nt_buf, &S.nt_cap);
+        if (nn < 0) { M->nv--; status = OR_INTERNAL; goto done; }
+        M->n_steiner++;
+        after_insert(&S, nn);
+    }
+done:
+    free(ctris);
+    free(cbnd);
+    free(S.H.a);
+    free(S.Q.a);
+    free(S.nt_buf);
+    free(S.A.off);
+    free(S.A.adj);
+    return status;
+}
+
+/* ---------------- fixed batches (parity of the insertion kernels) ---------------- */
+int or_insert_points(or_mesh* M, const double* xy, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) {
+        double px = xy[2 * i], py = xy[2 * i + 1];
+        int64_t t = or_locate(M, M->last_tri, px, py, 0, NULL, NULL);
+        if (t < 0) return OR_INPUT;
+        const int32_t* v = M->tv + 3 * t;
+        for (int e = 0; e < 3; ++e) {
+            int64_t a = v[(e + 1) % 3], b = v[(e + 2) % 3];
+            if (M->x[v[e]] == px && M->y[v[e]] == py) return OR_INPUT;
+            if (or_is_sub(M, a, b) &&
+                or_orient(M->x[a], M->y[a], M->x[b], M->y[b], px, py) == 0)
+                return OR_INPUT;
+        }
+        int64_t p = or_add_vertex(M, px, py, -1);
+        if (or_insert_vertex(M, p, t, -1, -1, NULL, NULL) < 0) { M->nv--; return OR_INTERNAL; }
+        M->n_steiner++;
+    }
+    return OR_OK;
+}
+
+int or_split_subsegments(or_mesh* M, const double* abxy, int64_t n) {
+    or_map pos;
+    or_map_init(&pos, 2 * M->nv + 16);
+    for (int64_t v = 0; v < M->nv; ++v) {
+        uint64_t kx, ky;
+        memcpy(&kx, &M->x[v], 8);
+        memcpy(&ky, &M->y[v], 8);
+        or_map_put(&pos, kx * 0x9e3779b97f4a7c15ULL ^ ky, v);
+    }
+    int st = OR_OK;
+    for (int64_t i = 0; i < n && st == OR_OK; ++i) {
+        int64_t ids[2];
+        for (int k = 0; k < 2; ++k) {
+            uint64_t kx, ky;
+            memcpy(&kx, &abxy[4 * i + 2 * k], 8);
+            memcpy(&ky, &abxy[4 * i + 2 * k + 1], 8);
+            ids[k] = or_map_get(&pos, kx * 0x9e3779b97f4a7c15ULL ^ ky);
+        }
+        for (int k = 0; k < 2; ++k)
+            if (ids[k] >= 0 && (M->x[ids[k]] != abxy[4 * i + 2 * k] ||
+                                M->y[ids[k]] != abxy[4 * i + 2 * k + 1]))
+                ids[k] = -1;
+        if (ids[0] < 0 || ids[1] < 0 || !or_is_sub(M, ids[0], ids[1])) { st = OR_INPUT; break; }
+        double px, py;
+        or_midpoint(M->x[ids[0]], M->y[ids[0]], M->x[ids[1]], M->y[ids[1]], &px, &py);
+        int32_t sid = (int32_t)or_map_get(&M->subs, or_ukey(ids[0], ids[1]));
+        int64_t p = or_add_vertex(M, px, py, sid);
+        uint64_t kx, ky;
+        memcpy(&kx, &px, 8);
+        memcpy(&ky, &py, 8);
+        or_map_put(&pos, kx * 0x9e3779b97f4a7c15ULL ^ ky, p);
+        if (or_insert_vertex(M, p, -1, ids[0], ids[1], NULL, NULL) < 0) { M->nv--; st = OR_INTERNAL; }
+        else M->n_steiner++;
+    }
+    or_map_free(&pos);
+    return st;
+}
