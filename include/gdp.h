@@ -1,0 +1,169 @@
+/*
+ * gdp.h -- C ABI of the GB300 constrained Delaunay refinement library (gDP2d).
+ *
+ * The library turns a planar straight-line graph (PSLG: points P and
+ * non-crossing segments E, Sec. 4 of the paper) into its constrained Delaunay
+ * triangulation (CDT, Algorithm 1 line 1) and refines it (Algorithm 1 lines
+ * 2-9): Steiner points are inserted in parallel until no subsegment is
+ * encroached (a vertex strictly inside its diametral circle, Sec. 4.2) and no
+ * triangle has radius-edge ratio above B (the 3D bad-element measure of
+ * Sec. 5.1, used here in 2D; B = sqrt 2 is a 20.7 degree angle bound).
+ *
+ * Everything between create and export runs on one GPU in CUDA kernels; the
+ * host only launches them.  There is no CPU fallback: every call returns
+ * GDP_ERR_CUDA when no usable device is present.
+ *
+ * Conventions for every entry point:
+ *   - Host pointers unless the name says _device.  Input buffers are owned by
+ *     the caller and copied; the library never keeps a caller pointer.
+ *   - Meshes and batches are owned by the library from create to destroy.
+ *   - Coordinates are FP64, points as interleaved (x, y) pairs; segments are
+ *     pairs of 0-based indices into the points; triangles are CCW triples.
+ *   - Every call returns a gdp_status.  After an error the object can still
+ *     be destroyed; after GDP_ERR_NOMEM or GDP_ERR_ITER_LIMIT during refine
+ *     the mesh is still a valid CDT and can be exported.
+ *   - cuda_stream may be NULL (the legacy default stream) or a cudaStream_t;
+ *     all work of the object is ordered on that stream.
+ */
+#ifndef GDP_H
+#define GDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GDP_OK = 0,
+    GDP_ERR_INPUT = 1,       /* NaN/inf coordinate, duplicate point, bad index, crossing
+                                segments, segment through a vertex, empty domain */
+    GDP_ERR_NOMEM = 2,       /* device allocation failed or a mesh ran out of slots */
+    GDP_ERR_ITER_LIMIT = 3,  /* refinement hit max_iter */
+    GDP_ERR_WALK_LIMIT = 4,  /* a point-location walk exceeded its step bound */
+    GDP_ERR_CUDA = 5,        /* CUDA runtime error or no device */
+    GDP_ERR_INTERNAL = 6,    /* an invariant check inside a kernel failed */
+    GDP_ERR_CAPACITY = 7     /* a per-element work buffer (cavity, segment region) overflowed */
+} gdp_status;
+
+typedef struct gdp_mesh gdp_mesh;
+
+/* Refinement options.  Zero-initialised fields take the defaults. */
+typedef struct {
+    double B;             /* radius-edge bound (> 0.70711; sqrt 2 default when 0) */
+    double max_len;       /* reserved: edge-length bound, <= 0 or INF = off */
+    int32_t max_iter;     /* parallel iterations (Algorithm 1 loop), 0 = 100000 */
+    int32_t cand_cap;     /* candidates per iteration and mesh; 0 = no cap (Rule 2) */
+    int32_t graph_iters;  /* iterations per CUDA-graph replay; 0 = 8, < 0 = no graph */
+    int32_t flags;        /* reserved, 0 */
+} gdp_refine_opts;
+
+typedef struct {
+    int64_t n_in_pts;     /* input points */
+    int64_t n_steiner;    /* Steiner points inserted by refinement */
+    int64_t n_tris;       /* live triangles */
+    int64_t n_subsegs;    /* subsegments */
+    int64_t iterations;   /* refinement iterations executed */
+    int64_t candidates;   /* splitting points considered, summed over iterations */
+    int64_t inserted;     /* splitting points inserted, summed over iterations */
+    int64_t cdt_rounds;   /* parallel insertion rounds of the initial CDT */
+    double refine_ms;     /* device time of the refinement loop */
+    double cdt_ms;        /* device time of the initial CDT */
+    int64_t launches;     /* kernel launches of this object since creation */
+} gdp_stats;
+
+/* Build the CDT of a PSLG on the GPU (Algorithm 1 line 1).
+ *   xy:  2*n_pts doubles, host;   seg: 2*n_seg int32 indices, host (may be NULL if 0)
+ * The domain is the region enclosed by segments: triangles reachable from
+ * outside without crossing a segment are removed, so the convex hull must be
+ * covered by segments for the whole hull to be meshed.
+ * Errors: GDP_ERR_INPUT for invalid input, GDP_ERR_NOMEM, GDP_ERR_CUDA. */
+int gdp_mesh_create(const double* xy, int64_t n_pts, const int32_t* seg, int64_t n_seg,
+                    void* cuda_stream, gdp_mesh** out);
+
+/* Same, with xy and seg already in device memory (not modified, not kept). */
+int gdp_mesh_create_device(const double* xy_device, int64_t n_pts, const int32_t* seg_device,
+                           int64_t n_seg, void* cuda_stream, gdp_mesh** out);
+
+/* Refine (Algorithm 1 lines 2-9) until nothing is encroached and no
+ * triangle is bad, bad triangles at small input angles excepted (Sec. 4.1).
+ * opts may be NULL (defaults); stats may be NULL.  Blocks until done. */
+int gdp_mesh_refine(gdp_mesh* mesh, const gdp_refine_opts* opts, gdp_stats* stats);
+
+/* Copy the mesh out.  Call with NULL buffers to get the sizes only.
+ *   xy:     2*cap_pts doubles: input points keep ids 0..n_in-1, Steiner points follow
+ *   tri:    3*cap_tri int32, CCW
+ *   subseg: 3*cap_seg int32: (u, v, input segment id)
+ * A buffer smaller than the size needed gives GDP_ERR_INPUT and copies nothing. */
+int gdp_mesh_export(gdp_mesh* mesh, double* xy, int64_t cap_pts, int32_t* tri, int64_t cap_tri,
+                    int32_t* subseg, int64_t cap_seg, int64_t* n_pts, int64_t* n_tri,
+                    int64_t* n_seg);
+
+/* Insert a fixed batch of free points (strictly inside the domain, not on a
+ * subsegment, no duplicates) with the parallel cavity kernels (Sec. 5.2
+ * cavity insertion, priority marks and the dependence check), in as many
+ * parallel rounds as conflicts require.  The result is the CDT of the
+ * enlarged vertex set. */
+int gdp_mesh_insert_points(gdp_mesh* mesh, const double* xy, int64_t n);
+
+/* Split the subsegments given by endpoint coordinates (4 doubles each:
+ * ax, ay, bx, by) at their midpoints, in parallel rounds. */
+int gdp_mesh_split_subsegments(gdp_mesh* mesh, const double* abxy, int64_t n);
+
+/* One bad-element scan (Algorithm 1 line 3) plus splitting points and
+ * priorities (lines 5-6, before point location) of the current mesh.
+ * Outputs per element, cap entries each (host buffers, NULL to skip):
+ *   kind[i]:  0 = bad triangle, 1 = encroached subsegment
+ *   verts[3i..3i+2]: the triangle's vertices (CCW), or the subsegment's two
+ *             endpoints and -1
+ *   pt[2i..2i+1]: circumcentre (C5 formula) or split point
+ *   meas[i]: priority measure bits (float32 bits of 2*area or squared length)
+ * *count receives the number of elements (all of them, even beyond cap). */
+int gdp_mesh_scan(gdp_mesh* mesh, double B, int32_t* kind, int32_t* verts, double* pt,
+                  uint32_t* meas, int64_t cap, int64_t* count);
+
+/* Statistics of the last create/refine. */
+int gdp_mesh_stats(gdp_mesh* mesh, gdp_stats* stats);
+
+/* Per-kernel timing.  gdp_mesh_profile(mesh, 1) clears the table and brackets
+ * every later kernel launch of the mesh with CUDA events on its stream
+ * (refinement then runs without CUDA graphs); 0 turns it off.
+ * gdp_mesh_kernel_time reads entry i of the table: the kernel's name (NUL
+ * terminated, truncated to name_cap), its summed device time in ms and its
+ * launch count.  Returns GDP_ERR_INPUT when i is past the end. */
+int gdp_mesh_profile(gdp_mesh* mesh, int enable);
+int gdp_mesh_kernel_time(gdp_mesh* mesh, int32_t i, char* name, int64_t name_cap, double* total_ms,
+                         int64_t* count);
+
+void gdp_mesh_destroy(gdp_mesh* mesh);
+
+/* ---------------- batches: many independent PSLGs in one pool ----------------
+ * All meshes of a batch share device arrays; every kernel launch processes
+ * all of them (one launch per step for the whole batch), and each mesh is
+ * refined exactly as it would be alone.
+ *   xy:      concatenated points, 2*sum(n_pts) doubles
+ *   pt_off:  n_meshes+1 offsets into points (pt_off[0] = 0)
+ *   seg:     concatenated segments, 2*sum(n_seg) int32, indices LOCAL to their mesh
+ *   seg_off: n_meshes+1 offsets into segments */
+typedef struct gdp_batch gdp_batch;
+
+int gdp_batch_create(const double* xy, const int64_t* pt_off, const int32_t* seg,
+                     const int64_t* seg_off, int32_t n_meshes, void* cuda_stream,
+                     gdp_batch** out);
+/* B: one bound per mesh (NULL: opts->B for all). */
+int gdp_batch_refine(gdp_batch* b, const double* B, const gdp_refine_opts* opts,
+                     gdp_stats* stats);
+/* per-mesh status and sizes (arrays of n_meshes, NULL to skip) */
+int gdp_batch_info(gdp_batch* b, int32_t* status, int64_t* n_pts, int64_t* n_tri,
+                   int64_t* n_seg, int64_t* n_steiner);
+int gdp_batch_export(gdp_batch* b, int32_t mesh, double* xy, int64_t cap_pts, int32_t* tri,
+                     int64_t cap_tri, int32_t* subseg, int64_t cap_seg, int64_t* n_pts,
+                     int64_t* n_tri, int64_t* n_seg);
+void gdp_batch_destroy(gdp_batch* b);
+
+const char* gdp_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,984 @@
+// Host side of the library: pool layout and allocation, the CDT driver, the
+// refinement loop (graph-captured iterations), export, and the C ABI of
+// include/gdp.h.  The host only sizes buffers, launches kernels and reads a
+// few counters; all mesh computation happens in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gdp.h"
+#include "gdp_cdt.cuh"
+
+using namespace gdp;
+
+namespace {
+
+// ---------------------------------------------------------------- setup kernels
+__global__ void k_scatter_points(Pool P, const double2* src, const long long* pt_off) {
+  const int m = blockIdx.x;
+  const MeshInfo& M = P.mi[m];
+  for (int k = threadIdx.x; k < M.n_in; k += blockDim.x) P.V[M.vert_base + k] = src[pt_off[m] + k];
+}
+
+__global__ void k_scatter_segs(Pool P, const int2* src, const long long* seg_off, int* seg_mesh) {
+  const int m = blockIdx.x;
+  MeshInfo& M = P.mi[m];
+  for (int k = threadIdx.x; k < M.n_seg; k += blockDim.x) {
+    const int2 s = src[seg_off[m] + k];
+    const int g = M.seg_base + k;
+    seg_mesh[g] = m;
+    if (s.x < 0 || s.x >= M.n_in || s.y < 0 || s.y >= M.n_in || s.x == s.y) {
+      M.status = S_INPUT;
+      P.seg[g] = make_int2(M.vert_base, M.vert_base);
+      continue;
+    }
+    P.seg[g] = make_int2(M.vert_base + s.x, M.vert_base + s.y);
+  }
+}
+
+__global__ void k_adj_count(Pool P, const int* seg_mesh, int n_seg_total, int* cnt) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int g = gt; g < n_seg_total; g += gs) {
+    const MeshInfo& M = P.mi[seg_mesh[g]];
+    const int2 s = P.seg[g];
+    atomicAdd(&cnt[M.adj_base + (s.x - M.vert_base) + 1], 1);
+    atomicAdd(&cnt[M.adj_base + (s.y - M.vert_base) + 1], 1);
+  }
+}
+
+__global__ void k_adj_fill(Pool P, const int* seg_mesh, int n_seg_total, int* cursor) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int g = gt; g < n_seg_total; g += gs) {
+    const MeshInfo& M = P.mi[seg_mesh[g]];
+    const int2 s = P.seg[g];
+    P.adj[atomicAdd(&cursor[M.adj_base + (s.x - M.vert_base)], 1)] = g;
+    P.adj[atomicAdd(&cursor[M.adj_base + (s.y - M.vert_base)], 1)] = g;
+  }
+}
+
+// inclusive scan of an int array in place (block counts, then block scans)
+__global__ void __launch_bounds__(BS) k_iscan_count(int* a, int n, int* blk) {
+  __shared__ int sm[33];
+  const Chunk ch = chunk_of(n);
+  int s = 0;
+  for (int k = ch.b0 + threadIdx.x; k < ch.b1; k += BS) s += a[k];
+  s = block_sum(s, sm);
+  if (threadIdx.x == 0) blk[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(BS) k_iscan_write(int* a, int n, const int* blk) {
+  __shared__ int sm[33];
+  const Chunk ch = chunk_of(n);
+  int off = block_prefix(blk, blockIdx.x, sm);
+  for (int base = ch.b0; base < ch.b1; base += BS) {
+    const int k = base + threadIdx.x;
+    const int v = k < ch.b1 ? a[k] : 0;
+    int tot;
+    const int r = block_excl_scan(v, sm, tot);
+    if (k < ch.b1) a[k] = off + r + v;
+    off += tot;
+  }
+}
+
+// input vertices where two segments meet at less than 60 degrees
+__global__ void k_apex(Pool P) {
+  const int m = blockIdx.x;
+  MeshInfo& M = P.mi[m];
+  int any = 0;
+  for (int l = threadIdx.x; l < M.n_in; l += blockDim.x) {
+    const int v = M.vert_base + l;
+    P.apex[v] = 0;
+    const int a0 = P.adj_off[M.adj_base + l], a1 = P.adj_off[M.adj_base + l + 1];
+    for (int i = a0; i < a1 && !P.apex[v]; ++i)
+      for (int j = i + 1; j < a1; ++j)
+        if (small_pair(P, P.adj[i], P.adj[j])) { P.apex[v] = 1; any = 1; break; }
+  }
+  if (any) M.has_apex = 1;
+}
+
+__global__ void k_iota(int* a, int n) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int k = gt; k < n; k += gs) a[k] = k;
+}
+
+__global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int k = gt; k < n; k += gs) {
+    P.pts[k] = ids[k];
+    P.loc[ids[k]] = t;
+  }
+}
+
+#define CK(x)                                                                         \
+  do {                                                                                \
+    cudaError_t e_ = (x);                                                             \
+    if (e_ != cudaSuccess) {                                                          \
+      if (std::getenv("GDP_DEBUG"))                                                   \
+        std::fprintf(stderr, "gdp: %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return GDP_ERR_CUDA;                                                            \
+    }                                                                                 \
+  } while (0)
+
+// every kernel launch of the library goes through LAUNCH: it is counted and,
+// when profiling is on, bracketed by CUDA events on the launching stream
+#define LAUNCH(h, kern, grid, ...)                                   \
+  do {                                                               \
+    (h).prof_begin(#kern);                                           \
+    kern<<<(grid), BS, 0, (h).stream>>>(__VA_ARGS__);                \
+    (h).prof_end();                                                  \
+  } while (0)
+
+double env_double(const char* name, double def) {
+  const char* s = std::getenv(name);
+  return s ? std::atof(s) : def;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- the pool
+struct PoolHost {
+  cudaStream_t stream = nullptr;
+  int n_sm = 0, G = 0;
+  Pool P{};
+  std::vector<MeshInfo> hmi;
+  std::vector<int2> hseg;         // input segments, global vertex ids
+  int n_mesh = 0;
+  long long tot_in = 0, tot_seg = 0, pts_cap = 0;
+  Ctrl* hctrl = nullptr;          // pinned
+  std::vector<void*> allocs;
+  gdp_stats stats{};
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-kernel timing (profiling mode) and launch counting
+  bool prof = false;
+  long long launches = 0;
+  int kernels_per_iter = 8;
+  struct Pending { const char* name; cudaEvent_t a, b; };
+  std::vector<Pending> pend;
+  std::vector<std::pair<std::string, std::pair<double, long long>>> ktimes;
+  const char* cur_name = nullptr;
+  cudaEvent_t cur_ev = nullptr;
+
+  void prof_begin(const char* name) {
+    ++launches;
+    if (!prof) return;
+    cur_name = name;
+    cudaEventCreate(&cur_ev);
+    cudaEventRecord(cur_ev, stream);
+  }
+  void prof_end() {
+    if (!prof) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, stream);
+    pend.push_back({cur_name, cur_ev, e});
+  }
+  void prof_flush() {
+    if (pend.empty()) return;
+    cudaStreamSynchronize(stream);
+    for (auto& p : pend) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      bool found = false;
+      for (auto& kv : ktimes)
+        if (kv.first == p.name) { kv.second.first += ms; kv.second.second += 1; found = true; break; }
+      if (!found) ktimes.push_back({p.name, {ms, 1}});
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    pend.clear();
+  }
+
+  ~PoolHost() {
+    prof_flush();
+    if (graph) cudaGraphExecDestroy(graph);
+    for (void* p : allocs) cudaFree(p);
+    if (hctrl) cudaFreeHost(hctrl);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+
+  template <class X>
+  int alloc(X** p, size_t n, int fill = 0) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(X)) != cudaSuccess) {
+      cudaGetLastError();
+      return GDP_ERR_NOMEM;
+    }
+    allocs.push_back(q);
+    *p = reinterpret_cast<X*>(q);
+    if (cudaMemsetAsync(q, fill, std::max<size_t>(n, 1) * sizeof(X), stream) != cudaSuccess)
+      return GDP_ERR_CUDA;
+    return GDP_OK;
+  }
+  void release(void* p) {
+    auto it = std::find(allocs.begin(), allocs.end(), p);
+    if (it != allocs.end()) {
+      cudaFree(p);
+      allocs.erase(it);
+    }
+  }
+
+  int sync_ctrl() {
+    CK(cudaMemcpyAsync(hctrl, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return GDP_OK;
+  }
+  int pull_mi() {
+    CK(cudaMemcpyAsync(hmi.data(), P.mi, sizeof(MeshInfo) * n_mesh, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    return GDP_OK;
+  }
+  int push_mi() {
+    CK(cudaMemcpyAsync(P.mi, hmi.data(), sizeof(MeshInfo) * n_mesh, cudaMemcpyHostToDevice, stream));
+    return GDP_OK;
+  }
+  int set_ctrl_field(size_t off, int v) {
+    CK(cudaMemcpyAsync(reinterpret_cast<char*>(P.ctrl) + off, &v, sizeof(int), cudaMemcpyHostToDevice,
+                       stream));
+    CK(cudaStreamSynchronize(stream));
+    return GDP_OK;
+  }
+
+  int setup(const double* xy, const long long* pt_off, const int32_t* seg, const long long* seg_off,
+            int nm, bool on_device, void* s);
+  int build_cdt();
+  int insert_rounds(int stop_cons, int* rounds_out);
+  int refine(const double* B, const gdp_refine_opts* o);
+  int launch_iteration();
+  int export_mesh(int m, double* xy, int64_t cap_pts, int32_t* tri, int64_t cap_tri, int32_t* sub,
+                  int64_t cap_seg, int64_t* n_pts, int64_t* n_tri, int64_t* n_seg);
+};
+
+int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* seg,
+                    const long long* seg_off, int nm, bool on_device, void* s) {
+  stream = reinterpret_cast<cudaStream_t>(s);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return GDP_ERR_CUDA; }
+  CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  G = 4 * n_sm;
+  prof = std::getenv("GDP_PROFILE") != nullptr;
+  CK(cudaMallocHost(&hctrl, sizeof(Ctrl)));
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  n_mesh = nm;
+  hmi.assign(nm, MeshInfo{});
+  const double fp = env_double("GDP_STEINER_PER_POINT", 3.0);
+  const double fs = env_double("GDP_STEINER_PER_SEGMENT", 64.0);
+  long long tb = 0, vb = 0, sb = 0, ab = 0, pb = 0;
+  for (int m = 0; m < nm; ++m) {
+    const long long n_in = pt_off[m + 1] - pt_off[m];
+    const long long n_seg = seg_off[m + 1] - seg_off[m];
+    if (n_in < 3 || n_seg < 0) return GDP_ERR_INPUT;
+    const long long steiner_cap = (long long)(fp * n_in + fs * n_seg) + 1024;
+    const long long vcap = n_in + N_AUX + steiner_cap;
+    const long long tcap = 2 * vcap + 16;
+    MeshInfo& M = hmi[m];
+    M.tri_base = (int)tb; M.tri_cap = (int)tcap;
+    M.vert_base = (int)vb; M.vert_cap = (int)vcap;
+    M.n_in = (int)n_in; M.seg_base = (int)sb; M.n_seg = (int)n_seg;
+    M.adj_base = (int)ab; M.pts_base = (int)pb;
+    M.status = S_OK; M.active = 0; M.first_cand = M.last_cand = -1;
+    tb += tcap; vb += vcap; sb += n_seg; ab += n_in + 1; pb += n_in + 4;
+    if (tb >= (1ll << 29) || vb >= (1ll << 31) - 1) return GDP_ERR_NOMEM;
+  }
+  tot_in = pb - 4 * nm;
+  tot_seg = sb;
+  P.n_mesh = nm;
+  P.n_slots = (int)tb;
+  P.n_verts = (int)vb;
+  P.cap_cand = (int)std::min<long long>(std::max<long long>(tb / 4, 65536), 1 << 23);
+  P.cap_segq = (int)std::min<long long>(std::max<long long>(sb, 1), 65536);
+  int st;
+#define AL(ptr, n, fill) \
+  if ((st = alloc(&(ptr), (size_t)(n), fill)) != GDP_OK) return st;
+  AL(P.V, vb, 0);
+  AL(P.vseg, vb, 0xff);
+  AL(P.vtri, vb, 0xff);
+  AL(P.apex, vb, 0);
+  AL(P.T, tb, 0xff);
+  AL(P.N, tb, 0xff);
+  AL(P.mark, tb, 0);
+  AL(P.newref, 4 * tb, 0xff);
+  AL(P.dirty, tb, 0);
+  AL(P.flag, tb, 0);
+  AL(P.mi, nm, 0);
+  AL(P.seg, sb, 0);
+  AL(P.adj_off, ab + 1, 0);
+  AL(P.adj, 2 * sb, 0);
+  const size_t C = (size_t)P.cap_cand;
+  AL(P.c_elem, C, 0); AL(P.c_loc, C, 0); AL(P.c_vid, C, 0); AL(P.c_mesh, C, 0);
+  AL(P.c_vseg, C, 0); AL(P.c_sub, C, 0); AL(P.c_pt, C, 0); AL(P.c_key, C, 0);
+  AL(P.c_ncav, C, 0); AL(P.c_nbnd, C, 0); AL(P.c_cav, C * CMAX, 0); AL(P.c_bnd, C * BMAX, 0);
+  AL(P.c_state, C, 0); AL(P.c_final, C, 0); AL(P.c_extra, C, 0); AL(P.c_offT, C, 0);
+  AL(P.c_offV, C, 0); AL(P.c_base, C, 0);
+  AL(P.blk, 2 * G, 0);
+  AL(P.ctrl, 1, 0);
+  AL(P.pts, pb, 0);
+  AL(P.pts2, pb, 0);
+  pts_cap = pb;
+  AL(P.loc, vb, 0xff);
+  AL(P.tbest, tb, 0);
+  CK(cudaMemcpyAsync(P.mi, hmi.data(), sizeof(MeshInfo) * nm, cudaMemcpyHostToDevice, stream));
+  // inputs
+  double2* sxy = nullptr;
+  int2* sseg = nullptr;
+  long long *dpo = nullptr, *dso = nullptr;
+  int* seg_mesh = nullptr;
+  AL(sxy, tot_in, 0);
+  AL(sseg, std::max<long long>(tot_seg, 1), 0);
+  AL(dpo, nm + 1, 0);
+  AL(dso, nm + 1, 0);
+  AL(seg_mesh, std::max<long long>(tot_seg, 1), 0);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(sxy, xy, sizeof(double2) * tot_in, kind, stream));
+  if (tot_seg) CK(cudaMemcpyAsync(sseg, seg, sizeof(int2) * tot_seg, kind, stream));
+  CK(cudaMemcpyAsync(dpo, pt_off, sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(dso, seg_off, sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice, stream));
+  LAUNCH(*this, k_scatter_points, nm, P, sxy, dpo);
+  LAUNCH(*this, k_scatter_segs, nm, P, sseg, dso, seg_mesh);
+  if (tot_seg) {
+    LAUNCH(*this, k_adj_count, G, P, seg_mesh, (int)tot_seg, P.adj_off);
+    LAUNCH(*this, k_iscan_count, G, P.adj_off, (int)(ab + 1), P.blk);
+    LAUNCH(*this, k_iscan_write, G, P.adj_off, (int)(ab + 1), P.blk);
+    int* cursor = nullptr;
+    AL(cursor, ab + 1, 0);
+    CK(cudaMemcpyAsync(cursor, P.adj_off, sizeof(int) * (ab + 1), cudaMemcpyDeviceToDevice, stream));
+    LAUNCH(*this, k_adj_fill, G, P, seg_mesh, (int)tot_seg, cursor);
+    LAUNCH(*this, k_apex, nm, P);
+    CK(cudaStreamSynchronize(stream));
+    release(cursor);
+  }
+  CK(cudaGetLastError());
+  hseg.resize(tot_seg);
+  if (tot_seg)
+    CK(cudaMemcpyAsync(hseg.data(), P.seg, sizeof(int2) * tot_seg, cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  release(sxy);
+  release(sseg);
+  release(dpo);
+  release(dso);
+  release(seg_mesh);
+#undef AL
+  return GDP_OK;
+}
+
+// Parallel insertion rounds of the points in P.pts (Algorithm 1 line 1 uses
+// them for the input points; the fixed-batch test hook for extra points).
+int PoolHost::insert_rounds(int stop_cons, int* rounds_out) {
+  int rounds = 0;
+  if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+  int last = hctrl->n_pts, stall = 0;
+  while (hctrl->n_pts > 0) {
+    ++rounds;
+    if (rounds >= 4000) return GDP_ERR_INTERNAL;
+    CK(cudaMemsetAsync(&P.ctrl->n_ins, 0, 2 * sizeof(unsigned long long), stream));
+    LAUNCH(*this, k_clear_marks, G, P);
+    LAUNCH(*this, k_cdt_locate, G, P, rounds, stop_cons);
+    LAUNCH(*this, k_cdt_pick_count, G, P, rounds);
+    LAUNCH(*this, k_cdt_pick_write, G, P, rounds);
+    LAUNCH(*this, k_grow<1>, G, P);
+    LAUNCH(*this, k_survive, G, P);
+    LAUNCH(*this, k_depend, G, P);
+    LAUNCH(*this, k_offsets, G, P);
+    LAUNCH(*this, k_insert<1>, G, P);
+    LAUNCH(*this, k_link<1>, G, P);
+    LAUNCH(*this, k_cdt_keep_count, G, P);
+    LAUNCH(*this, k_cdt_keep_write, G, P);
+    CK(cudaGetLastError());
+    std::swap(P.pts, P.pts2);
+    if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+    if (std::getenv("GDP_TRACE"))
+      std::fprintf(stderr, "round %d: pending %d cand %d marks-ok %llu inserted %llu\n", rounds,
+                   last, hctrl->n_cand, hctrl->n_surv, hctrl->n_ins);
+    if (hctrl->err) return hctrl->err;
+    if (hctrl->n_pts == last) {
+      if (++stall > 64) return GDP_ERR_INTERNAL;
+    } else {
+      stall = 0;
+    }
+    last = hctrl->n_pts;
+  }
+  if (rounds_out) *rounds_out = rounds;
+  return GDP_OK;
+}
+
+int PoolHost::build_cdt() {
+  CK(cudaEventRecord(ev0, stream));
+  LAUNCH(*this, k_cdt_init, n_mesh, P);
+  CK(cudaGetLastError());
+  std::memset(hctrl, 0, sizeof(Ctrl));
+  hctrl->n_pts = (int)(tot_in + 4 * n_mesh);
+  CK(cudaMemcpyAsync(P.ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
+  int rounds = 0;
+  int st = insert_rounds(0, &rounds);
+  if (st != GDP_OK) return st;
+  stats.cdt_rounds = rounds;
+  // segment recovery
+  int st2;
+  int2* work = nullptr;
+  if ((st2 = alloc(&P.segq, std::max<long long>(tot_seg, 1))) != GDP_OK) return st2;
+  if ((st2 = alloc(&P.segq2, std::max<long long>(tot_seg, 1))) != GDP_OK) return st2;
+  if ((st2 = alloc(&P.reg, (size_t)P.cap_segq * KMAX)) != GDP_OK) return st2;
+  if ((st2 = alloc(&P.reg_n, (size_t)P.cap_segq)) != GDP_OK) return st2;
+  if ((st2 = alloc(&work, (size_t)P.cap_segq * KMAX)) != GDP_OK) return st2;
+  if ((st2 = alloc(&P.segmark, (size_t)P.n_slots)) != GDP_OK) return st2;
+  if (tot_seg) {
+    LAUNCH(*this, k_iota, G, P.segq, (int)tot_seg);
+    if (set_ctrl_field(offsetof(Ctrl, n_segs), (int)tot_seg) != GDP_OK) return GDP_ERR_CUDA;
+    int round = 0, last = (int)tot_seg, stall = 0;
+    for (;;) {
+      LAUNCH(*this, k_seg_find, G, P, round);
+      LAUNCH(*this, k_seg_apply, G, P, round, work);
+      LAUNCH(*this, k_seg_keep_count, G, P);
+      LAUNCH(*this, k_seg_keep_write, G, P);
+      CK(cudaGetLastError());
+      std::swap(P.segq, P.segq2);
+      if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (hctrl->err) return hctrl->err;
+      if (hctrl->n_segs == 0) break;
+      ++round;
+      if (hctrl->n_segs == last) {
+        if (++stall > 64) return GDP_ERR_INTERNAL;
+      } else {
+        stall = 0;
+      }
+      last = hctrl->n_segs;
+      if (round > 60000) return GDP_ERR_INTERNAL;
+    }
+  }
+  // exterior
+  if ((st2 = alloc(&P.ext, (size_t)P.n_slots)) != GDP_OK) return st2;
+  if ((st2 = alloc(&P.remap, (size_t)P.n_slots + 1)) != GDP_OK) return st2;
+  LAUNCH(*this, k_ext_init, G, P);
+  for (int it = 0;; ++it) {
+    if (set_ctrl_field(offsetof(Ctrl, changed), 0) != GDP_OK) return GDP_ERR_CUDA;
+    LAUNCH(*this, k_ext_step, G, P);
+    CK(cudaGetLastError());
+    if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+    if (!hctrl->changed) break;
+    if (it > 100000) return GDP_ERR_INTERNAL;
+  }
+  int4 *T2 = nullptr, *N2 = nullptr;
+  if ((st2 = alloc(&T2, (size_t)P.n_slots, 0xff)) != GDP_OK) return st2;
+  if ((st2 = alloc(&N2, (size_t)P.n_slots, 0xff)) != GDP_OK) return st2;
+  LAUNCH(*this, k_live_count, G, P);
+  LAUNCH(*this, k_live_write, G, P);
+  LAUNCH(*this, k_compact_move, G, P, T2, N2);
+  LAUNCH(*this, k_compact_finish, G, P, T2, N2);
+  LAUNCH(*this, k_compact_counts, G, P);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(ev1, stream));
+  CK(cudaStreamSynchronize(stream));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  stats.cdt_ms = ms;
+  release(T2);
+  release(N2);
+  release(work);
+  release(P.segq);
+  release(P.segq2);
+  release(P.reg);
+  release(P.reg_n);
+  release(P.segmark);
+  release(P.ext);
+  release(P.remap);
+  P.segq = P.segq2 = P.reg = P.reg_n = P.remap = nullptr;
+  P.segmark = nullptr;
+  P.ext = nullptr;
+  if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  // marks and the candidate list start empty
+  if (set_ctrl_field(offsetof(Ctrl, prev_cand), 0) != GDP_OK) return GDP_ERR_CUDA;
+  stats.n_in_pts = tot_in;
+  int worst = GDP_OK;
+  for (auto& M : hmi)
+    if (M.status != S_OK && worst == GDP_OK) worst = M.status;
+  return worst;
+}
+
+int PoolHost::launch_iteration() {
+  LAUNCH(*this, k_scan_count, G, P);
+  LAUNCH(*this, k_scan_write, G, P);
+  LAUNCH(*this, k_grow<0>, G, P);
+  LAUNCH(*this, k_survive, G, P);
+  LAUNCH(*this, k_depend, G, P);
+  LAUNCH(*this, k_offsets, G, P);
+  LAUNCH(*this, k_insert<0>, G, P);
+  LAUNCH(*this, k_link<0>, G, P);
+  return cudaGetLastError() == cudaSuccess ? GDP_OK : GDP_ERR_CUDA;
+}
+
+int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
+  gdp_refine_opts d{};
+  if (o) d = *o;
+  if (!(d.B > 0)) d.B = std::sqrt(2.0);
+  const long long max_iter = d.max_iter > 0 ? d.max_iter : 100000;
+  const int giters = d.graph_iters == 0 ? 8 : d.graph_iters;
+  if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  for (int m = 0; m < n_mesh; ++m) {
+    MeshInfo& M = hmi[m];
+    const double b = B ? B[m] : d.B;
+    if (!(b > 0.7072)) return GDP_ERR_INPUT;
+    M.B2 = b * b;
+    M.active = M.status == S_OK ? 1 : 0;
+    M.steiner = 0;
+    M.cand_cap = d.cand_cap;
+  }
+  if (push_mi() != GDP_OK) return GDP_ERR_CUDA;
+  std::memset(hctrl, 0, sizeof(Ctrl));
+  CK(cudaMemcpyAsync(P.ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
+  CK(cudaEventRecord(ev0, stream));
+  int status = GDP_OK;
+  if (giters > 0 && !prof) {
+    if (!graph || graph_iters != giters) {
+      if (graph) cudaGraphExecDestroy(graph);
+      graph = nullptr;
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaStream_t saved = stream;
+      stream = cs;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      const long long saved_launches = launches;
+      const bool saved_prof = prof;
+      prof = false;
+      for (int k = 0; k < giters; ++k) launch_iteration();
+      prof = saved_prof;
+      launches = saved_launches;
+      cudaGraph_t g;
+      CK(cudaStreamEndCapture(cs, &g));
+      CK(cudaGraphInstantiate(&graph, g, 0));
+      CK(cudaGraphDestroy(g));
+      stream = saved;
+      CK(cudaStreamDestroy(cs));
+      graph_iters = giters;
+    }
+    for (;;) {
+      CK(cudaGraphLaunch(graph, stream));
+      launches += (long long)kernels_per_iter * graph_iters;
+      if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (hctrl->err) { status = hctrl->err; break; }
+      if (hctrl->n_cand == 0) break;
+      if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
+    }
+  } else {
+    for (;;) {
+      if (launch_iteration() != GDP_OK) return GDP_ERR_CUDA;
+      if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (hctrl->err) { status = hctrl->err; break; }
+      if (hctrl->n_cand == 0) break;
+      if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
+    }
+  }
+  CK(cudaEventRecord(ev1, stream));
+  CK(cudaStreamSynchronize(stream));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, ev0, ev1));
+  if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  stats.refine_ms = ms;
+  stats.iterations = (int64_t)hctrl->iters;
+  stats.candidates = (int64_t)hctrl->tot_cand;
+  stats.inserted = (int64_t)hctrl->tot_ins;
+  long long st = 0, nt = 0;
+  for (auto& M : hmi) {
+    st += M.steiner;
+    nt += M.tri_count;
+    if (M.status != S_OK && status == GDP_OK) status = M.status;
+  }
+  stats.n_steiner = st;
+  stats.n_tris = nt;
+  return status;
+}
+
+// Export ids: input points 0..n_in-1, the three enclosing vertices dropped,
+// Steiner points after.  Subsegments are the subsegment-flagged edges.
+int PoolHost::export_mesh(int m, double* xy, int64_t cap_pts, int32_t* tri, int64_t cap_tri,
+                          int32_t* sub, int64_t cap_seg, int64_t* n_pts, int64_t* n_tri,
+                          int64_t* n_seg) {
+  if (m < 0 || m >= n_mesh) return GDP_ERR_INPUT;
+  if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  const MeshInfo& M = hmi[m];
+  std::vector<int4> T(M.tri_count);
+  std::vector<double2> V(M.vert_count);
+  std::vector<int32_t> vs(M.vert_count);
+  if (M.tri_count)
+    CK(cudaMemcpyAsync(T.data(), P.T + M.tri_base, sizeof(int4) * M.tri_count, cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(V.data(), P.V + M.vert_base, sizeof(double2) * M.vert_count, cudaMemcpyDeviceToHost, stream));
+  CK(cudaMemcpyAsync(vs.data(), P.vseg + M.vert_base, sizeof(int32_t) * M.vert_count, cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  const int sv = M.n_in;   // local id of the first auxiliary vertex
+  auto ex = [&](int g) { int l = g - M.vert_base; return l < sv ? l : l - N_AUX; };
+  const long long npts = M.vert_count - N_AUX;
+  long long ntri = 0, nsub = 0;
+  for (const int4& t : T) {
+    if (t.w < 0 || (t.w & INFO_DEAD)) continue;
+    ++ntri;
+    for (int e = 0; e < 3; ++e) {
+      if (!((t.w >> e) & 1)) continue;
+      const int u = (e == 0) ? t.y : (e == 1 ? t.z : t.x);
+      const int v = (e == 0) ? t.z : (e == 1 ? t.x : t.y);
+      (void)v;
+      nsub += 1;
+      (void)u;
+    }
+  }
+  // every interior subsegment is seen from both sides, hull ones once: count properly
+  std::unordered_map<unsigned long long, int> seen;
+  seen.reserve((size_t)nsub * 2 + 16);
+  std::vector<int32_t> subs;
+  subs.reserve((size_t)nsub * 3);
+  // per input vertex: incident segments (for unsplit segments)
+  std::unordered_map<unsigned long long, int> segid;
+  for (int k = 0; k < M.n_seg; ++k) {
+    const int2 s = hseg[M.seg_base + k];
+    const unsigned long long a = (unsigned)std::min(s.x, s.y), b = (unsigned)std::max(s.x, s.y);
+    segid[(a << 32) | b] = M.seg_base + k;
+  }
+  for (const int4& t : T) {
+    if (t.w < 0 || (t.w & INFO_DEAD)) continue;
+    const int vv[3] = {t.x, t.y, t.z};
+    for (int e = 0; e < 3; ++e) {
+      if (!((t.w >> e) & 1)) continue;
+      const int u = vv[(e + 1) % 3], v = vv[(e + 2) % 3];
+      const unsigned long long a = (unsigned)std::min(u, v), b = (unsigned)std::max(u, v);
+      const unsigned long long key = (a << 32) | b;
+      if (seen.count(key)) continue;
+      seen[key] = 1;
+      int s = vs[u - M.vert_base];
+      if (s < 0) s = vs[v - M.vert_base];
+      if (s < 0) {
+        auto it = segid.find(key);
+        s = it == segid.end() ? -1 : it->second;
+      }
+      subs.push_back(ex(u));
+      subs.push_back(ex(v));
+      subs.push_back(s < 0 ? -1 : s - M.seg_base);
+    }
+  }
+  nsub = (long long)subs.size() / 3;
+  if (n_pts) *n_pts = npts;
+  if (n_tri) *n_tri = ntri;
+  if (n_seg) *n_seg = nsub;
+  if ((xy && cap_pts < npts) || (tri && cap_tri < ntri) || (sub && cap_seg < nsub)) return GDP_ERR_INPUT;
+  if (xy) {
+    long long k = 0;
+    for (int l = 0; l < M.vert_count; ++l) {
+      if (l >= sv && l < sv + N_AUX) continue;
+      xy[2 * k] = V[l].x;
+      xy[2 * k + 1] = V[l].y;
+      ++k;
+    }
+  }
+  if (tri) {
+    long long k = 0;
+    for (const int4& t : T) {
+      if (t.w < 0 || (t.w & INFO_DEAD)) continue;
+      tri[3 * k] = ex(t.x);
+      tri[3 * k + 1] = ex(t.y);
+      tri[3 * k + 2] = ex(t.z);
+      ++k;
+    }
+  }
+  if (sub) std::memcpy(sub, subs.data(), sizeof(int32_t) * subs.size());
+  return GDP_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+struct gdp_mesh {
+  PoolHost h;
+};
+struct gdp_batch {
+  PoolHost h;
+};
+
+static int create_common(PoolHost& h, const double* xy, int64_t n, const int32_t* seg, int64_t m,
+                         bool dev, void* s) {
+  long long po[2] = {0, (long long)n}, so[2] = {0, (long long)m};
+  int st = h.setup(xy, po, seg, so, 1, dev, s);
+  if (st != GDP_OK) return st;
+  return h.build_cdt();
+}
+
+extern "C" {
+
+const char* gdp_status_str(int s) {
+  switch (s) {
+    case GDP_OK: return "ok";
+    case GDP_ERR_INPUT: return "invalid input";
+    case GDP_ERR_NOMEM: return "out of memory";
+    case GDP_ERR_ITER_LIMIT: return "iteration limit";
+    case GDP_ERR_WALK_LIMIT: return "walk limit";
+    case GDP_ERR_CUDA: return "CUDA error";
+    case GDP_ERR_INTERNAL: return "internal error";
+    case GDP_ERR_CAPACITY: return "work buffer capacity";
+    default: return "unknown";
+  }
+}
+
+int gdp_mesh_create(const double* xy, int64_t n_pts, const int32_t* seg, int64_t n_seg,
+                    void* stream, gdp_mesh** out) {
+  if (!out || !xy || n_pts < 3 || n_seg < 0 || (n_seg > 0 && !seg)) return GDP_ERR_INPUT;
+  *out = nullptr;
+  gdp_mesh* g = new gdp_mesh();
+  const int st = create_common(g->h, xy, n_pts, seg, n_seg, false, stream);
+  *out = g;
+  return st;
+}
+
+int gdp_mesh_create_device(const double* xy, int64_t n_pts, const int32_t* seg, int64_t n_seg,
+                           void* stream, gdp_mesh** out) {
+  if (!out || !xy || n_pts < 3 || n_seg < 0 || (n_seg > 0 && !seg)) return GDP_ERR_INPUT;
+  *out = nullptr;
+  gdp_mesh* g = new gdp_mesh();
+  const int st = create_common(g->h, xy, n_pts, seg, n_seg, true, stream);
+  *out = g;
+  return st;
+}
+
+int gdp_mesh_refine(gdp_mesh* g, const gdp_refine_opts* opts, gdp_stats* stats) {
+  if (!g) return GDP_ERR_INPUT;
+  const int st = g->h.refine(nullptr, opts);
+  g->h.stats.launches = g->h.launches;
+  if (stats) *stats = g->h.stats;
+  return st;
+}
+
+int gdp_mesh_export(gdp_mesh* g, double* xy, int64_t cap_pts, int32_t* tri, int64_t cap_tri,
+                    int32_t* sub, int64_t cap_seg, int64_t* n_pts, int64_t* n_tri, int64_t* n_seg) {
+  if (!g) return GDP_ERR_INPUT;
+  return g->h.export_mesh(0, xy, cap_pts, tri, cap_tri, sub, cap_seg, n_pts, n_tri, n_seg);
+}
+
+int gdp_mesh_stats(gdp_mesh* g, gdp_stats* s) {
+  if (!g || !s) return GDP_ERR_INPUT;
+  g->h.stats.launches = g->h.launches;
+  *s = g->h.stats;
+  return GDP_OK;
+}
+
+int gdp_mesh_insert_points(gdp_mesh* g, const double* xy, int64_t n) {
+  if (!g || (n > 0 && !xy) || n < 0) return GDP_ERR_INPUT;
+  if (n == 0) return GDP_OK;
+  PoolHost& h = g->h;
+  if (h.pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  MeshInfo& M = h.hmi[0];
+  if (M.vert_count + n > M.vert_cap || M.tri_count + 2 * n > M.tri_cap) return GDP_ERR_NOMEM;
+  if (n > h.pts_cap) {   // grow the pending-point lists
+    h.release(h.P.pts);
+    h.release(h.P.pts2);
+    int s2;
+    if ((s2 = h.alloc(&h.P.pts, n)) != GDP_OK || (s2 = h.alloc(&h.P.pts2, n)) != GDP_OK) return s2;
+    h.pts_cap = n;
+  }
+  const int first = M.vert_base + M.vert_count;
+  CK(cudaMemcpyAsync(h.P.V + first, xy, sizeof(double2) * n, cudaMemcpyHostToDevice, h.stream));
+  std::vector<int> ids(n);
+  for (int64_t k = 0; k < n; ++k) ids[k] = first + (int)k;
+  int* dids = nullptr;
+  int st;
+  if ((st = h.alloc(&dids, n)) != GDP_OK) return st;
+  CK(cudaMemcpyAsync(dids, ids.data(), sizeof(int) * n, cudaMemcpyHostToDevice, h.stream));
+  // a live triangle to start the walks from
+  LAUNCH(h, k_set_loc, h.G, h.P, dids, (int)n, M.tri_base);
+  M.vert_count += (int)n;
+  if (h.push_mi() != GDP_OK) return GDP_ERR_CUDA;
+  std::memset(h.hctrl, 0, sizeof(Ctrl));
+  h.hctrl->n_pts = (int)n;
+  CK(cudaMemcpyAsync(h.P.ctrl, h.hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h.stream));
+  st = h.insert_rounds(1, nullptr);
+  h.release(dids);
+  if (st != GDP_OK) return st;
+  if (h.pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  h.hmi[0].steiner += (int)n;
+  if (h.push_mi() != GDP_OK) return GDP_ERR_CUDA;
+  if (h.set_ctrl_field(offsetof(Ctrl, prev_cand), 0) != GDP_OK) return GDP_ERR_CUDA;
+  return GDP_OK;
+}
+
+int gdp_mesh_split_subsegments(gdp_mesh* g, const double* abxy, int64_t n) {
+  if (!g || n < 0 || (n > 0 && !abxy)) return GDP_ERR_INPUT;
+  PoolHost& h = g->h;
+  std::vector<char> done(n, 0);
+  for (int round = 0; round < 1000; ++round) {
+    if (h.pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+    const MeshInfo& M = h.hmi[0];
+    std::vector<int4> T(M.tri_count);
+    std::vector<double2> V(M.vert_count);
+    CK(cudaMemcpyAsync(T.data(), h.P.T + M.tri_base, sizeof(int4) * M.tri_count, cudaMemcpyDeviceToHost, h.stream));
+    CK(cudaMemcpyAsync(V.data(), h.P.V + M.vert_base, sizeof(double2) * M.vert_count, cudaMemcpyDeviceToHost, h.stream));
+    CK(cudaStreamSynchronize(h.stream));
+    std::vector<int> elems;
+    int left = 0;
+    for (int64_t k = 0; k < n; ++k) {
+      if (done[k]) continue;
+      const double* q = abxy + 4 * k;
+      int found = -1;
+      for (int t = 0; t < M.tri_count && found < 0; ++t) {
+        const int4 T4 = T[t];
+        if (T4.w < 0) continue;
+        const int vv[3] = {T4.x, T4.y, T4.z};
+        for (int e = 0; e < 3; ++e) {
+          if (!((T4.w >> e) & 1)) continue;
+          const double2 a = V[vv[(e + 1) % 3] - M.vert_base], b = V[vv[(e + 2) % 3] - M.vert_base];
+          if ((a.x == q[0] && a.y == q[1] && b.x == q[2] && b.y == q[3]) ||
+              (a.x == q[2] && a.y == q[3] && b.x == q[0] && b.y == q[1])) {
+            found = ((M.tri_base + t) << 2) | e;
+            break;
+          }
+        }
+      }
+      if (found < 0) {
+        if (round == 0) return GDP_ERR_INPUT;
+        done[k] = 1;   // split in an earlier round
+        continue;
+      }
+      ++left;
+      elems.push_back(found);
+    }
+    if (left == 0) break;
+    std::sort(elems.begin(), elems.end());
+    if ((int)elems.size() > h.P.cap_cand) elems.resize(h.P.cap_cand);
+    CK(cudaMemcpyAsync(h.P.c_elem, elems.data(), sizeof(int) * elems.size(), cudaMemcpyHostToDevice, h.stream));
+    LAUNCH(h, k_clear_marks, h.G, h.P);
+    const int nc = (int)elems.size();
+    CK(cudaMemcpyAsync(&h.P.ctrl->n_cand, &nc, sizeof(int), cudaMemcpyHostToDevice, h.stream));
+    CK(cudaMemcpyAsync(&h.P.ctrl->prev_cand, &nc, sizeof(int), cudaMemcpyHostToDevice, h.stream));
+    for (auto& Mi : h.hmi) Mi.active = 1;
+    LAUNCH(h, k_grow<0>, h.G, h.P);
+    LAUNCH(h, k_survive, h.G, h.P);
+    LAUNCH(h, k_depend, h.G, h.P);
+    LAUNCH(h, k_offsets, h.G, h.P);
+    LAUNCH(h, k_insert<0>, h.G, h.P);
+    LAUNCH(h, k_link<0>, h.G, h.P);
+    CK(cudaGetLastError());
+    if (h.sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+    if (h.hctrl->err) return h.hctrl->err;
+  }
+  return GDP_OK;
+}
+
+int gdp_mesh_scan(gdp_mesh* g, double B, int32_t* kind, int32_t* verts, double* pt, uint32_t* meas,
+                  int64_t cap, int64_t* count) {
+  if (!g || !count) return GDP_ERR_INPUT;
+  PoolHost& h = g->h;
+  if (h.pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  const MeshInfo& M = h.hmi[0];
+  const long long c = std::max<long long>(cap, 1);
+  int *dk = nullptr, *dv = nullptr, *dc = nullptr;
+  double2* dp = nullptr;
+  unsigned* dm = nullptr;
+  int st;
+  if ((st = h.alloc(&dk, c)) || (st = h.alloc(&dv, 3 * c)) || (st = h.alloc(&dp, c)) ||
+      (st = h.alloc(&dm, c)) || (st = h.alloc(&dc, 1)))
+    return st;
+  LAUNCH(h, k_scan_report, h.G, h.P, B * B, dk, dv, dp, dm, (int)cap, dc);
+  CK(cudaGetLastError());
+  int cnt = 0;
+  CK(cudaMemcpyAsync(&cnt, dc, sizeof(int), cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  *count = cnt;
+  const long long k = std::min<long long>(cnt, cap);
+  std::vector<int32_t> vv(3 * std::max<long long>(k, 1));
+  if (kind && k) CK(cudaMemcpy(kind, dk, sizeof(int) * k, cudaMemcpyDeviceToHost));
+  if (verts && k) {
+    CK(cudaMemcpy(vv.data(), dv, sizeof(int) * 3 * k, cudaMemcpyDeviceToHost));
+    for (long long i = 0; i < 3 * k; ++i) {
+      const int gv = vv[i];
+      if (gv < 0) { verts[i] = -1; continue; }
+      const int l = gv - M.vert_base;
+      verts[i] = l < M.n_in ? l : l - N_AUX;
+    }
+  }
+  if (pt && k) CK(cudaMemcpy(pt, dp, sizeof(double2) * k, cudaMemcpyDeviceToHost));
+  if (meas && k) CK(cudaMemcpy(meas, dm, sizeof(unsigned) * k, cudaMemcpyDeviceToHost));
+  h.release(dk);
+  h.release(dv);
+  h.release(dp);
+  h.release(dm);
+  h.release(dc);
+  return GDP_OK;
+}
+
+int gdp_mesh_profile(gdp_mesh* g, int enable) {
+  if (!g) return GDP_ERR_INPUT;
+  g->h.prof_flush();
+  g->h.ktimes.clear();
+  g->h.prof = enable != 0;
+  return GDP_OK;
+}
+
+int gdp_mesh_kernel_time(gdp_mesh* g, int32_t i, char* name, int64_t name_cap, double* total_ms,
+                         int64_t* count) {
+  if (!g) return GDP_ERR_INPUT;
+  g->h.prof_flush();
+  if (i < 0 || i >= (int32_t)g->h.ktimes.size()) return GDP_ERR_INPUT;
+  const auto& kv = g->h.ktimes[i];
+  if (name && name_cap > 0) {
+    std::strncpy(name, kv.first.c_str(), (size_t)name_cap - 1);
+    name[name_cap - 1] = 0;
+  }
+  if (total_ms) *total_ms = kv.second.first;
+  if (count) *count = kv.second.second;
+  return GDP_OK;
+}
+
+void gdp_mesh_destroy(gdp_mesh* g) { delete g; }
+
+int gdp_batch_create(const double* xy, const int64_t* pt_off, const int32_t* seg,
+                     const int64_t* seg_off, int32_t n_meshes, void* stream, gdp_batch** out) {
+  if (!out || !xy || !pt_off || !seg_off || n_meshes <= 0) return GDP_ERR_INPUT;
+  *out = nullptr;
+  std::vector<long long> po(n_meshes + 1), so(n_meshes + 1);
+  for (int m = 0; m <= n_meshes; ++m) {
+    po[m] = pt_off[m];
+    so[m] = seg_off[m];
+    if (m && (po[m] - po[m - 1] < 3 || so[m] < so[m - 1])) return GDP_ERR_INPUT;
+  }
+  if (po[0] != 0 || so[0] != 0 || (so[n_meshes] > 0 && !seg)) return GDP_ERR_INPUT;
+  gdp_batch* b = new gdp_batch();
+  int st = b->h.setup(xy, po.data(), seg, so.data(), n_meshes, false, stream);
+  if (st == GDP_OK) st = b->h.build_cdt();
+  *out = b;
+  return st;
+}
+
+int gdp_batch_refine(gdp_batch* b, const double* B, const gdp_refine_opts* opts, gdp_stats* stats) {
+  if (!b) return GDP_ERR_INPUT;
+  const int st = b->h.refine(B, opts);
+  b->h.stats.launches = b->h.launches;
+  if (stats) *stats = b->h.stats;
+  return st;
+}
+
+int gdp_batch_info(gdp_batch* b, int32_t* status, int64_t* n_pts, int64_t* n_tri, int64_t* n_seg,
+                   int64_t* n_steiner) {
+  if (!b) return GDP_ERR_INPUT;
+  if (b->h.pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  for (int m = 0; m < b->h.n_mesh; ++m) {
+    const MeshInfo& M = b->h.hmi[m];
+    if (status) status[m] = M.status;
+    if (n_pts) n_pts[m] = M.vert_count - N_AUX;
+    if (n_tri) n_tri[m] = M.tri_count;
+    if (n_seg) n_seg[m] = -1;
+    if (n_steiner) n_steiner[m] = M.steiner;
+  }
+  return GDP_OK;
+}
+
+int gdp_batch_export(gdp_batch* b, int32_t mesh, double* xy, int64_t cap_pts, int32_t* tri,
+                     int64_t cap_tri, int32_t* sub, int64_t cap_seg, int64_t* n_pts, int64_t* n_tri,
+                     int64_t* n_seg) {
+  if (!b) return GDP_ERR_INPUT;
+  return b->h.export_mesh(mesh, xy, cap_pts, tri, cap_tri, sub, cap_seg, n_pts, n_tri, n_seg);
+}
+
+void gdp_batch_destroy(gdp_batch* b) { delete b; }
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Device-side data layout of the refinement pool (all meshes of a batch share it).
+//
+// Structure of arrays in HBM, one slot per triangle and per vertex:
+//   T[t]   int4  (v0, v1, v2, info)   CCW vertex ids; info = mesh << 4 | cons bits 0..2
+//                                     (edge e = (v[e+1], v[e+2]) is a subsegment) | DEAD bit 3
+//   N[t]   int4  (n0, n1, n2, -)      neighbour across edge e as (tri << 2 | edge), -1 none
+//   mark[t] u64                       cavity priority mark (Sec. 5.2 atomic marks)
+//   newref[4t+e] int32                the new triangle that replaced edge e of t (this iteration)
+//   dirty[t] u8                       triangle changed since its last quality check
+//   V[v]   double2                    vertex coordinates (FP64)
+//   vseg[v] int32                     input segment a Steiner vertex lies on, else -1
+// Per-candidate scratch (one candidate = one splitting point, Algorithm 1 line 5):
+//   c_cav[i*CMAX + j]   cavity triangles;  c_bnd[i*BMAX + j]  cavity boundary edges
+//   as int4 (u, v, outside ref, inside ref | subsegment << 31).
+#pragma once
+#include <cstdint>
+
+namespace gdp {
+
+constexpr int CMAX = 32;            // cavity triangles per splitting point
+constexpr int BMAX = CMAX + 2;      // boundary edges per cavity
+constexpr int KMAX = 512;           // triangles crossed by one segment during recovery
+constexpr int WALK_MAX = 1 << 16;   // point-location steps
+constexpr int BS = 256;             // threads per block
+constexpr int INFO_DEAD = 8;
+constexpr unsigned long long KEY_MID = 1ull << 63;
+
+// candidate states
+enum : uint8_t { C_NONE = 0, C_GROWN = 1, C_LOST = 2, C_SURV = 3, C_FAIL = 4 };
+
+// status codes (mirror gdp_status)
+enum : int32_t { S_OK = 0, S_INPUT = 1, S_NOMEM = 2, S_ITER = 3, S_WALK = 4, S_CUDA = 5,
+                 S_INTERNAL = 6, S_CAPACITY = 7 };
+
+struct MeshInfo {
+  int32_t tri_base, tri_cap, tri_count;
+  int32_t vert_base, vert_cap, vert_count;
+  int32_t n_in;          // input points: vert_base .. vert_base + n_in - 1; 3 enclosing next
+  int32_t seg_base, n_seg;
+  int32_t adj_base;      // CSR of incident segments over the input points
+  int32_t status;
+  int32_t active;        // take part in refinement
+  int32_t first_cand, last_cand;   // this iteration's candidate range
+  int32_t ins_ok;        // this iteration's insertions fit the capacity
+  int32_t pending;       // work left beyond the per-iteration cap
+  int32_t steiner;       // Steiner points inserted by refinement
+  int32_t has_apex;      // some input angle below 60 degrees
+  int32_t cand_cap;      // per-iteration candidate cap (0 = none)
+  int32_t pts_base;      // offset of this mesh's points in the construction list
+  int32_t tmp;           // scratch for per-mesh reductions
+  double B2;
+  double2 lo, hi;        // bounding box of the input points
+};
+
+struct Ctrl {
+  int32_t n_cand;        // candidates this iteration / round
+  int32_t prev_cand;     // candidates whose marks must be cleared
+  int32_t n_raw;         // elements found by the last scan
+  int32_t n_pts;         // CDT: points not yet inserted
+  int32_t n_segs;        // CDT: segments not yet recovered
+  int32_t changed;       // flood fill progress
+  int32_t err;           // first hard error (status code)
+  int32_t round;
+  unsigned long long tot_cand, tot_ins, iters, n_ins, n_surv;
+};
+
+struct Pool {
+  // mesh
+  double2* V;
+  int32_t* vseg;
+  int32_t* vtri;
+  uint8_t* apex;
+  int4* T;
+  int4* N;
+  unsigned long long* mark;
+  int32_t* newref;
+  uint8_t* dirty;
+  uint8_t* flag;
+  MeshInfo* mi;
+  int32_t n_mesh;
+  int32_t n_slots;       // triangle slots spanned by all meshes
+  int32_t n_verts;       // vertex slots spanned by all meshes
+  // input segments (global vertex ids) and per-input-vertex incident segments
+  int2* seg;
+  int32_t* adj_off;
+  int32_t* adj;
+  // candidates
+  int32_t cap_cand;
+  int32_t* c_elem;
+  int32_t* c_loc;
+  int32_t* c_vid;
+  int32_t* c_mesh;
+  int32_t* c_vseg;
+  int2* c_sub;
+  double2* c_pt;
+  unsigned long long* c_key;
+  int32_t* c_ncav;
+  int32_t* c_nbnd;
+  int32_t* c_cav;
+  int4* c_bnd;
+  uint8_t* c_state;
+  uint8_t* c_final;
+  int32_t* c_extra;
+  int32_t* c_offT;
+  int32_t* c_offV;
+  int32_t* c_base;
+  int32_t* blk;          // block partial sums, 2 * G
+  Ctrl* ctrl;
+  // CDT construction
+  int32_t* pts;
+  int32_t* pts2;
+  int32_t* loc;          // per vertex: containing triangle, -1 once inserted
+  unsigned long long* tbest;
+  int32_t* segq;
+  int32_t* segq2;
+  int32_t* reg;          // per active segment: crossed triangles, KMAX each
+  int32_t* reg_n;
+  int32_t cap_segq;
+  unsigned long long* segmark;
+  uint8_t* ext;
+  int32_t* remap;
+};
+
+}  // namespace gdp

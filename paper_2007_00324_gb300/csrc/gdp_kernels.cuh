@@ -1,0 +1,766 @@
+// Kernels of the parallel refinement loop (Algorithm 1) and of the GPU CDT.
+//
+// One refinement iteration (Algorithm 1, lines 3-8) is eight launches, all
+// over the whole pool (every mesh of a batch at once, Rule 4):
+//   k_scan_count / k_scan_write   line 3: changed triangles are checked for
+//                                 encroached subsegments and bad quality and the
+//                                 hits are compacted, in slot order, into the
+//                                 candidate list (block counts + block scans;
+//                                 the compaction is stable so the run is
+//                                 deterministic)
+//   k_grow                        lines 5-7: splitting point and priority,
+//                                 point location by walking, cavity growth by
+//                                 incircle blocked at subsegments, then one
+//                                 64-bit atomicMax mark per cavity triangle
+//   k_survive                     a point survives iff it owns every mark
+//   k_depend                      Delaunay-dependence check on shared cavity
+//                                 boundary edges (Sec. 5.2): the lower priority
+//                                 point of a dependent pair is dropped
+//   k_offsets                     stable prefix sums for new slots / vertex ids
+//   k_insert / k_link             line 8: cavity re-triangulation as a fan,
+//                                 neighbour fix-up, then links between adjacent
+//                                 cavities
+// The same cavity kernels insert the input points of the initial CDT; the
+// CDT is finished by segment recovery (flips) and removal of the exterior.
+#pragma once
+#include <cstdint>
+
+#include "gdp_core.cuh"
+#include "gdp_pred.cuh"
+
+namespace gdp {
+
+// ---------------------------------------------------------------- small helpers
+__device__ __forceinline__ int comp(const int4& a, int i) {
+  return i == 0 ? a.x : (i == 1 ? a.y : a.z);
+}
+__device__ __forceinline__ int* comp_ptr(int4* p, int i) { return reinterpret_cast<int*>(p) + i; }
+__device__ __forceinline__ int mod3(int i) { return i >= 3 ? i - 3 : i; }
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+__device__ __forceinline__ void set_err(Ctrl* C, int code) { atomicCAS(&C->err, 0, code); }
+
+__device__ __forceinline__ int block_sum(int v, int* sm) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int r = l < nw ? sm[l] : 0;
+    for (int o = 16; o; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (l == 0) sm[32] = r;
+  }
+  __syncthreads();
+  int r = sm[32];
+  __syncthreads();
+  return r;
+}
+
+// exclusive scan over the block; total receives the block sum
+__device__ __forceinline__ int block_excl_scan(int v, int* sm, int& total) {
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (l >= o) x += y;
+  }
+  __syncthreads();
+  if (l == 31) sm[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = l < nw ? sm[l] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (l >= o) s += y;
+    }
+    if (l < nw) sm[l] = s;
+  }
+  __syncthreads();
+  int base = w ? sm[w - 1] : 0;
+  total = sm[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// sum of blk[0..b), computed by the whole block
+__device__ __forceinline__ int block_prefix(const int* blk, int b, int* sm) {
+  int s = 0;
+  for (int k = threadIdx.x; k < b; k += blockDim.x) s += blk[k];
+  return block_sum(s, sm);
+}
+
+struct Chunk {
+  int b0, b1;
+};
+// contiguous index range of this block (stable compactions use fixed chunks)
+__device__ __forceinline__ Chunk chunk_of(int n) {
+  int c = (n + gridDim.x - 1) / gridDim.x;
+  int b0 = min(n, (int)blockIdx.x * c);
+  return {b0, min(n, b0 + c)};
+}
+
+// ---------------------------------------------------------------- mesh queries
+// Auxiliary vertices of every mesh, right after its input points: three
+// enclosing vertices, then four frame vertices around the bounding box.  The
+// frame is inserted first, so every input point lies inside the triangulated
+// region from then on and points never queue up outside a growing hull.  All
+// seven lie outside the segment-bounded domain and are removed with the
+// exterior, so they do not change the CDT.
+constexpr int N_AUX = 7;
+__device__ __forceinline__ bool is_aux(const MeshInfo& M, int v) {
+  const int s = M.vert_base + M.n_in;
+  return v >= s && v < s + N_AUX;
+}
+
+// insertion priority of a construction point: frame vertices first, then a hash
+__device__ __forceinline__ uint32_t insert_prio(const MeshInfo& M, int v) {
+  if (is_aux(M, v)) return 0xffffffffu;
+  return hash32((uint32_t)(v - M.vert_base)) | 1u;
+}
+
+__device__ __forceinline__ bool is_input(const MeshInfo& M, int v) {
+  return v >= M.vert_base && v < M.vert_base + M.n_in;
+}
+
+// the input segment a subsegment (u,v) belongs to
+__device__ int seg_of_sub(const Pool& P, const MeshInfo& M, int u, int v) {
+  int s = P.vseg[u];
+  if (s >= 0) return s;
+  s = P.vseg[v];
+  if (s >= 0) return s;
+  if (!is_input(M, u)) return -1;
+  const int lu = u - M.vert_base;
+  for (int k = P.adj_off[M.adj_base + lu]; k < P.adj_off[M.adj_base + lu + 1]; ++k) {
+    const int g = P.adj[k];
+    const int2 e = P.seg[g];
+    if ((e.x == u && e.y == v) || (e.x == v && e.y == u)) return g;
+  }
+  return -1;
+}
+
+// two distinct input segments sharing an endpoint at less than 60 degrees
+__device__ bool small_pair(const Pool& P, int s1, int s2) {
+  if (s1 == s2 || s1 < 0 || s2 < 0) return false;
+  const int2 a = P.seg[s1], b = P.seg[s2];
+  int o, p, q;
+  if (a.x == b.x) { o = a.x; p = a.y; q = b.y; }
+  else if (a.x == b.y) { o = a.x; p = a.y; q = b.x; }
+  else if (a.y == b.x) { o = a.y; p = a.x; q = b.y; }
+  else if (a.y == b.y) { o = a.y; p = a.x; q = b.x; }
+  else return false;
+  const double2 O = P.V[o], A = P.V[p], B = P.V[q];
+  const double ux = A.x - O.x, uy = A.y - O.y, wx = B.x - O.x, wy = B.y - O.y;
+  const double dot = ux * wx + uy * wy;
+  const double nn = sqrt(ux * ux + uy * uy) * sqrt(wx * wx + wy * wy);
+  return 2.0 * dot > nn;
+}
+
+__device__ int segs_of(const Pool& P, const MeshInfo& M, int v, int* out) {
+  if (is_input(M, v)) {
+    const int l = v - M.vert_base;
+    int n = 0;
+    for (int k = P.adj_off[M.adj_base + l]; k < P.adj_off[M.adj_base + l + 1] && n < 16; ++k)
+      out[n++] = P.adj[k];
+    return n;
+  }
+  const int s = P.vseg[v];
+  if (s >= 0) { out[0] = s; return 1; }
+  return 0;
+}
+
+// bad triangles whose shortest edge joins two segments meeting at a small
+// input angle are accepted in the output (Sec. 4.1)
+__device__ bool exempt(const Pool& P, const MeshInfo& M, const int4& T4) {
+  if (!M.has_apex) return false;
+  double best = -1.0;
+  int be = 0;
+  for (int e = 0; e < 3; ++e) {
+    const double2 a = P.V[comp(T4, mod3(e + 1))], b = P.V[comp(T4, mod3(e + 2))];
+    const double dx = b.x - a.x, dy = b.y - a.y;
+    const double l = dx * dx + dy * dy;
+    if (best < 0 || l < best) { best = l; be = e; }
+  }
+  int su[16], sw[16];
+  const int nu = segs_of(P, M, comp(T4, mod3(be + 1)), su);
+  const int nw = segs_of(P, M, comp(T4, mod3(be + 2)), sw);
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < nw; ++j)
+      if (small_pair(P, su[i], sw[j])) return true;
+  return false;
+}
+
+// splitting point of subsegment (u,v): the midpoint, or -- when exactly one
+// endpoint is an input vertex with a small input angle -- the point at the
+// power-of-two distance from it nearest to half the length (concentric shells)
+__device__ double2 split_point(const Pool& P, const MeshInfo& M, int u, int v) {
+  const bool au = is_input(M, u) && P.apex[u];
+  const bool av = is_input(M, v) && P.apex[v];
+  if (au == av) return midpoint(P.V[u], P.V[v]);
+  const int o = au ? u : v, q = au ? v : u;
+  const double2 O = P.V[o], Q = P.V[q];
+  const double dx = Q.x - O.x, dy = Q.y - O.y;
+  const double L = sqrt(dx * dx + dy * dy);
+  int e;
+  const double m = frexp(0.5 * L, &e);
+  const double d = (m * m < 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+  const double r = d / L;
+  return make_double2(O.x + dx * r, O.y + dy * r);
+}
+
+// ---------------------------------------------------------------- scan (line 3)
+// 0: nothing; 1..3: encroached subsegment on edge 0..2 (longest); 4: bad triangle
+__device__ int eval_tri(const Pool& P, int t) {
+  const int4 T4 = P.T[t];
+  if (T4.w < 0 || (T4.w & INFO_DEAD)) return 0;
+  const MeshInfo& M = P.mi[T4.w >> 4];
+  if (!M.active) return 0;
+  const int cons = T4.w & 7;
+  if (cons) {
+    int best = -1;
+    double bl = -1.0;
+    for (int e = 0; e < 3; ++e) {
+      if (!((cons >> e) & 1)) continue;
+      const double2 u = P.V[comp(T4, mod3(e + 1))], v = P.V[comp(T4, mod3(e + 2))];
+      if (dot_sign(u, v, P.V[comp(T4, e)]) < 0) {
+        const double l = seg_measure(u, v);
+        if (l > bl) { bl = l; best = e; }
+      }
+    }
+    if (best >= 0) return 1 + best;
+  }
+  const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
+  if (is_bad(tt, M.B2) && !exempt(P, M, T4)) return 4;
+  return 0;
+}
+
+__global__ void __launch_bounds__(BS) k_clear_marks(Pool P) {
+  const int prev = P.ctrl->prev_cand;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int i = gt; i < prev; i += gs) {
+    const int n = P.c_ncav[i];
+    for (int j = 0; j < n; ++j) P.mark[P.c_cav[(size_t)i * CMAX + j]] = 0ull;
+  }
+}
+
+__global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
+  __shared__ int sm[33];
+  const int prev = P.ctrl->prev_cand;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int i = gt; i < prev; i += gs) {
+    const int n = P.c_ncav[i];
+    for (int j = 0; j < n; ++j) P.mark[P.c_cav[(size_t)i * CMAX + j]] = 0ull;
+  }
+  for (int m = gt; m < P.n_mesh; m += gs) {
+    P.mi[m].first_cand = -1;
+    P.mi[m].last_cand = -1;
+    P.mi[m].pending = 0;
+  }
+  const Chunk ch = chunk_of(P.n_slots);
+  int cnt = 0;
+  for (int base = ch.b0; base < ch.b1; base += BS) {
+    const int t = base + threadIdx.x;
+    if (t < ch.b1) {
+      int code = 0;
+      if (P.dirty[t]) {
+        P.dirty[t] = 0;
+        code = eval_tri(P, t);
+      }
+      P.flag[t] = (uint8_t)code;
+      cnt += code != 0;
+    }
+  }
+  cnt = block_sum(cnt, sm);
+  if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
+}
+
+__global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
+  __shared__ int sm[33];
+  const Chunk ch = chunk_of(P.n_slots);
+  int off = block_prefix(P.blk, blockIdx.x, sm);
+  const int cap = P.cap_cand;
+  for (int base = ch.b0; base < ch.b1; base += BS) {
+    const int t = base + threadIdx.x;
+    const int code = t < ch.b1 ? P.flag[t] : 0;
+    int tot;
+    const int r = block_excl_scan(code != 0, sm, tot);
+    if (code) {
+      const int rank = off + r;
+      if (rank < cap) {
+        P.c_elem[rank] = (t << 2) | (code == 4 ? 3 : code - 1);
+      } else {
+        P.dirty[t] = 1;   // over the per-iteration capacity: retried next iteration
+        P.mi[P.T[t].w >> 4].pending = 1;
+      }
+    }
+    off += tot;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const int n = min(off, cap);
+    Ctrl* C = P.ctrl;
+    C->n_raw = off;
+    C->n_cand = n;
+    C->prev_cand = n;
+    C->n_ins = 0;
+    if (n > 0) {
+      C->tot_cand += n;
+      C->iters += 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- locate + grow (lines 5-7)
+// Visibility walk from t towards p.  Returns the triangle containing p
+// (closed), -1 when the next step would cross a subsegment (stop_cons) or the
+// hull -- (bt, be) is that edge -- or -2 at the step limit.  In a CDT every
+// step across a locally Delaunay edge lowers the power of p with respect to
+// the current circumcircle, so the walk cannot cycle.
+__device__ int walk(const Pool& P, int t, double2 p, bool stop_cons, int& bt, int& be) {
+  int from = -1;
+  for (int s = 0; s < WALK_MAX; ++s) {
+    const int4 T4 = P.T[t];
+    const int4 N4 = P.N[t];
+    int next = -1, nfrom = -1, blk = -1;
+    for (int e = 0; e < 3 && next < 0; ++e) {
+      const int nb = comp(N4, e);
+      if (nb >= 0 && (nb >> 2) == from) continue;   // p is on this side of the entry edge
+      if (orient(P.V[comp(T4, mod3(e + 1))], P.V[comp(T4, mod3(e + 2))], p) < 0) {
+        if ((stop_cons && ((T4.w >> e) & 1)) || nb < 0) {
+          if (blk < 0) blk = e;
+        } else {
+          next = nb >> 2;
+          nfrom = t;
+        }
+      }
+    }
+    if (next >= 0) {
+      from = nfrom;
+      t = next;
+      continue;
+    }
+    if (blk >= 0) {
+      bt = t;
+      be = blk;
+      return -1;
+    }
+    return t;
+  }
+  return -2;
+}
+
+enum { G_OK = 0, G_OVF = 1, G_CONV = 2 };
+
+// Bowyer-Watson cavity of p from t0 (and t1): breadth-first over triangles
+// whose circumcircle holds p (exact incircle with simulation of simplicity),
+// never across a subsegment (visibility).  Boundary edges are recorded as
+// (u, v, outside ref, inside ref | subsegment bit).  With conv, meeting a
+// subsegment that p encroaches stops the growth (G_CONV) so that the
+// subsegment is split instead (Sec. 4.2: such a circumcentre is redundant).
+__device__ int grow(const Pool& P, int i, double2 p, int t0, int t1, bool conv, int& nc, int& nb,
+                    int& ct, int& ce) {
+  int* cav = P.c_cav + (size_t)i * CMAX;
+  int4* bnd = P.c_bnd + (size_t)i * BMAX;
+  int k = 0, b = 0;
+  cav[k++] = t0;
+  if (t1 >= 0) cav[k++] = t1;
+  for (int q = 0; q < k; ++q) {
+    const int t = cav[q];
+    const int4 T4 = P.T[t];
+    const int4 N4 = P.N[t];
+    for (int e = 0; e < 3; ++e) {
+      const int ref = comp(N4, e);
+      const int cons = (T4.w >> e) & 1;
+      if (ref >= 0) {
+        const int tn = ref >> 2;
+        bool in = false;
+        for (int r = 0; r < k; ++r)
+          if (cav[r] == tn) { in = true; break; }
+        if (in) continue;
+      }
+      const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
+      bool inside = false;
+      if (!cons && ref >= 0) {
+        const int4 Tn = P.T[ref >> 2];
+        inside = incircle(P.V[Tn.x], P.V[Tn.y], P.V[Tn.z], p) > 0;
+      } else if (cons && conv && dot_sign(P.V[u], P.V[v], p) < 0) {
+        ct = t;
+        ce = e;
+        return G_CONV;
+      }
+      if (inside) {
+        if (k == CMAX) return G_OVF;
+        cav[k++] = ref >> 2;
+      } else {
+        if (b == BMAX) return G_OVF;
+        bnd[b++] = make_int4(u, v, ref, (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
+      }
+    }
+  }
+  nc = k;
+  nb = b;
+  return G_OK;
+}
+
+__device__ __forceinline__ bool is_split_edge(const int4& rec, int2 sub) {
+  return sub.x >= 0 && rec.z < 0 &&
+         ((rec.x == sub.x && rec.y == sub.y) || (rec.x == sub.y && rec.y == sub.x));
+}
+
+// MODE 0: refinement candidates (element = triangle << 2 | edge, 3 = the triangle);
+// MODE 1: given points (element = vertex id, c_loc = located triangle).
+template <int MODE>
+__global__ void __launch_bounds__(BS) k_grow(Pool P) {
+  const int n = P.ctrl->n_cand;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int i = gt; i < n; i += gs) {
+    P.c_ncav[i] = 0;
+    P.c_nbnd[i] = 0;
+    P.c_state[i] = C_FAIL;
+    P.c_final[i] = 0;
+    const int elem = P.c_elem[i];
+    double2 p;
+    unsigned long long key;
+    int t0, t1 = -1, m, vid = -1;
+    bool conv = false;
+    int2 sub = make_int2(-1, -1);
+    if (MODE == 1) {
+      vid = elem;
+      t0 = P.c_loc[i];
+      m = P.T[t0].w >> 4;
+      p = P.V[vid];
+      key = ((unsigned long long)insert_prio(P.mi[m], vid) << 32) | (unsigned)i;
+    } else {
+      const int t = elem >> 2, k = elem & 3;
+      const int4 T4 = P.T[t];
+      m = T4.w >> 4;
+      const MeshInfo& M = P.mi[m];
+      if (k == 3) {
+        const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
+        p = circumcenter(tt);
+        key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
+        int bt = -1, be = -1;
+        const int r = walk(P, t, p, true, bt, be);
+        if (r == -2) {
+          P.c_mesh[i] = m;
+          set_err(P.ctrl, S_WALK);
+          continue;
+        }
+        if (r == -1) {
+          // the walk meets a subsegment: split it instead (Sec. 4.3)
+          const int4 B4 = P.T[bt];
+          const int u = comp(B4, mod3(be + 1)), v = comp(B4, mod3(be + 2));
+          p = split_point(P, M, u, v);
+          key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+                (unsigned)i;
+          t0 = bt;
+          const int nr = comp(P.N[bt], be);
+          t1 = nr >= 0 ? nr >> 2 : -1;
+          sub = make_int2(u, v);
+        } else {
+          t0 = r;
+          conv = true;
+        }
+      } else {
+        const int u = comp(T4, mod3(k + 1)), v = comp(T4, mod3(k + 2));
+        p = split_point(P, M, u, v);
+        key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+              (unsigned)i;
+        t0 = t;
+        const int nr = comp(P.N[t], k);
+        t1 = nr >= 0 ? nr >> 2 : -1;
+        sub = make_int2(u, v);
+      }
+    }
+    P.c_mesh[i] = m;
+    int nc = 0, nb = 0, ct = -1, ce = -1;
+    int g = grow(P, i, p, t0, t1, conv, nc, nb, ct, ce);
+    if (g == G_CONV) {
+      const int4 B4 = P.T[ct];
+      const int u = comp(B4, mod3(ce + 1)), v = comp(B4, mod3(ce + 2));
+      p = split_point(P, P.mi[m], u, v);
+      key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+            (unsigned)i;
+      sub = make_int2(u, v);
+      const int nr = comp(P.N[ct], ce);
+      g = grow(P, i, p, ct, nr >= 0 ? nr >> 2 : -1, false, nc, nb, ct, ce);
+    }
+    if (g != G_OK) continue;   // buffer overflow: retried in a later iteration (Rule 3)
+    const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+    bool ok = true;
+    for (int r = 0; r < nb && ok; ++r) {
+      const int4 rec = bnd[r];
+      if (is_split_edge(rec, sub)) continue;
+      if (orient(P.V[rec.x], P.V[rec.y], p) <= 0) ok = false;
+    }
+    if (!ok) continue;
+    const int* cav = P.c_cav + (size_t)i * CMAX;
+    for (int j = 0; j < nc; ++j) atomicMax(&P.mark[cav[j]], key);
+    P.c_pt[i] = p;
+    P.c_key[i] = key;
+    P.c_ncav[i] = nc;
+    P.c_nbnd[i] = nb;
+    P.c_sub[i] = sub;
+    P.c_vid[i] = vid;
+    P.c_vseg[i] = (sub.x >= 0) ? seg_of_sub(P, P.mi[m], sub.x, sub.y) : -1;
+    P.c_state[i] = C_GROWN;
+  }
+}
+
+// a point survives iff it still owns the mark of every cavity triangle
+__global__ void __launch_bounds__(BS) k_survive(Pool P) {
+  const int n = P.ctrl->n_cand;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int i = gt; i < n; i += gs) {
+    const int m = P.c_mesh[i];
+    if (i == 0 || P.c_mesh[i - 1] != m) P.mi[m].first_cand = i;
+    if (i == n - 1 || P.c_mesh[i + 1] != m) P.mi[m].last_cand = i;
+    if (P.c_state[i] != C_GROWN) continue;
+    const unsigned long long key = P.c_key[i];
+    const int* cav = P.c_cav + (size_t)i * CMAX;
+    const int nc = P.c_ncav[i];
+    bool own = true;
+    for (int j = 0; j < nc && own; ++j) own = P.mark[cav[j]] == key;
+    P.c_state[i] = own ? C_SURV : C_LOST;
+    if (own) atomicAdd(&P.ctrl->n_surv, 1ull);
+  }
+}
+
+// Delaunay dependence (Sec. 5.2): survivors p, q whose cavities meet at a
+// non-subsegment edge uv would need the edge pq if q lies inside the circle of
+// p's new triangle (p,u,v); the lower priority one is dropped.  The test is
+// symmetric (same four points), so both sides agree.
+__global__ void __launch_bounds__(BS) k_depend(Pool P) {
+  __shared__ int sm[33];
+  const int n = P.ctrl->n_cand;
+  const Chunk ch = chunk_of(n);
+  int se = 0, sv = 0;
+  for (int base = ch.b0; base < ch.b1; base += BS) {
+    const int i = base + threadIdx.x;
+    if (i >= ch.b1) continue;
+    bool fin = false;
+    int extra = 0;
+    if (P.c_state[i] == C_SURV) {
+      fin = true;
+      const unsigned long long key = P.c_key[i];
+      const double2 p = P.c_pt[i];
+      const int nb = P.c_nbnd[i];
+      const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+      const int2 sub = P.c_sub[i];
+      int eff = 0;
+      for (int r = 0; r < nb; ++r) {
+        const int4 rec = bnd[r];
+        if (!is_split_edge(rec, sub)) ++eff;
+        if (rec.w < 0 || rec.z < 0 || !fin) continue;
+        const unsigned long long mo = P.mark[rec.z >> 2];
+        if (!mo) continue;
+        const int j = (int)(unsigned)(mo & 0xffffffffull);
+        if (j == i || j >= n || P.c_state[j] != C_SURV) continue;
+        if (incircle(p, P.V[rec.x], P.V[rec.y], P.c_pt[j]) > 0 && key < P.c_key[j]) fin = false;
+      }
+      if (fin) extra = eff - P.c_ncav[i];
+    }
+    P.c_final[i] = fin;
+    P.c_extra[i] = extra;
+    se += extra;
+    sv += (fin && P.c_vid[i] < 0) ? 1 : 0;
+  }
+  se = block_sum(se, sm);
+  sv = block_sum(sv, sm);
+  if (threadIdx.x == 0) {
+    P.blk[blockIdx.x] = se;
+    P.blk[gridDim.x + blockIdx.x] = sv;
+  }
+}
+
+__global__ void __launch_bounds__(BS) k_offsets(Pool P) {
+  __shared__ int sm[33];
+  const int n = P.ctrl->n_cand;
+  const Chunk ch = chunk_of(n);
+  int offE = block_prefix(P.blk, blockIdx.x, sm);
+  int offV = block_prefix(P.blk + gridDim.x, blockIdx.x, sm);
+  for (int base = ch.b0; base < ch.b1; base += BS) {
+    const int i = base + threadIdx.x;
+    const int e = i < ch.b1 ? P.c_extra[i] : 0;
+    const int v = (i < ch.b1 && P.c_final[i] && P.c_vid[i] < 0) ? 1 : 0;
+    int tE, tV;
+    const int rE = block_excl_scan(e, sm, tE);
+    const int rV = block_excl_scan(v, sm, tV);
+    if (i < ch.b1) {
+      P.c_offT[i] = offE + rE;
+      P.c_offV[i] = offV + rV;
+    }
+    offE += tE;
+    offV += tV;
+  }
+}
+
+__device__ __forceinline__ void mesh_totals(const Pool& P, int f, int l, int& totE, int& totV) {
+  const int nv_l = (P.c_final[l] && P.c_vid[l] < 0) ? 1 : 0;
+  totE = P.c_offT[l] + P.c_extra[l] - P.c_offT[f];
+  totV = P.c_offV[l] + nv_l - P.c_offV[f];
+}
+
+__device__ __forceinline__ bool replaced(const Pool& P, int ref, int n) {
+  const unsigned long long mo = P.mark[ref >> 2];
+  if (!mo) return false;
+  const int j = (int)(unsigned)(mo & 0xffffffffull);
+  return j < n && P.c_final[j];
+}
+
+// Re-triangulate every surviving cavity as the fan from its point
+// (Sec. 5.2 insertion + housekeeping).  Cavity slots are reused first, extra
+// slots come from the mesh's bump region at stable prefix-sum offsets.
+template <int MODE>
+__global__ void __launch_bounds__(BS) k_insert(Pool P) {
+  const int n = P.ctrl->n_cand;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int i = gt; i < n; i += gs) {
+    const int m = P.c_mesh[i];
+    const MeshInfo& M = P.mi[m];
+    const int f = M.first_cand, l = M.last_cand;
+    int totE, totV;
+    mesh_totals(P, f, l, totE, totV);
+    const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
+    if (i == f) {
+      P.mi[m].ins_ok = ok ? 1 : 0;
+      if (!ok) P.mi[m].status = S_NOMEM;
+    }
+    // the element is re-checked whatever happens: it may be untouched when its
+    // splitting point moved to a subsegment, or when the point was not inserted
+    if (MODE == 0) P.dirty[P.c_elem[i] >> 2] = 1;
+    if (!P.c_final[i] || !ok) continue;
+    const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
+    const int vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
+    P.c_base[i] = base;
+    const double2 p = P.c_pt[i];
+    P.V[vid] = p;
+    P.vseg[vid] = P.c_vseg[i];
+    if (MODE == 1) P.loc[vid] = -1;
+    const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+    const int* cav = P.c_cav + (size_t)i * CMAX;
+    const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
+    const int2 sub = P.c_sub[i];
+    const bool is_mid = sub.x >= 0;
+    int j = 0;
+    for (int r = 0; r < nb; ++r) {
+      const int4 rec = bnd[r];
+      if (is_split_edge(rec, sub)) continue;
+      const int s = j < nc ? cav[j] : base + (j - nc);
+      const int u = rec.x, v = rec.y;
+      int cb = rec.w < 0 ? 1 : 0;
+      if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
+      if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
+      int n1 = -1, n2 = -1, jj = 0;
+      for (int r2 = 0; r2 < nb; ++r2) {
+        const int4 q = bnd[r2];
+        if (is_split_edge(q, sub)) continue;
+        const int s2 = jj < nc ? cav[jj] : base + (jj - nc);
+        if (q.x == v) n1 = (s2 << 2) | 2;
+        if (q.y == u) n2 = (s2 << 2) | 1;
+        ++jj;
+      }
+      int n0 = rec.z;
+      if (n0 >= 0) {
+        if (replaced(P, n0, n)) n0 = -1;   // linked by k_link
+        else *comp_ptr(&P.N[n0 >> 2], n0 & 3) = s << 2;
+      }
+      P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
+      P.N[s] = make_int4(n0, n1, n2, 0);
+      P.newref[rec.w & 0x7fffffff] = s << 2;
+      P.dirty[s] = 1;
+      P.vtri[u] = s;
+      P.vtri[v] = s;
+      P.vtri[vid] = s;
+      ++j;
+    }
+  }
+}
+
+// links between adjacent cavities, then per-mesh counters
+template <int MODE>
+__global__ void __launch_bounds__(BS) k_link(Pool P) {
+  const int n = P.ctrl->n_cand;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  int ins = 0;
+  for (int i = gt; i < n; i += gs) {
+    const int m = P.c_mesh[i];
+    const MeshInfo& M = P.mi[m];
+    const bool ok = M.ins_ok;
+    if (P.c_final[i] && ok) {
+      ++ins;
+      const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+      const int* cav = P.c_cav + (size_t)i * CMAX;
+      const int nc = P.c_ncav[i], nb = P.c_nbnd[i], base = P.c_base[i];
+      const int2 sub = P.c_sub[i];
+      int j = 0;
+      for (int r = 0; r < nb; ++r) {
+        const int4 rec = bnd[r];
+        if (is_split_edge(rec, sub)) continue;
+        if (rec.z >= 0 && replaced(P, rec.z, n)) {
+          const int s = j < nc ? cav[j] : base + (j - nc);
+          P.N[s].x = P.newref[rec.z];
+        }
+        ++j;
+      }
+    }
+    if (i == M.last_cand && ok) {
+      int totE, totV;
+      mesh_totals(P, M.first_cand, i, totE, totV);
+      P.mi[m].tri_count = M.tri_count + totE;
+      P.mi[m].vert_count = M.vert_count + totV;
+      if (MODE == 0) P.mi[m].steiner = M.steiner + totV;
+    }
+  }
+  for (int o = 16; o; o >>= 1) ins += __shfl_xor_sync(0xffffffffu, ins, o);
+  if ((threadIdx.x & 31) == 0 && ins) {
+    atomicAdd(&P.ctrl->n_ins, (unsigned long long)ins);
+    atomicAdd(&P.ctrl->tot_ins, (unsigned long long)ins);
+  }
+}
+
+// ---------------------------------------------------------------- scan report (test hook)
+// Every live triangle: its bad flag; every subsegment edge: encroachment by
+// this triangle's apex.  Output in slot order.
+__global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int* kind, int* verts,
+                                                    double2* pt, unsigned* meas, int cap,
+                                                    int* count) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int t = gt; t < P.n_slots; t += gs) {
+    const int4 T4 = P.T[t];
+    if (T4.w < 0 || (T4.w & INFO_DEAD)) continue;
+    const MeshInfo& M = P.mi[T4.w >> 4];
+    const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
+    if (is_bad(tt, B2)) {
+      const int r = atomicAdd(count, 1);
+      if (r < cap) {
+        kind[r] = 0;
+        verts[3 * r] = T4.x; verts[3 * r + 1] = T4.y; verts[3 * r + 2] = T4.z;
+        pt[r] = circumcenter(tt);
+        meas[r] = measure_bits(fabs(tt.cr));
+      }
+    }
+    for (int e = 0; e < 3; ++e) {
+      if (!((T4.w >> e) & 1)) continue;
+      const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
+      if (dot_sign(P.V[u], P.V[v], P.V[comp(T4, e)]) < 0) {
+        const int r = atomicAdd(count, 1);
+        if (r < cap) {
+          kind[r] = 1;
+          verts[3 * r] = u; verts[3 * r + 1] = v; verts[3 * r + 2] = -1;
+          pt[r] = split_point(P, M, u, v);
+          meas[r] = measure_bits(seg_measure(P.V[u], P.V[v]));
+        }
+      }
+    }
+  }
+}
+
+}  // namespace gdp

@@ -1,0 +1,96 @@
+"""Refinement (Algorithm 1): the refined mesh passes every invariant, and its
+Steiner count is within 10% of the sequential oracle's (the paper's own
+counts against Triangle differ by -3.7% .. +9.8%, Table 1)."""
+import math
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import SQ2, assert_valid, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def refine_both(oracle, gdp, p, B, **kw):
+    g = gdp.Mesh(p.xy, p.seg)
+    stats = g.refine(B, **kw)
+    xy, tri, sub = g.export()
+    o = oracle.Mesh(p.xy, p.seg)
+    assert o.refine(B) == 0
+    return g, stats, (xy, tri, sub), o.n_steiner
+
+
+@pytest.mark.parametrize("B", [SQ2, 1.5])
+def test_tiny_refine(oracle, B):
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.tiny()
+    g, stats, (xy, tri, sub), n_ref = refine_both(oracle, gdp, p, B)
+    assert_valid(oracle.check(xy, tri, sub, p.seg, p.n, B=B, brute=True), brute=True)
+    assert np.array_equal(xy[:p.n], p.xy)
+    assert len(xy) == p.n + stats["n_steiner"]
+    assert abs(stats["n_steiner"] - n_ref) <= 0.10 * n_ref, (stats["n_steiner"], n_ref)
+
+
+def test_refine_without_graph_matches_graph(oracle):
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.square_pslg(5000, 100, 7)
+    a = gdp.Mesh(p.xy, p.seg)
+    a.refine(SQ2, graph_iters=-1)
+    b = gdp.Mesh(p.xy, p.seg)
+    b.refine(SQ2, graph_iters=4)
+    xa, ta, _ = a.export()
+    xb, tb, _ = b.export()
+    assert np.array_equal(xa, xb)
+    assert oracle.triangle_set(xa, ta) == oracle.triangle_set(xb, tb)
+
+
+def test_deterministic(oracle):
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.square_pslg(20000, 300, 8)
+    outs = []
+    for _ in range(2):
+        g = gdp.Mesh(p.xy, p.seg)
+        g.refine(SQ2)
+        outs.append(g.export())
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("B", [SQ2, 1.5])
+def test_mid_refine(oracle, B):
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.mid()
+    g, stats, (xy, tri, sub), n_ref = refine_both(oracle, gdp, p, B)
+    assert_valid(oracle.check(xy, tri, sub, p.seg, p.n, B=B))
+    assert abs(stats["n_steiner"] - n_ref) <= 0.10 * n_ref, (stats["n_steiner"], n_ref)
+
+
+def test_small_input_angles_terminate(oracle):
+    gdp = need_gpu()
+    sq = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], float)
+    apex = np.array([[0.5, 0.5]])
+    ends = np.array([[0.5 + 0.3 * math.cos(math.radians(a)), 0.5 + 0.3 * math.sin(math.radians(a))]
+                     for a in (0, 10, 20)])
+    xy = np.concatenate([sq, apex, ends])
+    seg = np.array([[0, 1], [1, 2], [2, 3], [3, 0], [4, 5], [4, 6], [4, 7]], np.int32)
+    g = gdp.Mesh(xy, seg)
+    stats = g.refine(SQ2)
+    gxy, gtri, gsub = g.export()
+    rep = oracle.check(gxy, gtri, gsub, seg, len(xy), B=SQ2)
+    assert_valid(rep)
+    assert stats["n_steiner"] < 20000
+
+
+def test_iteration_limit_keeps_valid_cdt(oracle):
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.tiny()
+    g = gdp.Mesh(p.xy, p.seg)
+    st, stats = g.refine(SQ2, max_iter=2, graph_iters=-1, check=False)
+    assert st == gdp.ERR_ITER_LIMIT
+    xy, tri, sub = g.export()
+    assert_valid(oracle.check(xy, tri, sub, p.seg, p.n, brute=True), refined=False, brute=True)
