@@ -161,6 +161,40 @@ int gdp_batch_export(gdp_batch* b, int32_t mesh, double* xy, int64_t cap_pts, in
                      int64_t* n_tri, int64_t* n_seg);
 void gdp_batch_destroy(gdp_batch* b);
 
+/* ---------------- scan without device allocation ----------------
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that must not allocate device memory (code running inside another
+ * allocator's callbacks, processes whose device memory is fully pre-reserved
+ * by a framework pool, real-time paths where an allocation could block).
+ * It runs the same per-element tests as gdp_mesh_scan on a triangulation the
+ * caller keeps in its own device buffers and writes into output buffers the
+ * caller owns; it calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ *   xy_device:  2*n_vert doubles (x, y), 16-byte aligned
+ *   tri_device: 4 int32 per triangle, 16-byte aligned: v0, v1, v2 (CCW) and a
+ *               flags word whose bit e says that edge e = (v[e+1], v[e+2]) is a
+ *               subsegment
+ *   outputs (device, cap entries each, as in gdp_mesh_scan): kind_device,
+ *               verts_device (3 per entry), pt_device (2 doubles per entry,
+ *               circumcentre or midpoint), meas_device
+ *   *count (host): number of entries found, even beyond cap.  Entries come in
+ *               triangle order: a bad triangle first, then its encroached edges.
+ * Scratch: one file-scope device array of about 4.2 MB (per-triangle counts for
+ * up to GDP_NOALLOC_MAX_TRIANGLES triangles plus block sums) that every GPU
+ * which loads the library keeps until the process exits.  n_tri above
+ * GDP_NOALLOC_MAX_TRIANGLES gives GDP_ERR_CAPACITY; a vertex id outside
+ * [0, n_vert) or a misaligned buffer gives GDP_ERR_INPUT.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU (for example
+ * on two streams) race on it: issue them one after another.  The call blocks
+ * until the count has been read back. */
+#define GDP_NOALLOC_MAX_TRIANGLES (1 << 22)
+int gdp_scan_noalloc(const double* xy_device, int64_t n_vert, const int32_t* tri_device,
+                     int64_t n_tri, double B, int32_t* kind_device, int32_t* verts_device,
+                     double* pt_device, uint32_t* meas_device, int64_t cap, int64_t* count,
+                     void* cuda_stream);
+
 const char* gdp_status_str(int status);
 
 #ifdef __cplusplus

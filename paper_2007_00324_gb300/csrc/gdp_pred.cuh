@@ -60,7 +60,7 @@ struct Expansion {
     for (int i = 0; i < n; ++i) {
       double h;
       two_sum(q, e[i], q, h);
-      if (h != 0.0) e[k++] = h;
+      if (h != 0.0 && k < N - 1) e[k++] = h;   // k < N-1 keeps room for q (bounded range)
     }
     if (q != 0.0) e[k++] = q;
     n = k;
@@ -115,7 +115,7 @@ __device__ __forceinline__ void add_prod2(Expansion<N>& X, double ah, double al,
 }
 
 // ---------------------------------------------------------------- orient
-__device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
+static __device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
                                          double cy) {
   // (ax-cx)(by-cy) - (ay-cy)(bx-cx) with each difference as an exact pair
   double acxh, acxl, acyh, acyl, bcxh, bcxl, bcyh, bcyl;
@@ -151,7 +151,7 @@ __device__ __forceinline__ int orient(double2 a, double2 b, double2 c) {
 // ---------------------------------------------------------------- incircle
 // det = alift_a*(bdx*cdy - cdx*bdy) + alift_b*(cdx*ady - adx*cdy) + alift_c*(adx*bdy - bdx*ady)
 // with every difference relative to d.
-__device__ __noinline__ int incircle_exact(double ax, double ay, double bx, double by, double cx,
+static __device__ __noinline__ int incircle_exact(double ax, double ay, double bx, double by, double cx,
                                            double cy, double dx, double dy) {
   double h[6], l[6];   // adx ady bdx bdy cdx cdy as exact pairs
   two_diff(ax, dx, h[0], l[0]);
@@ -237,7 +237,7 @@ GDP_HD bool lex_less(double ax, double ay, double bx, double by) {
 // row i's lift entry: C_a = +orient(b,c,d), C_b = -orient(a,c,d),
 // C_c = +orient(a,b,d), C_d = -orient(a,b,c).  Ranking by coordinates (not by
 // vertex number) makes the result independent of how vertices are numbered.
-__device__ __noinline__ int incircle_sos_tie(double2 a, double2 b, double2 c, double2 d) {
+static __device__ __noinline__ int incircle_sos_tie(double2 a, double2 b, double2 c, double2 d) {
   double2 P[4] = {a, b, c, d};
   int ord[4] = {0, 1, 2, 3};
   for (int i = 1; i < 4; ++i) {       // decreasing lexicographic order
@@ -267,7 +267,7 @@ __device__ __forceinline__ int incircle(double2 a, double2 b, double2 c, double2
 }
 
 // ---------------------------------------------------------------- diametral circle
-__device__ __noinline__ int dot_exact(double ax, double ay, double bx, double by, double px,
+static __device__ __noinline__ int dot_exact(double ax, double ay, double bx, double by, double px,
                                       double py) {
   double axh, axl, ayh, ayl, bxh, bxl, byh, byl;
   two_diff(ax, px, axh, axl);

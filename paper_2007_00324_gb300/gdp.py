@@ -44,8 +44,10 @@ class Stats(C.Structure):
 
 SYMBOLS = ["gdp_mesh_create", "gdp_mesh_create_device", "gdp_mesh_refine", "gdp_mesh_export",
            "gdp_mesh_insert_points", "gdp_mesh_split_subsegments", "gdp_mesh_scan",
-           "gdp_mesh_stats", "gdp_mesh_profile", "gdp_mesh_kernel_time", "gdp_mesh_destroy", "gdp_batch_create", "gdp_batch_refine",
-           "gdp_batch_info", "gdp_batch_export", "gdp_batch_destroy", "gdp_status_str"]
+           "gdp_mesh_stats", "gdp_mesh_profile", "gdp_mesh_kernel_time", "gdp_mesh_destroy",
+           "gdp_batch_create", "gdp_batch_refine",
+           "gdp_batch_info", "gdp_batch_export", "gdp_batch_destroy", "gdp_scan_noalloc",
+           "gdp_status_str"]
 
 
 def load(build_if_missing: bool = True):
@@ -80,6 +82,8 @@ def load(build_if_missing: bool = True):
                                            C.POINTER(i64), C.POINTER(i64)]
             L.gdp_batch_destroy.argtypes = [vp]
             L.gdp_batch_destroy.restype = None
+            L.gdp_scan_noalloc.argtypes = [vp, i64, vp, i64, d, vp, vp, vp, vp, i64,
+                                           C.POINTER(i64), vp]
             L.gdp_status_str.argtypes = [C.c_int]
             L.gdp_status_str.restype = C.c_char_p
             for n in SYMBOLS:
@@ -288,3 +292,18 @@ class Batch:
         if st != OK:
             raise GdpError(st, "gdp_batch_export")
         return xy, tri, sub
+
+
+def scan_noalloc(xy, tri4, B, kind, verts, pt, meas, stream=None):
+    """gdp_scan_noalloc on caller-owned torch CUDA tensors: xy (n,2) float64,
+    tri4 (t,4) int32, outputs kind (cap,) int32, verts (cap,3) int32,
+    pt (cap,2) float64, meas (cap,) int32.  Returns the entry count."""
+    cnt = C.c_int64()
+    st = load().gdp_scan_noalloc(C.c_void_p(xy.data_ptr()), int(xy.shape[0]),
+                                 C.c_void_p(tri4.data_ptr()), int(tri4.shape[0]), float(B),
+                                 C.c_void_p(kind.data_ptr()), C.c_void_p(verts.data_ptr()),
+                                 C.c_void_p(pt.data_ptr()), C.c_void_p(meas.data_ptr()),
+                                 int(kind.shape[0]), C.byref(cnt), _stream_handle(stream))
+    if st != OK:
+        raise GdpError(st, "gdp_scan_noalloc")
+    return cnt.value
