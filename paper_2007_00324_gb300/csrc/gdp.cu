@@ -110,9 +110,11 @@ __global__ void k_iota(int* a, int n) {
 
 __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const double2 org = P.mi[P.T[t].w >> 4].org;
   for (int k = gt; k < n; k += gs) {
     P.pts[k] = ids[k];
     P.loc[ids[k]] = t;
+    P.Vf[ids[k]] = to_f(P.V[ids[k]], org);
   }
 }
 
@@ -134,6 +136,15 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
     kern<<<(grid), BS, 0, (h).stream>>>(__VA_ARGS__);                \
     (h).prof_end();                                                  \
   } while (0)
+// per-candidate kernels: small blocks over a wide grid, so that a few
+// thousand latency-bound threads land on every SM instead of a few blocks
+constexpr int BS_CAND = 64;
+#define LAUNCH_C(h, kern, ...)                                       \
+  do {                                                               \
+    (h).prof_begin(#kern);                                           \
+    kern<<<(h).Gc, BS_CAND, 0, (h).stream>>>(__VA_ARGS__);           \
+    (h).prof_end();                                                  \
+  } while (0)
 
 double env_double(const char* name, double def) {
   const char* s = std::getenv(name);
@@ -142,10 +153,23 @@ double env_double(const char* name, double def) {
 
 }  // namespace
 
+static void print_diag(const char* where) {
+  if (!std::getenv("GDP_TRACE")) return;
+  unsigned long long d[16];
+  cudaDeviceSynchronize();
+  if (cudaMemcpyFromSymbol(d, g_diag, sizeof(d)) != cudaSuccess) return;
+  std::fprintf(stderr,
+               "[%s] orient_exact %llu incircle_exact %llu (inexact diffs %llu, max %llu cyc) sos %llu "
+               "dot_exact %llu | max walk steps %llu, max walk cyc %llu, max grow cyc %llu\n",
+               where, d[0], d[1], d[4], d[8], d[2], d[3], d[5], d[7], d[6]);
+  unsigned long long z[16] = {};
+  cudaMemcpyToSymbol(g_diag, z, sizeof(z));
+}
+
 // ---------------------------------------------------------------- the pool
 struct PoolHost {
   cudaStream_t stream = nullptr;
-  int n_sm = 0, G = 0;
+  int n_sm = 0, G = 0, Gc = 0;
   Pool P{};
   std::vector<MeshInfo> hmi;
   std::vector<int2> hseg;         // input segments, global vertex ids
@@ -265,6 +289,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return GDP_ERR_CUDA; }
   CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   G = 4 * n_sm;
+  Gc = 16 * n_sm;
   prof = std::getenv("GDP_PROFILE") != nullptr;
   CK(cudaMallocHost(&hctrl, sizeof(Ctrl)));
   CK(cudaEventCreate(&ev0));
@@ -301,6 +326,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
 #define AL(ptr, n, fill) \
   if ((st = alloc(&(ptr), (size_t)(n), fill)) != GDP_OK) return st;
   AL(P.V, vb, 0);
+  AL(P.Vf, vb, 0);
   AL(P.vseg, vb, 0xff);
   AL(P.vtri, vb, 0xff);
   AL(P.apex, vb, 0);
@@ -316,7 +342,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   AL(P.adj, 2 * sb, 0);
   const size_t C = (size_t)P.cap_cand;
   AL(P.c_elem, C, 0); AL(P.c_loc, C, 0); AL(P.c_vid, C, 0); AL(P.c_mesh, C, 0);
-  AL(P.c_vseg, C, 0); AL(P.c_sub, C, 0); AL(P.c_pt, C, 0); AL(P.c_key, C, 0);
+  AL(P.c_vseg, C, 0); AL(P.c_sub, C, 0); AL(P.c_pt, C, 0); AL(P.c_ptf, C, 0); AL(P.c_key, C, 0);
   AL(P.c_ncav, C, 0); AL(P.c_nbnd, C, 0); AL(P.c_cav, C * CMAX, 0); AL(P.c_bnd, C * BMAX, 0);
   AL(P.c_state, C, 0); AL(P.c_final, C, 0); AL(P.c_extra, C, 0); AL(P.c_offT, C, 0);
   AL(P.c_offV, C, 0); AL(P.c_base, C, 0);
@@ -385,12 +411,12 @@ int PoolHost::insert_rounds(int stop_cons, int* rounds_out) {
     LAUNCH(*this, k_cdt_locate, G, P, rounds, stop_cons);
     LAUNCH(*this, k_cdt_pick_count, G, P, rounds);
     LAUNCH(*this, k_cdt_pick_write, G, P, rounds);
-    LAUNCH(*this, k_grow<1>, G, P);
-    LAUNCH(*this, k_survive, G, P);
+    LAUNCH_C(*this, k_grow<1>, P);
+    LAUNCH_C(*this, k_survive, P);
     LAUNCH(*this, k_depend, G, P);
     LAUNCH(*this, k_offsets, G, P);
-    LAUNCH(*this, k_insert<1>, G, P);
-    LAUNCH(*this, k_link<1>, G, P);
+    LAUNCH_C(*this, k_insert<1>, P);
+    LAUNCH_C(*this, k_link<1>, P);
     LAUNCH(*this, k_cdt_keep_count, G, P);
     LAUNCH(*this, k_cdt_keep_write, G, P);
     CK(cudaGetLastError());
@@ -498,6 +524,7 @@ int PoolHost::build_cdt() {
   // marks and the candidate list start empty
   if (set_ctrl_field(offsetof(Ctrl, prev_cand), 0) != GDP_OK) return GDP_ERR_CUDA;
   stats.n_in_pts = tot_in;
+  print_diag("cdt");
   int worst = GDP_OK;
   for (auto& M : hmi)
     if (M.status != S_OK && worst == GDP_OK) worst = M.status;
@@ -507,12 +534,12 @@ int PoolHost::build_cdt() {
 int PoolHost::launch_iteration() {
   LAUNCH(*this, k_scan_count, G, P);
   LAUNCH(*this, k_scan_write, G, P);
-  LAUNCH(*this, k_grow<0>, G, P);
-  LAUNCH(*this, k_survive, G, P);
+  LAUNCH_C(*this, k_grow<0>, P);
+  LAUNCH_C(*this, k_survive, P);
   LAUNCH(*this, k_depend, G, P);
   LAUNCH(*this, k_offsets, G, P);
-  LAUNCH(*this, k_insert<0>, G, P);
-  LAUNCH(*this, k_link<0>, G, P);
+  LAUNCH_C(*this, k_insert<0>, P);
+  LAUNCH_C(*this, k_link<0>, P);
   return cudaGetLastError() == cudaSuccess ? GDP_OK : GDP_ERR_CUDA;
 }
 
@@ -528,6 +555,7 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
     const double b = B ? B[m] : d.B;
     if (!(b > 0.7072)) return GDP_ERR_INPUT;
     M.B2 = b * b;
+    M.B2f = (float)M.B2;
     M.active = M.status == S_OK ? 1 : 0;
     M.steiner = 0;
     M.cand_cap = d.cand_cap;
@@ -583,6 +611,7 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   CK(cudaEventElapsedTime(&ms, ev0, ev1));
   if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
   stats.refine_ms = ms;
+  print_diag("refine");
   stats.iterations = (int64_t)hctrl->iters;
   stats.candidates = (int64_t)hctrl->tot_cand;
   stats.inserted = (int64_t)hctrl->tot_ins;
@@ -851,12 +880,12 @@ int gdp_mesh_split_subsegments(gdp_mesh* g, const double* abxy, int64_t n) {
     CK(cudaMemcpyAsync(&h.P.ctrl->n_cand, &nc, sizeof(int), cudaMemcpyHostToDevice, h.stream));
     CK(cudaMemcpyAsync(&h.P.ctrl->prev_cand, &nc, sizeof(int), cudaMemcpyHostToDevice, h.stream));
     for (auto& Mi : h.hmi) Mi.active = 1;
-    LAUNCH(h, k_grow<0>, h.G, h.P);
-    LAUNCH(h, k_survive, h.G, h.P);
+    LAUNCH_C(h, k_grow<0>, h.P);
+    LAUNCH_C(h, k_survive, h.P);
     LAUNCH(h, k_depend, h.G, h.P);
     LAUNCH(h, k_offsets, h.G, h.P);
-    LAUNCH(h, k_insert<0>, h.G, h.P);
-    LAUNCH(h, k_link<0>, h.G, h.P);
+    LAUNCH_C(h, k_insert<0>, h.P);
+    LAUNCH_C(h, k_link<0>, h.P);
     CK(cudaGetLastError());
     if (h.sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
     if (h.hctrl->err) return h.hctrl->err;

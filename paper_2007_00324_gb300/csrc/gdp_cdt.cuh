@@ -58,6 +58,7 @@ __global__ void k_cdt_init(Pool P) {
     if (!(D > 0)) D = 1.0;
     M.lo = make_double2(sx0[0], sy0[0]);
     M.hi = make_double2(sx1[0], sy1[0]);
+    M.org = make_double2(cx, cy);
     const int s0 = M.vert_base + M.n_in;
     P.V[s0] = make_double2(cx - 64 * D, cy - 64 * D);
     P.V[s0 + 1] = make_double2(cx + 64 * D, cy - 64 * D);
@@ -76,10 +77,17 @@ __global__ void k_cdt_init(Pool P) {
       P.loc[s0 + k] = M.tri_base;
       P.pts[M.pts_base + M.n_in + k - 3] = s0 + k;
     }
+    for (int k = 0; k < N_AUX; ++k) P.Vf[s0 + k] = to_f(P.V[s0 + k], M.org);
     P.T[M.tri_base] = make_int4(s0, s0 + 1, s0 + 2, m << 4);
     P.N[M.tri_base] = make_int4(-1, -1, -1, 0);
     M.tri_count = 1;
     M.vert_count = M.n_in + N_AUX;
+  }
+  __syncthreads();
+  const double2 org = M.org;
+  for (int k = threadIdx.x; k < M.n_in; k += blockDim.x) {
+    const int v = M.vert_base + k;
+    P.Vf[v] = to_f(P.V[v], org);
   }
 }
 
@@ -91,7 +99,7 @@ __global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int round, int stop_c
     const int v = P.pts[k];
     const double2 p = P.V[v];
     int bt, be;
-    const int t = walk(P, P.loc[v], p, false, bt, be);
+    const int t = walk(P, P.loc[v], pt(P, v), false, bt, be);
     if (t < 0) {
       set_err(P.ctrl, t == -2 ? S_WALK : S_INTERNAL);
       continue;
@@ -108,7 +116,7 @@ __global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int round, int stop_c
       // inserted points must not lie on a subsegment
       for (int e = 0; e < 3; ++e)
         if (((T4.w >> e) & 1) &&
-            orient(P.V[comp(T4, mod3(e + 1))], P.V[comp(T4, mod3(e + 2))], p) == 0)
+            orient(pt(P, comp(T4, mod3(e + 1))), pt(P, comp(T4, mod3(e + 2))), pt(P, v)) == 0)
           dup = true;
     }
     if (dup) {
@@ -234,7 +242,7 @@ __device__ void flip(const Pool& P, int t1, int e1) {
 
 __device__ __forceinline__ bool crosses_seg(const Pool& P, int a, int b, int u, int v) {
   if (u == a || u == b || v == a || v == b) return false;
-  const double2 A = P.V[a], B = P.V[b], U = P.V[u], W = P.V[v];
+  const P2 A = pt(P, a), B = pt(P, b), U = pt(P, u), W = pt(P, v);
   return orient(A, B, U) * orient(A, B, W) < 0 && orient(U, W, A) * orient(U, W, B) < 0;
 }
 
@@ -270,9 +278,9 @@ __global__ void __launch_bounds__(BS) k_seg_find(Pool P, int round) {
         status = -1;
         break;
       }
-      const double2 A = P.V[a], B = P.V[b];
-      const int o1 = orient(A, P.V[u], B), o2 = orient(A, P.V[w], B);
-      if (o1 == 0 && dot_sign(P.V[u], B, A) > 0) { status = S_INPUT; break; }
+      const P2 A = pt(P, a), B = pt(P, b);
+      const int o1 = orient(A, pt(P, u), B), o2 = orient(A, pt(P, w), B);
+      if (o1 == 0 && dot_sign(pt(P, u), B, A) > 0) { status = S_INPUT; break; }
       if (o1 > 0 && o2 < 0) { start = t; ia = i; break; }
       const int nb = comp(P.N[t], mod3(i + 2));   // clockwise: across (a, u)
       if (nb < 0) { status = S_INTERNAL; break; }
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(BS) k_seg_find(Pool P, int round) {
       const int4 T4 = P.T[tn];
       const int z = comp(T4, ee);
       if (z == b) break;
-      const int o = orient(P.V[a], P.V[b], P.V[z]);
+      const int o = orient(pt(P, a), pt(P, b), pt(P, z));
       if (o == 0) { status = S_INPUT; break; }
       if (o > 0) {
         ref = comp(P.N[tn], idx_of(T4, l));
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(BS) k_seg_apply(Pool P, int round, int2* work)
       const int4 B = P.T[ref >> 2];
       const int p1 = comp(A, e1), u = comp(A, mod3(e1 + 1)), v = comp(A, mod3(e1 + 2));
       const int o = comp(B, ref & 3);
-      if (orient(P.V[p1], P.V[u], P.V[o]) > 0 && orient(P.V[p1], P.V[o], P.V[v]) > 0) {
+      if (orient(pt(P, p1), pt(P, u), pt(P, o)) > 0 && orient(pt(P, p1), pt(P, o), pt(P, v)) > 0) {
         flip(P, t1, e1);
         if (crosses_seg(P, a, b, p1, o)) {
           Q[(qh + qn) % KMAX] = make_int2(p1, o);
@@ -437,9 +445,9 @@ __global__ void __launch_bounds__(BS) k_seg_apply(Pool P, int round, int2* work)
           const int t2 = ref >> 2;
           if (!in_region(R, cnt, t2)) continue;
           const int o = comp(P.T[t2], ref & 3);
-          if (incircle(P.V[T4.x], P.V[T4.y], P.V[T4.z], P.V[o]) > 0) {
+          if (incircle(pt(P, T4.x), pt(P, T4.y), pt(P, T4.z), pt(P, o)) > 0) {
             const int p1 = comp(T4, e), u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
-            if (orient(P.V[p1], P.V[u], P.V[o]) > 0 && orient(P.V[p1], P.V[o], P.V[v]) > 0) {
+            if (orient(pt(P, p1), pt(P, u), pt(P, o)) > 0 && orient(pt(P, p1), pt(P, o), pt(P, v)) > 0) {
               flip(P, t, e);
               any = true;
             }

@@ -50,6 +50,8 @@ struct MeshInfo {
   int32_t tmp;           // scratch for per-mesh reductions
   double B2;
   double2 lo, hi;        // bounding box of the input points
+  double2 org;           // origin of the float coordinate copies (box centre)
+  float B2f;             // B^2 rounded to float (FP32 pre-checks)
 };
 
 struct Ctrl {
@@ -67,6 +69,7 @@ struct Ctrl {
 struct Pool {
   // mesh
   double2* V;
+  float2* Vf;            // float copies of V - org (FP32 filter stage)
   int32_t* vseg;
   int32_t* vtri;
   uint8_t* apex;
@@ -93,6 +96,7 @@ struct Pool {
   int32_t* c_vseg;
   int2* c_sub;
   double2* c_pt;
+  float2* c_ptf;
   unsigned long long* c_key;
   int32_t* c_ncav;
   int32_t* c_nbnd;

@@ -108,6 +108,11 @@ __device__ __forceinline__ Chunk chunk_of(int n) {
   return {b0, min(n, b0 + c)};
 }
 
+__device__ __forceinline__ P2 pt(const Pool& P, int v) { return P2{P.V[v], P.Vf[v]}; }
+__device__ __forceinline__ float2 to_f(double2 p, double2 org) {
+  return make_float2(__double2float_rn(__dsub_rn(p.x, org.x)), __double2float_rn(__dsub_rn(p.y, org.y)));
+}
+
 // ---------------------------------------------------------------- mesh queries
 // Auxiliary vertices of every mesh, right after its input points: three
 // enclosing vertices, then four frame vertices around the bounding box.  The
@@ -229,16 +234,17 @@ __device__ int eval_tri(const Pool& P, int t) {
     double bl = -1.0;
     for (int e = 0; e < 3; ++e) {
       if (!((cons >> e) & 1)) continue;
-      const double2 u = P.V[comp(T4, mod3(e + 1))], v = P.V[comp(T4, mod3(e + 2))];
-      if (dot_sign(u, v, P.V[comp(T4, e)]) < 0) {
-        const double l = seg_measure(u, v);
+      const P2 u = pt(P, comp(T4, mod3(e + 1))), v = pt(P, comp(T4, mod3(e + 2)));
+      if (dot_sign(u, v, pt(P, comp(T4, e))) < 0) {
+        const double l = seg_measure(u.d, v.d);
         if (l > bl) { bl = l; best = e; }
       }
     }
     if (best >= 0) return 1 + best;
   }
-  const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
-  if (is_bad(tt, M.B2) && !exempt(P, M, T4)) return 4;
+  const int q = bad_f32(P.Vf[T4.x], P.Vf[T4.y], P.Vf[T4.z], M.B2f);
+  const bool bad = q > 0 || (q == 0 && is_bad(tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]), M.B2));
+  if (bad && !exempt(P, M, T4)) return 4;
   return 0;
 }
 
@@ -323,16 +329,22 @@ __global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
 // hull -- (bt, be) is that edge -- or -2 at the step limit.  In a CDT every
 // step across a locally Delaunay edge lowers the power of p with respect to
 // the current circumcircle, so the walk cannot cycle.
-__device__ int walk(const Pool& P, int t, double2 p, bool stop_cons, int& bt, int& be) {
+__device__ int walk(const Pool& P, int t, const P2& p, bool stop_cons, int& bt, int& be) {
   int from = -1;
+#ifdef GDP_DIAG
+  const long long c0 = clock64();
+#endif
   for (int s = 0; s < WALK_MAX; ++s) {
+#ifdef GDP_DIAG
+    if (s > 0 && (s & 7) == 0) atomicMax(&g_diag[5], (unsigned long long)s);
+#endif
     const int4 T4 = P.T[t];
     const int4 N4 = P.N[t];
     int next = -1, nfrom = -1, blk = -1;
     for (int e = 0; e < 3 && next < 0; ++e) {
       const int nb = comp(N4, e);
       if (nb >= 0 && (nb >> 2) == from) continue;   // p is on this side of the entry edge
-      if (orient(P.V[comp(T4, mod3(e + 1))], P.V[comp(T4, mod3(e + 2))], p) < 0) {
+      if (orient(pt(P, comp(T4, mod3(e + 1))), pt(P, comp(T4, mod3(e + 2))), p) < 0) {
         if ((stop_cons && ((T4.w >> e) & 1)) || nb < 0) {
           if (blk < 0) blk = e;
         } else {
@@ -346,6 +358,9 @@ __device__ int walk(const Pool& P, int t, double2 p, bool stop_cons, int& bt, in
       t = next;
       continue;
     }
+#ifdef GDP_DIAG
+    atomicMax(&g_diag[7], (unsigned long long)(clock64() - c0));
+#endif
     if (blk >= 0) {
       bt = t;
       be = blk;
@@ -364,7 +379,7 @@ enum { G_OK = 0, G_OVF = 1, G_CONV = 2 };
 // (u, v, outside ref, inside ref | subsegment bit).  With conv, meeting a
 // subsegment that p encroaches stops the growth (G_CONV) so that the
 // subsegment is split instead (Sec. 4.2: such a circumcentre is redundant).
-__device__ int grow(const Pool& P, int i, double2 p, int t0, int t1, bool conv, int& nc, int& nb,
+__device__ int grow(const Pool& P, int i, const P2& p, int t0, int t1, bool conv, int& nc, int& nb,
                     int& ct, int& ce) {
   int* cav = P.c_cav + (size_t)i * CMAX;
   int4* bnd = P.c_bnd + (size_t)i * BMAX;
@@ -389,8 +404,8 @@ __device__ int grow(const Pool& P, int i, double2 p, int t0, int t1, bool conv, 
       bool inside = false;
       if (!cons && ref >= 0) {
         const int4 Tn = P.T[ref >> 2];
-        inside = incircle(P.V[Tn.x], P.V[Tn.y], P.V[Tn.z], p) > 0;
-      } else if (cons && conv && dot_sign(P.V[u], P.V[v], p) < 0) {
+        inside = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
+      } else if (cons && conv && dot_sign(pt(P, u), pt(P, v), p) < 0) {
         ct = t;
         ce = e;
         return G_CONV;
@@ -447,7 +462,7 @@ __global__ void __launch_bounds__(BS) k_grow(Pool P) {
         p = circumcenter(tt);
         key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
         int bt = -1, be = -1;
-        const int r = walk(P, t, p, true, bt, be);
+        const int r = walk(P, t, P2{p, to_f(p, M.org)}, true, bt, be);
         if (r == -2) {
           P.c_mesh[i] = m;
           set_err(P.ctrl, S_WALK);
@@ -480,8 +495,15 @@ __global__ void __launch_bounds__(BS) k_grow(Pool P) {
       }
     }
     P.c_mesh[i] = m;
+    P2 pp{p, MODE == 1 ? P.Vf[vid] : to_f(p, P.mi[m].org)};
     int nc = 0, nb = 0, ct = -1, ce = -1;
-    int g = grow(P, i, p, t0, t1, conv, nc, nb, ct, ce);
+#ifdef GDP_DIAG
+    const long long gc0 = clock64();
+#endif
+    int g = grow(P, i, pp, t0, t1, conv, nc, nb, ct, ce);
+#ifdef GDP_DIAG
+    atomicMax(&g_diag[6], (unsigned long long)(clock64() - gc0));
+#endif
     if (g == G_CONV) {
       const int4 B4 = P.T[ct];
       const int u = comp(B4, mod3(ce + 1)), v = comp(B4, mod3(ce + 2));
@@ -490,7 +512,8 @@ __global__ void __launch_bounds__(BS) k_grow(Pool P) {
             (unsigned)i;
       sub = make_int2(u, v);
       const int nr = comp(P.N[ct], ce);
-      g = grow(P, i, p, ct, nr >= 0 ? nr >> 2 : -1, false, nc, nb, ct, ce);
+      pp = P2{p, to_f(p, P.mi[m].org)};
+      g = grow(P, i, pp, ct, nr >= 0 ? nr >> 2 : -1, false, nc, nb, ct, ce);
     }
     if (g != G_OK) continue;   // buffer overflow: retried in a later iteration (Rule 3)
     const int4* bnd = P.c_bnd + (size_t)i * BMAX;
@@ -498,12 +521,13 @@ __global__ void __launch_bounds__(BS) k_grow(Pool P) {
     for (int r = 0; r < nb && ok; ++r) {
       const int4 rec = bnd[r];
       if (is_split_edge(rec, sub)) continue;
-      if (orient(P.V[rec.x], P.V[rec.y], p) <= 0) ok = false;
+      if (orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) ok = false;
     }
     if (!ok) continue;
     const int* cav = P.c_cav + (size_t)i * CMAX;
     for (int j = 0; j < nc; ++j) atomicMax(&P.mark[cav[j]], key);
     P.c_pt[i] = p;
+    P.c_ptf[i] = pp.f;
     P.c_key[i] = key;
     P.c_ncav[i] = nc;
     P.c_nbnd[i] = nb;
@@ -550,7 +574,7 @@ __global__ void __launch_bounds__(BS) k_depend(Pool P) {
     if (P.c_state[i] == C_SURV) {
       fin = true;
       const unsigned long long key = P.c_key[i];
-      const double2 p = P.c_pt[i];
+      const P2 p{P.c_pt[i], P.c_ptf[i]};
       const int nb = P.c_nbnd[i];
       const int4* bnd = P.c_bnd + (size_t)i * BMAX;
       const int2 sub = P.c_sub[i];
@@ -563,7 +587,9 @@ __global__ void __launch_bounds__(BS) k_depend(Pool P) {
         if (!mo) continue;
         const int j = (int)(unsigned)(mo & 0xffffffffull);
         if (j == i || j >= n || P.c_state[j] != C_SURV) continue;
-        if (incircle(p, P.V[rec.x], P.V[rec.y], P.c_pt[j]) > 0 && key < P.c_key[j]) fin = false;
+        if (incircle(p, pt(P, rec.x), pt(P, rec.y), P2{P.c_pt[j], P.c_ptf[j]}) > 0 &&
+            key < P.c_key[j])
+          fin = false;
       }
       if (fin) extra = eff - P.c_ncav[i];
     }
@@ -642,6 +668,7 @@ __global__ void __launch_bounds__(BS) k_insert(Pool P) {
     P.c_base[i] = base;
     const double2 p = P.c_pt[i];
     P.V[vid] = p;
+    P.Vf[vid] = P.c_ptf[i];
     P.vseg[vid] = P.c_vseg[i];
     if (MODE == 1) P.loc[vid] = -1;
     const int4* bnd = P.c_bnd + (size_t)i * BMAX;
@@ -730,7 +757,7 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
 // Every live triangle: its bad flag; every subsegment edge: encroachment by
 // this triangle's apex.  Output in slot order.
 __global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int* kind, int* verts,
-                                                    double2* pt, unsigned* meas, int cap,
+                                                    double2* spt, unsigned* meas, int cap,
                                                     int* count) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int t = gt; t < P.n_slots; t += gs) {
@@ -738,24 +765,25 @@ __global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int* kind
     if (T4.w < 0 || (T4.w & INFO_DEAD)) continue;
     const MeshInfo& M = P.mi[T4.w >> 4];
     const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
-    if (is_bad(tt, B2)) {
+    const int q = bad_f32(P.Vf[T4.x], P.Vf[T4.y], P.Vf[T4.z], __double2float_rn(B2));
+    if (q > 0 || (q == 0 && is_bad(tt, B2))) {
       const int r = atomicAdd(count, 1);
       if (r < cap) {
         kind[r] = 0;
         verts[3 * r] = T4.x; verts[3 * r + 1] = T4.y; verts[3 * r + 2] = T4.z;
-        pt[r] = circumcenter(tt);
+        spt[r] = circumcenter(tt);
         meas[r] = measure_bits(fabs(tt.cr));
       }
     }
     for (int e = 0; e < 3; ++e) {
       if (!((T4.w >> e) & 1)) continue;
       const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
-      if (dot_sign(P.V[u], P.V[v], P.V[comp(T4, e)]) < 0) {
+      if (dot_sign(pt(P, u), pt(P, v), pt(P, comp(T4, e))) < 0) {
         const int r = atomicAdd(count, 1);
         if (r < cap) {
           kind[r] = 1;
           verts[3 * r] = u; verts[3 * r + 1] = v; verts[3 * r + 2] = -1;
-          pt[r] = split_point(P, M, u, v);
+          spt[r] = split_point(P, M, u, v);
           meas[r] = measure_bits(seg_measure(P.V[u], P.V[v]));
         }
       }

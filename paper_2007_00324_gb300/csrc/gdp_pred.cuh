@@ -24,6 +24,12 @@
 namespace gdp {
 
 constexpr double kU = 1.1102230246251565e-16;   // 2^-53
+
+// diagnostic counters (per translation unit): exact-path calls and maxima
+// 0 orient_exact, 1 incircle_exact, 2 incircle tie (simulation of simplicity),
+// 3 dot_exact, 4 incircle_exact with inexact differences, 5 max walk steps,
+// 6 max cycles in one grow, 7 max cycles in one walk, 8 max cycles of one exact incircle
+static __device__ unsigned long long g_diag[16];
 constexpr double kTiny = 1e-250;                // below: relative bounds unsafe -> exact
 
 // ---------------------------------------------------------------- EFTs
@@ -114,15 +120,147 @@ __device__ __forceinline__ void add_prod2(Expansion<N>& X, double ah, double al,
   if (al != 0.0 && bl != 0.0) { two_prod(al, bl, x, y); X.grow(y); X.grow(x); }
 }
 
+// ---------------------------------------------------------------- exact sums in integers
+// When every coordinate difference of a predicate is itself an exact double
+// (two_diff leaves no tail -- the common case), the determinant is a signed
+// sum of products of those doubles.  Each double is m * 2^e with an integer
+// mantissa m < 2^53 (from its bit pattern, no floating-point operation), a
+// product of k doubles is an integer of at most 53k bits times 2^(sum of e),
+// and all products are summed exactly in a 576-bit two's-complement
+// accumulator after aligning them to the smallest exponent.  Integer
+// multiplies run at full rate on the SM, unlike FP64.
+constexpr int IL = 9;   // accumulator limbs
+
+struct Mono {
+  unsigned long long m[4];   // |product|, little-endian limbs
+  int nl;
+  int e;
+  bool neg;
+};
+
+__device__ __forceinline__ bool split_dbl(double x, unsigned long long& m, int& e, bool& neg) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0x7ff) return false;
+  neg = (b >> 63) != 0;
+  m = b & ((1ull << 52) - 1);
+  if (ex == 0) {
+    e = -1074;
+  } else {
+    m |= 1ull << 52;
+    e = ex - 1075;
+  }
+  return true;
+}
+
+// product of k doubles (none zero) into mo
+__device__ __forceinline__ bool mono_prod(const double* f, int k, double coef_sign, Mono& mo) {
+  mo.m[0] = 1;
+  mo.m[1] = mo.m[2] = mo.m[3] = 0;
+  mo.nl = 1;
+  mo.e = 0;
+  mo.neg = coef_sign < 0;
+  for (int j = 0; j < k; ++j) {
+    unsigned long long m;
+    int e;
+    bool ng;
+    if (!split_dbl(f[j], m, e, ng)) return false;
+    mo.neg ^= ng;
+    mo.e += e;
+    unsigned long long carry = 0;
+    for (int l = 0; l < mo.nl; ++l) {
+      const unsigned long long lo = mo.m[l] * m;
+      const unsigned long long hi = __umul64hi(mo.m[l], m);
+      const unsigned long long s = lo + carry;
+      carry = hi + (s < lo ? 1ull : 0ull);
+      mo.m[l] = s;
+    }
+    if (carry) mo.m[mo.nl++] = carry;
+  }
+  return true;
+}
+
+// acc += (neg ? -1 : 1) * (m << sh); false if the shifted value does not fit
+__device__ __forceinline__ bool acc_add(unsigned long long* acc, const Mono& mo, int sh) {
+  const int w = sh >> 6, bsh = sh & 63;
+  if (w + mo.nl + 1 > IL - 1) return false;
+  unsigned long long t[IL];
+  for (int l = 0; l < IL; ++l) t[l] = 0;
+  for (int l = 0; l < mo.nl; ++l) {
+    t[w + l] |= mo.m[l] << bsh;
+    if (bsh) t[w + l + 1] |= mo.m[l] >> (64 - bsh);
+  }
+  if (!mo.neg) {
+    unsigned long long c = 0;
+    for (int l = 0; l < IL; ++l) {
+      const unsigned long long s = acc[l] + t[l];
+      const unsigned long long s2 = s + c;
+      c = (s < acc[l] ? 1ull : 0ull) + (s2 < s ? 1ull : 0ull);
+      acc[l] = s2;
+    }
+  } else {
+    unsigned long long br = 0;
+    for (int l = 0; l < IL; ++l) {
+      const unsigned long long d = acc[l] - t[l];
+      const unsigned long long d2 = d - br;
+      br = (acc[l] < t[l] ? 1ull : 0ull) + (d < br ? 1ull : 0ull);
+      acc[l] = d2;
+    }
+  }
+  return true;
+}
+
+// exact sign of sum_i sign_i * prod_j f[i*k + j]; returns 2 when the integer
+// range does not suffice (caller falls back to expansions)
+static __device__ __noinline__ int int_sign(const double* f, const double* sg, int nmono, int k) {
+  int emin = 1 << 30;
+  for (int i = 0; i < nmono; ++i) {
+    int e = 0;
+    bool zero = false;
+    for (int j = 0; j < k; ++j) {
+      const double x = f[i * k + j];
+      if (x == 0.0) { zero = true; break; }
+      unsigned long long m;
+      int ej;
+      bool ng;
+      if (!split_dbl(x, m, ej, ng)) return 2;
+      e += ej;
+    }
+    if (!zero && e < emin) emin = e;
+  }
+  if (emin == (1 << 30)) return 0;
+  unsigned long long acc[IL];
+  for (int l = 0; l < IL; ++l) acc[l] = 0;
+  for (int i = 0; i < nmono; ++i) {
+    bool zero = false;
+    for (int j = 0; j < k; ++j) zero |= f[i * k + j] == 0.0;
+    if (zero) continue;
+    Mono mo;
+    if (!mono_prod(f + i * k, k, sg[i], mo)) return 2;
+    if (!acc_add(acc, mo, mo.e - emin)) return 2;
+  }
+  if ((long long)acc[IL - 1] < 0) return -1;
+  for (int l = 0; l < IL; ++l)
+    if (acc[l]) return 1;
+  return 0;
+}
+
 // ---------------------------------------------------------------- orient
 static __device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
                                          double cy) {
   // (ax-cx)(by-cy) - (ay-cy)(bx-cx) with each difference as an exact pair
+  atomicAdd(&g_diag[0], 1ull);
   double acxh, acxl, acyh, acyl, bcxh, bcxl, bcyh, bcyl;
   two_diff(ax, cx, acxh, acxl);
   two_diff(ay, cy, acyh, acyl);
   two_diff(bx, cx, bcxh, bcxl);
   two_diff(by, cy, bcyh, bcyl);
+  if (acxl == 0.0 && acyl == 0.0 && bcxl == 0.0 && bcyl == 0.0) {
+    const double f[4] = {acxh, bcyh, acyh, bcxh};
+    const double sg[2] = {1.0, -1.0};
+    const int r = int_sign(f, sg, 2, 2);
+    if (r != 2) return r;
+  }
   Expansion<24> X;
   add_prod2(X, acxh, acxl, bcyh, bcyl, 1.0);
   add_prod2(X, acyh, acyl, bcxh, bcxl, -1.0);
@@ -131,8 +269,13 @@ static __device__ __noinline__ int orient_exact(double ax, double ay, double bx,
 
 __device__ __forceinline__ int orient(double ax, double ay, double bx, double by, double cx,
                                       double cy) {
-  double l = __dmul_rn(__dsub_rn(ax, cx), __dsub_rn(by, cy));
-  double r = __dmul_rn(__dsub_rn(ay, cy), __dsub_rn(bx, cx));
+  const double d1 = __dsub_rn(ax, cx), d2 = __dsub_rn(by, cy);
+  const double d3 = __dsub_rn(ay, cy), d4 = __dsub_rn(bx, cx);
+  // a difference of two doubles rounds to zero only when they are equal, so a
+  // zero factor on each side makes the determinant exactly zero
+  if ((d1 == 0.0 || d2 == 0.0) && (d3 == 0.0 || d4 == 0.0)) return 0;
+  double l = __dmul_rn(d1, d2);
+  double r = __dmul_rn(d3, d4);
   double det = __dsub_rn(l, r);
   double perm = __dadd_rn(fabs(l), fabs(r));
   // three roundings in each product, one in the difference: |err| <= 4u perm + O(u^2)
@@ -153,6 +296,8 @@ __device__ __forceinline__ int orient(double2 a, double2 b, double2 c) {
 // with every difference relative to d.
 static __device__ __noinline__ int incircle_exact(double ax, double ay, double bx, double by, double cx,
                                            double cy, double dx, double dy) {
+  const long long c0 = clock64();
+  atomicAdd(&g_diag[1], 1ull);
   double h[6], l[6];   // adx ady bdx bdy cdx cdy as exact pairs
   two_diff(ax, dx, h[0], l[0]);
   two_diff(ay, dy, h[1], l[1]);
@@ -160,6 +305,29 @@ static __device__ __noinline__ int incircle_exact(double ax, double ay, double b
   two_diff(by, dy, h[3], l[3]);
   two_diff(cx, dx, h[4], l[4]);
   two_diff(cy, dy, h[5], l[5]);
+  if (l[0] != 0.0 || l[1] != 0.0 || l[2] != 0.0 || l[3] != 0.0 || l[4] != 0.0 || l[5] != 0.0) {
+    atomicAdd(&g_diag[4], 1ull);
+  } else {
+    // sum over the three points t (q, r the other two) of
+    // (x_t^2 + y_t^2) (x_q y_r - x_r y_q): 12 monomials of degree 4
+    double f[48], sg[12];
+    int n = 0;
+    for (int t = 0; t < 3; ++t) {
+      const int q = (t + 1) % 3, r = (t + 2) % 3;
+      for (int c = 0; c < 2; ++c) {
+        const double a = h[2 * t + c];
+        f[4 * n] = a; f[4 * n + 1] = a; f[4 * n + 2] = h[2 * q]; f[4 * n + 3] = h[2 * r + 1];
+        sg[n++] = 1.0;
+        f[4 * n] = a; f[4 * n + 1] = a; f[4 * n + 2] = h[2 * r]; f[4 * n + 3] = h[2 * q + 1];
+        sg[n++] = -1.0;
+      }
+    }
+    const int rr = int_sign(f, sg, n, 4);
+    if (rr != 2) {
+      atomicMax(&g_diag[8], (unsigned long long)(clock64() - c0));
+      return rr;
+    }
+  }
   Expansion<64> X;
   for (int t = 0; t < 3; ++t) {
     const int p = 2 * t, q = 2 * ((t + 1) % 3), r = 2 * ((t + 2) % 3);
@@ -198,6 +366,7 @@ static __device__ __noinline__ int incircle_exact(double ax, double ay, double b
       }
     }
   }
+  atomicMax(&g_diag[8], (unsigned long long)(clock64() - c0));
   return X.sign();
 }
 
@@ -238,6 +407,7 @@ GDP_HD bool lex_less(double ax, double ay, double bx, double by) {
 // C_c = +orient(a,b,d), C_d = -orient(a,b,c).  Ranking by coordinates (not by
 // vertex number) makes the result independent of how vertices are numbered.
 static __device__ __noinline__ int incircle_sos_tie(double2 a, double2 b, double2 c, double2 d) {
+  atomicAdd(&g_diag[2], 1ull);
   double2 P[4] = {a, b, c, d};
   int ord[4] = {0, 1, 2, 3};
   for (int i = 1; i < 4; ++i) {       // decreasing lexicographic order
@@ -269,11 +439,18 @@ __device__ __forceinline__ int incircle(double2 a, double2 b, double2 c, double2
 // ---------------------------------------------------------------- diametral circle
 static __device__ __noinline__ int dot_exact(double ax, double ay, double bx, double by, double px,
                                       double py) {
+  atomicAdd(&g_diag[3], 1ull);
   double axh, axl, ayh, ayl, bxh, bxl, byh, byl;
   two_diff(ax, px, axh, axl);
   two_diff(ay, py, ayh, ayl);
   two_diff(bx, px, bxh, bxl);
   two_diff(by, py, byh, byl);
+  if (axl == 0.0 && ayl == 0.0 && bxl == 0.0 && byl == 0.0) {
+    const double f[4] = {axh, bxh, ayh, byh};
+    const double sg[2] = {1.0, 1.0};
+    const int r = int_sign(f, sg, 2, 2);
+    if (r != 2) return r;
+  }
   Expansion<24> X;
   add_prod2(X, axh, axl, bxh, bxl, 1.0);
   add_prod2(X, ayh, ayl, byh, byl, 1.0);
@@ -292,6 +469,98 @@ __device__ __forceinline__ int dot_sign(double2 a, double2 b, double2 p) {
     if (-s > bound) return -1;
   }
   return dot_exact(a.x, a.y, b.x, b.y, p.x, p.y);
+}
+
+// ---------------------------------------------------------------- FP32 filter stage
+// GB300 executes FP64 at 1/64 of the FP32 rate, so every predicate first runs
+// in FP32 on float copies of the coordinates, translated to the mesh's
+// bounding-box centre: f = fl32(fl64(x - origin)).  Each float coordinate is
+// within v*M*(1+3v) of the exact translated value (v = 2^-24, M the largest
+// |float coordinate| of the test), so each float difference is within
+// E = 4.001 v M of the exact difference.  The bounds below add that input
+// error to the rounding error of the float evaluation; when the float value
+// cannot decide, the FP64 filter and then exact arithmetic do.
+constexpr float kV = 5.9604645e-8f;   // 2^-24
+
+struct P2 {
+  double2 d;   // exact (FP64) coordinates
+  float2 f;    // translated float copy
+};
+
+__device__ __forceinline__ float fmax6(float a, float b, float c, float d, float e, float g) {
+  return fmaxf(fmaxf(fmaxf(a, b), fmaxf(c, d)), fmaxf(e, g));
+}
+
+// sign of (ax-cx)(by-cy) - (ay-cy)(bx-cx) when certain, else 0
+__device__ __forceinline__ int orient_f32(float2 a, float2 b, float2 c) {
+  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(c.x), fabsf(c.y));
+  if (!(M < 1e8f) || M < 1e-15f) return 0;
+  const float d1 = __fsub_rn(a.x, c.x), d2 = __fsub_rn(b.y, c.y);
+  const float d3 = __fsub_rn(a.y, c.y), d4 = __fsub_rn(b.x, c.x);
+  const float l = __fmul_rn(d1, d2), r = __fmul_rn(d3, d4);
+  const float det = __fsub_rn(l, r);
+  const float E = 4.001f * kV * M;
+  // |det - exact| <= E (|d1|+|d2|+|d3|+|d4| + 2E) + (2v + v^2)(|l| + |r|)
+  const float err = (E * (fabsf(d1) + fabsf(d2) + fabsf(d3) + fabsf(d4) + 2.0f * E) +
+                     2.0001f * kV * (fabsf(l) + fabsf(r))) * 1.001f + 1e-37f;
+  return det > err ? 1 : (-det > err ? -1 : 0);
+}
+
+// sign of the incircle determinant (same evaluation order as the FP64 filter)
+__device__ __forceinline__ int incircle_f32(float2 a, float2 b, float2 c, float2 d) {
+  const float M = fmaxf(fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(c.x), fabsf(c.y)),
+                        fmaxf(fabsf(d.x), fabsf(d.y)));
+  if (!(M < 1e7f) || M < 1e-7f) return 0;
+  const float adx = __fsub_rn(a.x, d.x), ady = __fsub_rn(a.y, d.y);
+  const float bdx = __fsub_rn(b.x, d.x), bdy = __fsub_rn(b.y, d.y);
+  const float cdx = __fsub_rn(c.x, d.x), cdy = __fsub_rn(c.y, d.y);
+  const float p1 = __fmul_rn(bdx, cdy), p2 = __fmul_rn(cdx, bdy);
+  const float p3 = __fmul_rn(cdx, ady), p4 = __fmul_rn(adx, cdy);
+  const float p5 = __fmul_rn(adx, bdy), p6 = __fmul_rn(bdx, ady);
+  const float al = __fadd_rn(__fmul_rn(adx, adx), __fmul_rn(ady, ady));
+  const float bl = __fadd_rn(__fmul_rn(bdx, bdx), __fmul_rn(bdy, bdy));
+  const float cl = __fadd_rn(__fmul_rn(cdx, cdx), __fmul_rn(cdy, cdy));
+  const float det = __fadd_rn(__fadd_rn(__fmul_rn(al, __fsub_rn(p1, p2)), __fmul_rn(bl, __fsub_rn(p3, p4))),
+                              __fmul_rn(cl, __fsub_rn(p5, p6)));
+  const float perm = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(p1), fabsf(p2)), al),
+                                         __fmul_rn(__fadd_rn(fabsf(p3), fabsf(p4)), bl)),
+                               __fmul_rn(__fadd_rn(fabsf(p5), fabsf(p6)), cl));
+  const float L = fmax6(fabsf(adx), fabsf(ady), fabsf(bdx), fabsf(bdy), fabsf(cdx), fabsf(cdy));
+  const float E = 4.001f * kV * M;
+  const float LE = L + E;
+  // input error: 12 degree-4 monomials, each off by <= (L+E)^4 - L^4 <= 4E(L+E)^3;
+  // rounding of the float evaluation: <= 11v perm to first order
+  const float err = (48.0f * E * LE * LE * LE + 12.5f * kV * perm) * 1.001f + 1e-37f;
+  return det > err ? 1 : (-det > err ? -1 : 0);
+}
+
+// sign of (a-p).(b-p) when certain, else 0
+__device__ __forceinline__ int dot_f32(float2 a, float2 b, float2 p) {
+  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(p.x), fabsf(p.y));
+  if (!(M < 1e8f) || M < 1e-15f) return 0;
+  const float d1 = __fsub_rn(a.x, p.x), d2 = __fsub_rn(b.x, p.x);
+  const float d3 = __fsub_rn(a.y, p.y), d4 = __fsub_rn(b.y, p.y);
+  const float t1 = __fmul_rn(d1, d2), t2 = __fmul_rn(d3, d4);
+  const float s = __fadd_rn(t1, t2);
+  const float E = 4.001f * kV * M;
+  const float err = (E * (fabsf(d1) + fabsf(d2) + fabsf(d3) + fabsf(d4) + 2.0f * E) +
+                     2.0001f * kV * (fabsf(t1) + fabsf(t2))) * 1.001f + 1e-37f;
+  return s > err ? 1 : (-s > err ? -1 : 0);
+}
+
+__device__ __forceinline__ int orient(const P2& a, const P2& b, const P2& c) {
+  const int s = orient_f32(a.f, b.f, c.f);
+  return s ? s : orient(a.d, b.d, c.d);
+}
+
+__device__ __forceinline__ int dot_sign(const P2& a, const P2& b, const P2& p) {
+  const int s = dot_f32(a.f, b.f, p.f);
+  return s ? s : dot_sign(a.d, b.d, p.d);
+}
+
+__device__ __forceinline__ int incircle(const P2& a, const P2& b, const P2& c, const P2& d) {
+  const int s = incircle_f32(a.f, b.f, c.f, d.f);
+  return s ? s : incircle(a.d, b.d, c.d, d.d);
 }
 
 // ---------------------------------------------------------------- fixed-order FP64 geometry
@@ -327,6 +596,43 @@ __device__ __forceinline__ bool is_bad(const TriTerms& t, double B2) {
   double lhs = __dmul_rn(__dmul_rn(t.la, t.lb), t.lc);
   double rhs = __dmul_rn(__dmul_rn(__dmul_rn(4.0, B2), lmin), __dmul_rn(t.cr, t.cr));
   return lhs > rhs;
+}
+
+// FP32 pre-check of is_bad: +1 when the FP64 formula above surely says bad,
+// -1 when it surely says good, 0 when the float intervals overlap.  Interval
+// bounds for the exact squared lengths and doubled area come from the float
+// differences (input error E each, as in the predicates); the FP64 formula is
+// within ~20 u of the exact quantities, far inside the float margins.
+__device__ __forceinline__ int bad_f32(float2 a, float2 b, float2 c, float B2f) {
+  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(c.x), fabsf(c.y));
+  if (!(M < 1e7f) || M < 1e-6f) return 0;
+  const float E = 4.001f * kV * M;
+  const float x1 = __fsub_rn(b.x, a.x), y1 = __fsub_rn(b.y, a.y);
+  const float x2 = __fsub_rn(c.x, a.x), y2 = __fsub_rn(c.y, a.y);
+  const float x3 = __fsub_rn(c.x, b.x), y3 = __fsub_rn(c.y, b.y);
+  const float la = __fadd_rn(__fmul_rn(x1, x1), __fmul_rn(y1, y1));
+  const float lb = __fadd_rn(__fmul_rn(x2, x2), __fmul_rn(y2, y2));
+  const float lc = __fadd_rn(__fmul_rn(x3, x3), __fmul_rn(y3, y3));
+  const float ea = E * (2.0f * (fabsf(x1) + fabsf(y1)) + 2.0f * E) + 2.001f * kV * la;
+  const float eb = E * (2.0f * (fabsf(x2) + fabsf(y2)) + 2.0f * E) + 2.001f * kV * lb;
+  const float ec = E * (2.0f * (fabsf(x3) + fabsf(y3)) + 2.0f * E) + 2.001f * kV * lc;
+  const float t1 = __fmul_rn(x1, y2), t2 = __fmul_rn(y1, x2);
+  const float cr = fabsf(__fsub_rn(t1, t2));
+  const float ecr = E * (fabsf(x1) + fabsf(y2) + fabsf(y1) + fabsf(x2) + 2.0f * E) +
+                    2.001f * kV * (fabsf(t1) + fabsf(t2));
+  if (!(la > ea && lb > eb && lc > ec && cr > ecr)) return 0;
+  const float lo = 1.0f - 16.0f * kV, hi = 1.0f + 16.0f * kV;
+  const float lhs_lo = (la - ea) * (lb - eb) * (lc - ec) * lo;
+  const float lhs_hi = (la + ea) * (lb + eb) * (lc + ec) * hi;
+  const float mn_lo = fminf(fminf(la - ea, lb - eb), lc - ec);
+  const float mn_hi = fminf(fminf(la + ea, lb + eb), lc + ec);
+  const float cl = cr - ecr, ch = cr + ecr;
+  const float rhs_lo = 4.0f * B2f * mn_lo * cl * cl * lo;
+  const float rhs_hi = 4.0f * B2f * mn_hi * ch * ch * hi;
+  if (!(lhs_hi < 1e37f && rhs_hi < 1e37f && lhs_lo > 1e-36f && rhs_lo > 1e-36f)) return 0;
+  if (lhs_lo > rhs_hi) return 1;
+  if (lhs_hi < rhs_lo) return -1;
+  return 0;
 }
 
 __device__ __forceinline__ double2 circumcenter(const TriTerms& t) {
