@@ -122,6 +122,13 @@ int gdp_mesh_split_subsegments(gdp_mesh* mesh, const double* abxy, int64_t n);
 int gdp_mesh_scan(gdp_mesh* mesh, double B, int32_t* kind, int32_t* verts, double* pt,
                   uint32_t* meas, int64_t cap, int64_t* count);
 
+/* Consistency of the device mesh (a test hook): counts[0..4] receive the
+ * number of neighbour links that are not mutual, links whose shared edge does
+ * not match, subsegment flags that differ across an edge, triangles that are
+ * not strictly CCW (exact orient), and hull edges that are not subsegments.
+ * All zero for a valid mesh. */
+int gdp_mesh_check(gdp_mesh* mesh, int64_t counts[5]);
+
 /* Statistics of the last create/refine. */
 int gdp_mesh_stats(gdp_mesh* mesh, gdp_stats* stats);
 

@@ -30,6 +30,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
            "-I", os.path.join(ROOT, "include"), "-o", tmp, *srcs]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
+    extra = os.environ.get("GDP_NVCC_FLAGS", "").split()
+    if extra:
+        cmd[1:1] = extra
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -166,6 +166,33 @@ static void print_diag(const char* where) {
   cudaMemcpyToSymbol(g_diag, z, sizeof(z));
 }
 
+// stage-by-stage consistency report (GDP_TRACE)
+static void trace_check(const Pool& P, cudaStream_t st, int G, const char* where) {
+  if (!std::getenv("GDP_TRACE")) return;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 10 * sizeof(unsigned long long)) != cudaSuccess) return;
+  cudaMemsetAsync(d, 0, 10 * sizeof(unsigned long long), st);
+  k_check<<<G, BS, 0, st>>>(P, d);
+  unsigned long long c[10] = {};
+  cudaMemcpyAsync(c, d, sizeof(c), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  cudaFree(d);
+  std::fprintf(stderr, "[check %s] not_mutual %llu edge_mismatch %llu flag_mismatch %llu not_ccw %llu open %llu\n",
+               where, c[0], c[1], c[2], c[3], c[4]);
+  for (unsigned long long k = 0; k < c[5] && k < 4; ++k) {
+    const int t = (int)(c[6 + k] >> 2), e = (int)(c[6 + k] & 3);
+    int4 T4, N4, T2, N2;
+    cudaMemcpy(&T4, P.T + t, sizeof(int4), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&N4, P.N + t, sizeof(int4), cudaMemcpyDeviceToHost);
+    const int r = e == 0 ? N4.x : (e == 1 ? N4.y : N4.z);
+    cudaMemcpy(&T2, P.T + (r >> 2), sizeof(int4), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&N2, P.N + (r >> 2), sizeof(int4), cudaMemcpyDeviceToHost);
+    std::fprintf(stderr, "  bad link t=%d e=%d T=(%d %d %d w=%x) N=(%d:%d %d:%d %d:%d) -> t2=%d e2=%d T2=(%d %d %d w=%x) N2=(%d:%d %d:%d %d:%d)\n",
+                 t, e, T4.x, T4.y, T4.z, T4.w, N4.x >> 2, N4.x & 3, N4.y >> 2, N4.y & 3, N4.z >> 2, N4.z & 3,
+                 r >> 2, r & 3, T2.x, T2.y, T2.z, T2.w, N2.x >> 2, N2.x & 3, N2.y >> 2, N2.y & 3, N2.z >> 2, N2.z & 3);
+  }
+}
+
 // ---------------------------------------------------------------- the pool
 struct PoolHost {
   cudaStream_t stream = nullptr;
@@ -321,7 +348,6 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   P.n_slots = (int)tb;
   P.n_verts = (int)vb;
   P.cap_cand = (int)std::min<long long>(std::max<long long>(tb / 4, 65536), 1 << 23);
-  P.cap_segq = (int)std::min<long long>(std::max<long long>(sb, 1), 65536);
   int st;
 #define AL(ptr, n, fill) \
   if ((st = alloc(&(ptr), (size_t)(n), fill)) != GDP_OK) return st;
@@ -448,39 +474,76 @@ int PoolHost::build_cdt() {
   int st = insert_rounds(0, &rounds);
   if (st != GDP_OK) return st;
   stats.cdt_rounds = rounds;
-  // segment recovery
+  trace_check(P, stream, G, "points");
+  // segment recovery: short segments with a small work space per segment,
+  // then the few long ones (e.g. boundary edges crossed by every point of the
+  // outer layer) with a large one
   int st2;
-  int2* work = nullptr;
+  int* segq2 = nullptr;
   if ((st2 = alloc(&P.segq, std::max<long long>(tot_seg, 1))) != GDP_OK) return st2;
-  if ((st2 = alloc(&P.segq2, std::max<long long>(tot_seg, 1))) != GDP_OK) return st2;
-  if ((st2 = alloc(&P.reg, (size_t)P.cap_segq * KMAX)) != GDP_OK) return st2;
-  if ((st2 = alloc(&P.reg_n, (size_t)P.cap_segq)) != GDP_OK) return st2;
-  if ((st2 = alloc(&work, (size_t)P.cap_segq * KMAX)) != GDP_OK) return st2;
+  if ((st2 = alloc(&segq2, std::max<long long>(tot_seg, 1))) != GDP_OK) return st2;
   if ((st2 = alloc(&P.segmark, (size_t)P.n_slots)) != GDP_OK) return st2;
+  // three tiers of per-segment work space: all segments at once with room for
+  // 64 crossed edges, then up to 16384 segments with 1024, then 8 with 32768
+  constexpr int NT = 3;
+  SegWork W[NT];
+  const int kcap[NT] = {64, 1024, 1 << 15};
+  const int lcap[NT] = {(int)std::max<long long>(tot_seg, 1),
+                        (int)std::min<long long>(std::max<long long>(tot_seg, 1), 16384), 8};
+  for (int tier = 0; tier < NT; ++tier) {
+    const size_t n = lcap[tier], K = kcap[tier];
+    W[tier].kcap = (int)K;
+    if ((st2 = alloc(&W[tier].R, n * (K + 1))) != GDP_OK) return st2;
+    if ((st2 = alloc(&W[tier].U, n * (K + 2))) != GDP_OK) return st2;
+    if ((st2 = alloc(&W[tier].L, n * (K + 2))) != GDP_OK) return st2;
+    if ((st2 = alloc(&W[tier].UR, n * (K + 2))) != GDP_OK) return st2;
+    if ((st2 = alloc(&W[tier].LR, n * (K + 2))) != GDP_OK) return st2;
+    if ((st2 = alloc(&W[tier].ST, n * (K + 2))) != GDP_OK) return st2;
+    if ((st2 = alloc(&W[tier].NR, 2 * n * (K + 2))) != GDP_OK) return st2;
+    if ((st2 = alloc(&W[tier].state, n)) != GDP_OK) return st2;
+  }
   if (tot_seg) {
     LAUNCH(*this, k_iota, G, P.segq, (int)tot_seg);
-    if (set_ctrl_field(offsetof(Ctrl, n_segs), (int)tot_seg) != GDP_OK) return GDP_ERR_CUDA;
-    int round = 0, last = (int)tot_seg, stall = 0;
-    for (;;) {
-      LAUNCH(*this, k_seg_find, G, P, round);
-      LAUNCH(*this, k_seg_apply, G, P, round, work);
-      LAUNCH(*this, k_seg_keep_count, G, P);
-      LAUNCH(*this, k_seg_keep_write, G, P);
+    int n = (int)tot_seg, tier = 0, round = 0, stall = 0;
+    while (n > 0) {
+      SegWork w = W[tier];
+      w.list = P.segq;
+      w.n_list = std::min(n, lcap[tier]);
+      if (std::getenv("GDP_SEG_SERIAL")) w.n_list = 1;
+      LAUNCH(*this, k_seg_find, G, P, w, round);
+      LAUNCH(*this, k_seg_apply, G, P, w, round);
+      LAUNCH(*this, k_seg_keep_count, G, P, w, n);
+      LAUNCH(*this, k_seg_keep_write, G, P, w, n, segq2);
       CK(cudaGetLastError());
-      std::swap(P.segq, P.segq2);
+      std::swap(P.segq, segq2);
       if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
       if (hctrl->err) return hctrl->err;
-      if (hctrl->n_segs == 0) break;
-      ++round;
-      if (hctrl->n_segs == last) {
-        if (++stall > 64) return GDP_ERR_INTERNAL;
-      } else {
-        stall = 0;
+      const int n2 = hctrl->n_segs;
+      if (std::getenv("GDP_TRACE")) {
+        std::fprintf(stderr, "seg round %d tier %d: %d -> %d (tier-handled pending %d)\n", round, tier, n, n2,
+                     hctrl->changed);
+        trace_check(P, stream, G, "segment round");
       }
-      last = hctrl->n_segs;
-      if (round > 60000) return GDP_ERR_INTERNAL;
+      if (hctrl->changed == 0 && n2 > 0) {
+        // only segments too long for this tier are left
+        if (++tier == NT) return GDP_ERR_CAPACITY;
+      }
+      stall = (n2 == n) ? stall + 1 : 0;
+      if (stall > 64 || ++round > 60000) return GDP_ERR_INTERNAL;
+      n = n2;
     }
   }
+  for (int tier = 0; tier < NT; ++tier) {
+    release(W[tier].R);
+    release(W[tier].U);
+    release(W[tier].L);
+    release(W[tier].UR);
+    release(W[tier].LR);
+    release(W[tier].ST);
+    release(W[tier].NR);
+    release(W[tier].state);
+  }
+  release(segq2);
   // exterior
   if ((st2 = alloc(&P.ext, (size_t)P.n_slots)) != GDP_OK) return st2;
   if ((st2 = alloc(&P.remap, (size_t)P.n_slots + 1)) != GDP_OK) return st2;
@@ -509,15 +572,11 @@ int PoolHost::build_cdt() {
   stats.cdt_ms = ms;
   release(T2);
   release(N2);
-  release(work);
   release(P.segq);
-  release(P.segq2);
-  release(P.reg);
-  release(P.reg_n);
   release(P.segmark);
   release(P.ext);
   release(P.remap);
-  P.segq = P.segq2 = P.reg = P.reg_n = P.remap = nullptr;
+  P.segq = P.remap = nullptr;
   P.segmark = nullptr;
   P.ext = nullptr;
   if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
@@ -932,6 +991,21 @@ int gdp_mesh_scan(gdp_mesh* g, double B, int32_t* kind, int32_t* verts, double* 
   h.release(dp);
   h.release(dm);
   h.release(dc);
+  return GDP_OK;
+}
+
+int gdp_mesh_check(gdp_mesh* g, int64_t counts[5]) {
+  if (!g || !counts) return GDP_ERR_INPUT;
+  PoolHost& h = g->h;
+  unsigned long long* d = nullptr;
+  int st;
+  if ((st = h.alloc(&d, 5)) != GDP_OK) return st;
+  LAUNCH(h, k_check, h.G, h.P, d);
+  unsigned long long c[5];
+  CK(cudaMemcpyAsync(c, d, sizeof(c), cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  h.release(d);
+  for (int i = 0; i < 5; ++i) counts[i] = (int64_t)c[i];
   return GDP_OK;
 }
 

@@ -203,6 +203,39 @@ __global__ void __launch_bounds__(BS) k_cdt_keep_write(Pool P) {
 }
 
 // ---------------------------------------------------------------- segment recovery
+// A missing segment ab is recovered by deleting the triangles it crosses and
+// re-triangulating the two pseudo-polygons on its sides (upper chain left of
+// a->b, lower chain right of it): for a base edge the chain vertex whose
+// circle with the base holds no other chain vertex (exact incircle) forms a
+// triangle, and both sides recurse.  The result is the constrained Delaunay
+// triangulation of the region, so no flips are needed afterwards.  The region
+// and its one-ring are claimed with 64-bit atomicMax marks so that segments
+// whose regions touch are recovered in different rounds.
+//
+// Per-segment work space (capacity K crossed edges): crossed triangles
+// R[K+1]; upper and lower chains U[K+2], L[K+2] (vertex ids, a first, b
+// last); the outside neighbour and subsegment bit of each chain edge UR[K+2],
+// LR[K+2] (as int2); an explicit recursion stack ST[K+2] (int4); NR[2(K+2)].
+//
+// A chain can run out and back along one edge: a vertex v between the
+// segment and a chain vertex x makes the boundary ..., x, v, x, ...  Such
+// twin edges (the same edge seen from both sides, possibly nested like
+// parentheses) are interior to the new triangulation: their two new
+// triangles are linked to each other, not to the old crossed triangles.
+struct SegWork {
+  int kcap;             // crossed edges that fit
+  int* R;
+  int* U;
+  int* L;
+  int2* UR;
+  int2* LR;
+  int4* ST;
+  int* NR;              // 2 (K+2): new triangle refs of twin chain edges (upper, lower)
+  int* list;            // segment ids to process
+  int n_list;           // entries in list (host-set)
+  int* state;           // per list entry: >= 0 crossings, -1 done, -2 error, -3 too long
+};
+
 __device__ __forceinline__ int idx_of(const int4& T4, int v) {
   return T4.x == v ? 0 : (T4.y == v ? 1 : (T4.z == v ? 2 : -1));
 }
@@ -211,60 +244,30 @@ __device__ __forceinline__ void set_nb(const Pool& P, int ref, int val) {
   if (ref >= 0) *comp_ptr(&P.N[ref >> 2], ref & 3) = val;
 }
 
-// Flip edge e1 of t1 (shared with t2): quad p1,u,o,v (CCW) gets the diagonal p1-o.
-// t1 = (p1,u,v) -> (p1,u,o);  t2 = (o,v,u) -> (p1,o,v).  Outside neighbours are
-// re-pointed; subsegment bits move with their edges.
-__device__ void flip(const Pool& P, int t1, int e1) {
-  const int4 A = P.T[t1], NA = P.N[t1];
-  const int ref = comp(NA, e1);
-  const int t2 = ref >> 2, e2 = ref & 3;
-  const int4 B = P.T[t2], NB = P.N[t2];
-  const int p1 = comp(A, e1), u = comp(A, mod3(e1 + 1)), v = comp(A, mod3(e1 + 2));
-  const int o = comp(B, e2);
-  const int m = A.w >> 4;
-  // outer edges: (p1,u) = A opp v [e1+2]; (v,p1) = A opp u [e1+1];
-  //              (u,o)  = B opp v [e2+1]; (o,v)  = B opp u [e2+2]
-  const int r_pu = comp(NA, mod3(e1 + 2)), r_vp = comp(NA, mod3(e1 + 1));
-  const int r_uo = comp(NB, mod3(e2 + 1)), r_ov = comp(NB, mod3(e2 + 2));
-  const int c_pu = (A.w >> mod3(e1 + 2)) & 1, c_vp = (A.w >> mod3(e1 + 1)) & 1;
-  const int c_uo = (B.w >> mod3(e2 + 1)) & 1, c_ov = (B.w >> mod3(e2 + 2)) & 1;
-  // t1' = (p1, u, o): e0 = (u,o), e1 = (o,p1) -> t2' e2, e2 = (p1,u)
-  // t2' = (p1, o, v): e0 = (o,v), e1 = (v,p1), e2 = (p1,o) -> t1' e1
-  P.T[t1] = make_int4(p1, u, o, (m << 4) | c_uo | (c_pu << 2));
-  P.N[t1] = make_int4(r_uo, (t2 << 2) | 2, r_pu, 0);
-  P.T[t2] = make_int4(p1, o, v, (m << 4) | c_ov | (c_vp << 1));
-  P.N[t2] = make_int4(r_ov, r_vp, (t1 << 2) | 1, 0);
-  set_nb(P, r_uo, (t1 << 2) | 0);
-  set_nb(P, r_pu, (t1 << 2) | 2);
-  set_nb(P, r_ov, (t2 << 2) | 0);
-  set_nb(P, r_vp, (t2 << 2) | 1);
-}
-
-__device__ __forceinline__ bool crosses_seg(const Pool& P, int a, int b, int u, int v) {
-  if (u == a || u == b || v == a || v == b) return false;
-  const P2 A = pt(P, a), B = pt(P, b), U = pt(P, u), W = pt(P, v);
-  return orient(A, B, U) * orient(A, B, W) < 0 && orient(U, W, A) * orient(U, W, B) < 0;
-}
-
+// s is the segment's id within its mesh, so that a mesh's segments compete
+// the same way alone and in a batch
 __device__ __forceinline__ unsigned long long seg_key(int round, int s, int k) {
   return ((unsigned long long)(round + 1) << 48) |
          ((unsigned long long)(hash32((uint32_t)s) & 0xffffu) << 32) | (unsigned)k;
 }
 
-// reg_n[k]: > 0 crossed triangles collected; -1 recovered; -2 error
-__global__ void __launch_bounds__(BS) k_seg_find(Pool P, int round) {
-  const int n = min(P.ctrl->n_segs, P.cap_segq);
+// walk a -> b, collecting the crossed triangles and both chains; claim the
+// region and its one-ring
+__global__ void __launch_bounds__(BS) k_seg_find(Pool P, SegWork W, int round) {
+  const int n = W.n_list;
+  const int K = W.kcap;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int k = gt; k < n; k += gs) {
-    const int s = P.segq[k];
+    const int s = W.list[k];
     const int a = P.seg[s].x, b = P.seg[s].y;
     if (a == b) {   // rejected at input (its mesh carries the status)
-      P.reg_n[k] = -1;
+      W.state[k] = -1;
       continue;
     }
     int t = P.vtri[a];
     const int m = P.T[t].w >> 4;
     int start = -1, ia = -1, status = 0;
+    const P2 A = pt(P, a), B = pt(P, b);
     for (int it = 0; it < 4096 && start < 0 && status == 0; ++it) {
       const int4 T4 = P.T[t];
       const int i = idx_of(T4, a);
@@ -278,9 +281,8 @@ __global__ void __launch_bounds__(BS) k_seg_find(Pool P, int round) {
         status = -1;
         break;
       }
-      const P2 A = pt(P, a), B = pt(P, b);
       const int o1 = orient(A, pt(P, u), B), o2 = orient(A, pt(P, w), B);
-      if (o1 == 0 && dot_sign(pt(P, u), B, A) > 0) { status = S_INPUT; break; }
+      if (o1 == 0 && dot_sign(A, B, pt(P, u)) < 0) { status = S_INPUT; break; }
       if (o1 > 0 && o2 < 0) { start = t; ia = i; break; }
       const int nb = comp(P.N[t], mod3(i + 2));   // clockwise: across (a, u)
       if (nb < 0) { status = S_INTERNAL; break; }
@@ -291,46 +293,77 @@ __global__ void __launch_bounds__(BS) k_seg_find(Pool P, int round) {
       if (status > 0) {
         P.mi[m].status = status;
         set_err(P.ctrl, status);
-        P.reg_n[k] = -2;
+        W.state[k] = -2;
       } else {
-        P.reg_n[k] = -1;
+        W.state[k] = -1;
       }
       continue;
     }
-    int* R = P.reg + (size_t)k * KMAX;
-    int cnt = 0;
-    R[cnt++] = start;
+    int* R = W.R + (size_t)k * (K + 1);
+    int* U = W.U + (size_t)k * (K + 2);
+    int* L = W.L + (size_t)k * (K + 2);
+    int2* UR = W.UR + (size_t)k * (K + 2);
+    int2* LR = W.LR + (size_t)k * (K + 2);
     const int4 S4 = P.T[start];
-    int l = comp(S4, mod3(ia + 2)), r = comp(S4, mod3(ia + 1));
-    int ref = comp(P.N[start], ia);
-    if ((S4.w >> ia) & 1) status = S_INPUT;
-    for (; status == 0;) {
+    const int4 SN = P.N[start];
+    // start = (a, r, l): lower boundary a->r (opposite l), upper boundary l->a (opposite r)
+    int r = comp(S4, mod3(ia + 1)), l = comp(S4, mod3(ia + 2));
+    int cnt = 0, nu = 0, nl = 0;
+    R[cnt++] = start;
+    U[nu++] = a; L[nl++] = a;
+    UR[0] = make_int2(comp(SN, mod3(ia + 1)), (S4.w >> mod3(ia + 1)) & 1);
+    LR[0] = make_int2(comp(SN, mod3(ia + 2)), (S4.w >> mod3(ia + 2)) & 1);
+    U[nu++] = l; L[nl++] = r;
+    int ref = comp(SN, ia);
+    if ((S4.w >> ia) & 1) status = S_INPUT;   // crosses a recovered segment
+    while (status == 0) {
       if (ref < 0) { status = S_INTERNAL; break; }
-      if (cnt == KMAX) { status = S_CAPACITY; break; }
+      if (cnt == K + 1) { status = 1000; break; }   // too long for this tier
       const int tn = ref >> 2, ee = ref & 3;
-      if ((P.T[tn].w >> ee) & 1) { status = S_INPUT; break; }   // crosses a recovered segment
-      R[cnt++] = tn;
       const int4 T4 = P.T[tn];
+      const int4 N4 = P.N[tn];
+      if ((T4.w >> ee) & 1) { status = S_INPUT; break; }
+      R[cnt++] = tn;
+      // tn = (z, l, r) with entry edge l->r opposite z
       const int z = comp(T4, ee);
-      if (z == b) break;
-      const int o = orient(pt(P, a), pt(P, b), pt(P, z));
+      if (z == b) {
+        UR[nu - 1] = make_int2(comp(N4, mod3(ee + 2)), (T4.w >> mod3(ee + 2)) & 1);   // b->l
+        LR[nl - 1] = make_int2(comp(N4, mod3(ee + 1)), (T4.w >> mod3(ee + 1)) & 1);   // r->b
+        U[nu++] = b;
+        L[nl++] = b;
+        break;
+      }
+      const int o = orient(A, B, pt(P, z));
       if (o == 0) { status = S_INPUT; break; }
-      if (o > 0) {
-        ref = comp(P.N[tn], idx_of(T4, l));
+      if (o > 0) {   // z upper: boundary z->l (opposite r), exit r->z (opposite l)
+        UR[nu - 1] = make_int2(comp(N4, mod3(ee + 2)), (T4.w >> mod3(ee + 2)) & 1);
+        U[nu++] = z;
+        ref = comp(N4, mod3(ee + 1));
         l = z;
-      } else {
-        ref = comp(P.N[tn], idx_of(T4, r));
+      } else {       // z lower: boundary r->z (opposite l), exit z->l (opposite r)
+        LR[nl - 1] = make_int2(comp(N4, mod3(ee + 1)), (T4.w >> mod3(ee + 1)) & 1);
+        L[nl++] = z;
+        ref = comp(N4, mod3(ee + 2));
         r = z;
       }
+    }
+#ifdef GDP_DIAG
+    for (int i = 0; i < cnt && status == 0; ++i)
+      for (int j = i + 1; j < cnt; ++j)
+        if (R[i] == R[j]) printf("seg %d: walk revisits slot %d (cnt %d)\n", s, R[i], cnt);
+#endif
+    if (status == 1000) {
+      W.state[k] = -3;
+      continue;
     }
     if (status != 0) {
       P.mi[m].status = status;
       set_err(P.ctrl, status);
-      P.reg_n[k] = -2;
+      W.state[k] = -2;
       continue;
     }
-    P.reg_n[k] = cnt;
-    const unsigned long long key = seg_key(round, s, k);
+    W.state[k] = cnt;
+    const unsigned long long key = seg_key(round, s - P.mi[m].seg_base, k);
     for (int j = 0; j < cnt; ++j) {
       atomicMax(&P.segmark[R[j]], key);
       const int4 N4 = P.N[R[j]];
@@ -342,32 +375,125 @@ __global__ void __launch_bounds__(BS) k_seg_find(Pool P, int round) {
   }
 }
 
-__device__ int region_find_edge(const Pool& P, const int* R, int cnt, int u, int v, int& e) {
-  for (int j = 0; j < cnt; ++j) {
-    const int4 T4 = P.T[R[j]];
-    for (int q = 0; q < 3; ++q)
-      if (comp(T4, mod3(q + 1)) == u && comp(T4, mod3(q + 2)) == v) { e = q; return R[j]; }
+// subsegment bit of a chain edge: read from the outside triangle now, since a
+// segment found to be an edge already may have flagged it during the walk
+__device__ __forceinline__ int out_cons(const Pool& P, int2 e) {
+  return e.x >= 0 ? ((P.T[e.x >> 2].w >> (e.x & 3)) & 1) : e.y;
+}
+
+// chain accessors: the upper polygon uses U in order (base a->b); the lower
+// one uses L reversed (base b->a).  Boundary edge j joins chain vertices j, j+1.
+struct Chain {
+  const int* v;
+  int2* r;
+  int* nr;        // new refs of twin edges, indexed like r
+  int n;          // vertices
+  bool rev;
+  __device__ __forceinline__ int vert(int j) const { return rev ? v[n - 1 - j] : v[j]; }
+  __device__ __forceinline__ int idx(int j) const { return rev ? n - 2 - j : j; }
+  __device__ __forceinline__ int2 edge(int j) const { return r[idx(j)]; }
+};
+
+// mark twin edges: r[idx].x = -2 - (twin's chain index), r[idx].y = the
+// subsegment bit, read from the old triangles before anything is rewritten
+__device__ void mark_twins(const Pool& P, Chain& C) {
+  int* stk = C.nr;   // nr is free until the re-triangulation
+  int sp = 0;
+  for (int j = 0; j + 1 < C.n; ++j) {
+    const int u = C.vert(j), v = C.vert(j + 1);
+    if (sp > 0) {
+      const int t = stk[sp - 1];
+      if (C.vert(t) == v && C.vert(t + 1) == u) {
+        --sp;
+        int2& ej = C.r[C.idx(j)];
+        int2& et = C.r[C.idx(t)];
+        const int cb = out_cons(P, ej) | out_cons(P, et) | ej.y | et.y;
+        ej = make_int2(-2 - t, cb);
+        et = make_int2(-2 - j, cb);
+        continue;
+      }
+    }
+    stk[sp++] = j;
   }
-  return -1;
 }
 
-__device__ __forceinline__ bool in_region(const int* R, int cnt, int t) {
-  for (int j = 0; j < cnt; ++j)
-    if (R[j] == t) return true;
-  return false;
+// link the new triangles on both sides of every twin edge
+__device__ void link_twins(const Pool& P, const Chain& C) {
+  for (int j = 0; j + 1 < C.n; ++j) {
+    const int2 e = C.edge(j);
+    if (e.x > -2) continue;
+    const int t = -2 - e.x;
+    if (t < j) continue;
+    const int a = C.nr[C.idx(j)], b = C.nr[C.idx(t)];
+    set_nb(P, a, b);
+    set_nb(P, b, a);
+  }
 }
 
-// the owner of a region makes the segment an edge by flips, then restores the
-// constrained Delaunay property inside the region
-__global__ void __launch_bounds__(BS) k_seg_apply(Pool P, int round, int2* work) {
-  const int n = min(P.ctrl->n_segs, P.cap_segq);
+// re-triangulate one pseudo-polygon; returns the root triangle's slot or -1
+__device__ int tri_pseudo(const Pool& P, Chain& C, int m, const int* R, int& next, int4* ST) {
+  int sp = 0, root = -1;
+  ST[sp++] = make_int4(0, C.n - 1, -1, 0);
+  while (sp > 0) {
+    const int4 tk = ST[--sp];
+    const int lo = tk.x, hi = tk.y;
+    const int u = C.vert(lo), w = C.vert(hi);
+    const P2 pu = pt(P, u), pw = pt(P, w);
+    int best = lo + 1;
+    P2 pb = pt(P, C.vert(best));
+    for (int j = lo + 2; j < hi; ++j) {
+      const P2 pj = pt(P, C.vert(j));
+      if (incircle(pu, pw, pb, pj) > 0) { best = j; pb = pj; }
+    }
+    const int c = C.vert(best);
+    const int sl = R[next++];
+    // (u, w, c): edge 0 = (w -> c), edge 1 = (c -> u), edge 2 = (u -> w) = base
+    int cons = 0, n0 = -1, n1 = -1;
+    if (hi == best + 1) {
+      const int2 e = C.edge(best);
+      if (e.x <= -2) {          // twin edge: linked after the re-triangulation
+        cons |= e.y;
+        C.nr[C.idx(best)] = (sl << 2) | 0;
+      } else {
+        n0 = e.x;
+        cons |= out_cons(P, e);
+        set_nb(P, e.x, (sl << 2) | 0);
+      }
+    } else {
+      ST[sp++] = make_int4(best, hi, (sl << 2) | 0, 0);
+    }
+    if (best == lo + 1) {
+      const int2 e = C.edge(lo);
+      if (e.x <= -2) {
+        cons |= e.y << 1;
+        C.nr[C.idx(lo)] = (sl << 2) | 1;
+      } else {
+        n1 = e.x;
+        cons |= out_cons(P, e) << 1;
+        set_nb(P, e.x, (sl << 2) | 1);
+      }
+    } else {
+      ST[sp++] = make_int4(lo, best, (sl << 2) | 1, 0);
+    }
+    const int n2 = tk.z;
+    P.T[sl] = make_int4(u, w, c, (m << 4) | cons);
+    P.N[sl] = make_int4(n0, n1, n2, 0);
+    if (n2 >= 0) set_nb(P, n2, (sl << 2) | 2);
+    else root = sl;
+  }
+  return root;
+}
+
+__global__ void __launch_bounds__(BS) k_seg_apply(Pool P, SegWork W, int round) {
+  const int n = W.n_list;
+  const int K = W.kcap;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int k = gt; k < n; k += gs) {
-    const int cnt = P.reg_n[k];
+    const int cnt = W.state[k];
     if (cnt <= 0) continue;
-    const int s = P.segq[k];
-    const unsigned long long key = seg_key(round, s, k);
-    const int* R = P.reg + (size_t)k * KMAX;
+    const int s = W.list[k];
+    const int* R = W.R + (size_t)k * (K + 1);
+    const unsigned long long key = seg_key(round, s - P.mi[P.T[R[0]].w >> 4].seg_base, k);
     bool own = true;
     for (int j = 0; j < cnt && own; ++j) {
       own = P.segmark[R[j]] == key;
@@ -378,127 +504,91 @@ __global__ void __launch_bounds__(BS) k_seg_apply(Pool P, int round, int2* work)
       }
     }
     if (!own) continue;
-    const int a = P.seg[s].x, b = P.seg[s].y;
     const int m = P.T[R[0]].w >> 4;
-    // crossing edges, as vertex pairs, in a circular queue
-    int2* Q = work + (size_t)k * KMAX;
-    int qh = 0, qn = 0;
-    for (int j = 0; j + 1 < cnt; ++j) {
-      const int4 T4 = P.T[R[j]];
-      const int4 N4 = P.N[R[j]];
-      for (int e = 0; e < 3; ++e)
-        if (comp(N4, e) >= 0 && (comp(N4, e) >> 2) == R[j + 1]) {
-          Q[qn++] = make_int2(comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)));
-          break;
-        }
-    }
-    int status = 0;
-    long long steps = 0;
-    const long long limit = 64ll * cnt * cnt + 256;
-    while (qn > 0 && status == 0) {
-      if (++steps > limit) { status = S_INTERNAL; break; }
-      const int2 ed = Q[qh];
-      qh = (qh + 1) % KMAX;
-      --qn;
-      int e1 = -1;
-      int t1 = region_find_edge(P, R, cnt, ed.x, ed.y, e1);
-      if (t1 < 0) { status = S_INTERNAL; break; }
-      const int4 A = P.T[t1];
-      const int ref = comp(P.N[t1], e1);
-      if (ref < 0) { status = S_INTERNAL; break; }
-      const int4 B = P.T[ref >> 2];
-      const int p1 = comp(A, e1), u = comp(A, mod3(e1 + 1)), v = comp(A, mod3(e1 + 2));
-      const int o = comp(B, ref & 3);
-      if (orient(pt(P, p1), pt(P, u), pt(P, o)) > 0 && orient(pt(P, p1), pt(P, o), pt(P, v)) > 0) {
-        flip(P, t1, e1);
-        if (crosses_seg(P, a, b, p1, o)) {
-          Q[(qh + qn) % KMAX] = make_int2(p1, o);
-          ++qn;
-        }
-      } else {
-        Q[(qh + qn) % KMAX] = ed;
-        ++qn;
-      }
-    }
-    if (status == 0) {
-      int e = -1;
-      int t = region_find_edge(P, R, cnt, a, b, e);
-      if (t < 0) t = region_find_edge(P, R, cnt, b, a, e);
-      if (t < 0) {
-        status = S_INTERNAL;
-      } else {
-        P.T[t].w |= 1 << e;
-        const int nb = comp(P.N[t], e);
-        if (nb >= 0) P.T[nb >> 2].w |= 1 << (nb & 3);
-      }
-    }
-    // Lawson flips on the region's interior, non-subsegment edges
-    for (int pass = 0; status == 0; ++pass) {
-      if (pass > 4 * cnt + 16) { status = S_INTERNAL; break; }
-      bool any = false;
-      for (int j = 0; j < cnt; ++j) {
-        const int t = R[j];
-        for (int e = 0; e < 3; ++e) {
-          const int4 T4 = P.T[t];
-          const int ref = comp(P.N[t], e);
-          if (ref < 0 || ((T4.w >> e) & 1)) continue;
-          const int t2 = ref >> 2;
-          if (!in_region(R, cnt, t2)) continue;
-          const int o = comp(P.T[t2], ref & 3);
-          if (incircle(pt(P, T4.x), pt(P, T4.y), pt(P, T4.z), pt(P, o)) > 0) {
-            const int p1 = comp(T4, e), u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
-            if (orient(pt(P, p1), pt(P, u), pt(P, o)) > 0 && orient(pt(P, p1), pt(P, o), pt(P, v)) > 0) {
-              flip(P, t, e);
-              any = true;
-            }
-          }
-        }
-      }
-      if (!any) break;
-    }
-    if (status != 0) {
-      P.mi[m].status = status;
-      set_err(P.ctrl, status);
-      P.reg_n[k] = -2;
-      continue;
-    }
+    const int* U = W.U + (size_t)k * (K + 2);
+    const int* L = W.L + (size_t)k * (K + 2);
+    int nu = 0, nl = 0;
+    const int b = P.seg[s].y;
+    while (U[nu] != b) ++nu;
+    while (L[nl] != b) ++nl;
+    ++nu;
+    ++nl;
+    int* NR = W.NR + (size_t)k * 2 * (K + 2);
+    Chain CU{U, W.UR + (size_t)k * (K + 2), NR, nu, false};
+    Chain CL{L, W.LR + (size_t)k * (K + 2), NR + (K + 2), nl, true};
+    mark_twins(P, CU);
+    mark_twins(P, CL);
+    int4* ST = W.ST + (size_t)k * (K + 2);
+    int next = 0;
+#ifdef GDP_DIAG
+    if (nu + nl - 4 != cnt) printf("seg %d: nu %d nl %d cnt %d\n", s, nu, nl, cnt);
+#endif
+    const int ru = tri_pseudo(P, CU, m, R, next, ST);
+    const int rl = tri_pseudo(P, CL, m, R, next, ST);
+#ifdef GDP_DIAG
+    if (next != cnt) printf("seg %d: created %d triangles for %d slots\n", s, next, cnt);
+    if (cnt > 60) printf("seg %d: long region cnt %d nu %d nl %d\n", s, cnt, nu, nl);
+#endif
+    link_twins(P, CU);
+    link_twins(P, CL);
+    // the two roots share the segment (edge 2 of both), now a subsegment
+    P.N[ru].z = (rl << 2) | 2;
+    P.N[rl].z = (ru << 2) | 2;
+    P.T[ru].w |= 4;
+    P.T[rl].w |= 4;
     for (int j = 0; j < cnt; ++j) {
       const int4 T4 = P.T[R[j]];
       P.vtri[T4.x] = R[j];
       P.vtri[T4.y] = R[j];
       P.vtri[T4.z] = R[j];
     }
-    P.reg_n[k] = -1;
+    W.state[k] = -1;
   }
 }
 
-// keep segments that still need work (stable); the rest of the list beyond
-// the per-round capacity is kept as is
-__global__ void __launch_bounds__(BS) k_seg_keep_count(Pool P) {
+// Keep the list entries that still need work (stable): not yet recovered
+// (state >= 0), too long for the tier (state -3), or beyond the processed
+// prefix.  ctrl->n_segs receives the kept count and ctrl->changed the number
+// of kept entries that the current tier can still handle.
+__global__ void __launch_bounds__(BS) k_seg_keep_count(Pool P, SegWork W, int n_total) {
   __shared__ int sm[33];
-  const int n = P.ctrl->n_segs, na = min(n, P.cap_segq);
-  const Chunk ch = chunk_of(n);
-  int cnt = 0;
-  for (int k = ch.b0 + threadIdx.x; k < ch.b1; k += BS) cnt += (k >= na || P.reg_n[k] >= 0) ? 1 : 0;
+  const Chunk ch = chunk_of(n_total);
+  int cnt = 0, shortc = 0;
+  for (int k = ch.b0 + threadIdx.x; k < ch.b1; k += BS) {
+    const int st = k < W.n_list ? W.state[k] : 0;
+    cnt += (st >= 0 || st == -3) ? 1 : 0;
+    shortc += st >= 0 ? 1 : 0;
+  }
   cnt = block_sum(cnt, sm);
-  if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
+  shortc = block_sum(shortc, sm);
+  if (threadIdx.x == 0) {
+    P.blk[blockIdx.x] = cnt;
+    P.blk[gridDim.x + blockIdx.x] = shortc;
+  }
 }
 
-__global__ void __launch_bounds__(BS) k_seg_keep_write(Pool P) {
+__global__ void __launch_bounds__(BS) k_seg_keep_write(Pool P, SegWork W, int n_total, int* out) {
   __shared__ int sm[33];
-  const int n = P.ctrl->n_segs, na = min(n, P.cap_segq);
-  const Chunk ch = chunk_of(n);
+  const Chunk ch = chunk_of(n_total);
   int off = block_prefix(P.blk, blockIdx.x, sm);
   for (int base = ch.b0; base < ch.b1; base += BS) {
     const int k = base + threadIdx.x;
     int keep = 0;
-    if (k < ch.b1) keep = (k >= na || P.reg_n[k] >= 0) ? 1 : 0;
+    if (k < ch.b1) {
+      const int st = k < W.n_list ? W.state[k] : 0;
+      keep = (st >= 0 || st == -3) ? 1 : 0;
+    }
     int tot;
     const int r = block_excl_scan(keep, sm, tot);
-    if (keep) P.segq2[off + r] = P.segq[k];
+    if (keep) out[off + r] = W.list[k];
     off += tot;
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) P.ctrl->n_segs = off;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    int sh = 0;
+    for (int k = 0; k < (int)gridDim.x; ++k) sh += P.blk[gridDim.x + k];
+    P.ctrl->n_segs = off;
+    P.ctrl->changed = sh;
+  }
 }
 
 // ---------------------------------------------------------------- exterior + compaction

@@ -19,7 +19,6 @@ namespace gdp {
 
 constexpr int CMAX = 32;            // cavity triangles per splitting point
 constexpr int BMAX = CMAX + 2;      // boundary edges per cavity
-constexpr int KMAX = 512;           // triangles crossed by one segment during recovery
 constexpr int WALK_MAX = 1 << 16;   // point-location steps
 constexpr int BS = 256;             // threads per block
 constexpr int INFO_DEAD = 8;
@@ -115,11 +114,7 @@ struct Pool {
   int32_t* pts2;
   int32_t* loc;          // per vertex: containing triangle, -1 once inserted
   unsigned long long* tbest;
-  int32_t* segq;
-  int32_t* segq2;
-  int32_t* reg;          // per active segment: crossed triangles, KMAX each
-  int32_t* reg_n;
-  int32_t cap_segq;
+  int32_t* segq;         // segments still to recover
   unsigned long long* segmark;
   uint8_t* ext;
   int32_t* remap;

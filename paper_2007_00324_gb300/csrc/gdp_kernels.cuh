@@ -753,6 +753,41 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
   }
 }
 
+// ---------------------------------------------------------------- consistency (test hook)
+// counts: [0] links that are not mutual, [1] links whose shared edge does not
+// match, [2] subsegment bits that differ across an edge, [3] triangles not CCW
+// (exact), [4] hull edges (no neighbour) that are not subsegments
+__global__ void __launch_bounds__(BS) k_check(Pool P, unsigned long long* cnt) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int t = gt; t < P.n_slots; t += gs) {
+    const int4 T4 = P.T[t];
+    if (T4.w < 0 || (T4.w & INFO_DEAD)) continue;
+    const int4 N4 = P.N[t];
+    if (orient(pt(P, T4.x), pt(P, T4.y), pt(P, T4.z)) <= 0) atomicAdd(&cnt[3], 1ull);
+    for (int e = 0; e < 3; ++e) {
+      const int ref = comp(N4, e);
+      const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
+      if (ref < 0) {
+        if (!((T4.w >> e) & 1)) atomicAdd(&cnt[4], 1ull);
+        continue;
+      }
+      const int t2 = ref >> 2, e2 = ref & 3;
+      const int4 B4 = P.T[t2];
+      bool badl = false;
+      if (comp(P.N[t2], e2) != ((t << 2) | e)) { atomicAdd(&cnt[0], 1ull); badl = true; }
+      if (comp(B4, mod3(e2 + 1)) != v || comp(B4, mod3(e2 + 2)) != u) {
+        atomicAdd(&cnt[1], 1ull);
+        badl = true;
+      }
+      if (badl) {   // keep the first four offenders (t << 2 | e) for diagnostics
+        const unsigned long long k = atomicAdd(&cnt[5], 1ull);
+        if (k < 4) cnt[6 + k] = (unsigned long long)((t << 2) | e);
+      }
+      if (((T4.w >> e) & 1) != ((B4.w >> e2) & 1)) atomicAdd(&cnt[2], 1ull);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- scan report (test hook)
 // Every live triangle: its bad flag; every subsegment edge: encroachment by
 // this triangle's apex.  Output in slot order.

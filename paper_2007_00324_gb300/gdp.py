@@ -44,7 +44,7 @@ class Stats(C.Structure):
 
 SYMBOLS = ["gdp_mesh_create", "gdp_mesh_create_device", "gdp_mesh_refine", "gdp_mesh_export",
            "gdp_mesh_insert_points", "gdp_mesh_split_subsegments", "gdp_mesh_scan",
-           "gdp_mesh_stats", "gdp_mesh_profile", "gdp_mesh_kernel_time", "gdp_mesh_destroy",
+           "gdp_mesh_stats", "gdp_mesh_check", "gdp_mesh_profile", "gdp_mesh_kernel_time", "gdp_mesh_destroy",
            "gdp_batch_create", "gdp_batch_refine",
            "gdp_batch_info", "gdp_batch_export", "gdp_batch_destroy", "gdp_scan_noalloc",
            "gdp_status_str"]
@@ -71,6 +71,7 @@ def load(build_if_missing: bool = True):
             L.gdp_mesh_split_subsegments.argtypes = [vp, vp, i64]
             L.gdp_mesh_scan.argtypes = [vp, d, vp, vp, vp, vp, i64, C.POINTER(i64)]
             L.gdp_mesh_stats.argtypes = [vp, C.POINTER(Stats)]
+            L.gdp_mesh_check.argtypes = [vp, vp]
             L.gdp_mesh_profile.argtypes = [vp, C.c_int]
             L.gdp_mesh_kernel_time.argtypes = [vp, i32, C.c_char_p, i64, C.POINTER(d), C.POINTER(i64)]
             L.gdp_mesh_destroy.argtypes = [vp]
@@ -161,6 +162,15 @@ class Mesh:
         s = Stats()
         load().gdp_mesh_stats(self._h, C.byref(s))
         return s.as_dict()
+
+    def check(self):
+        """device-side consistency counts (all zero for a valid mesh)"""
+        c = np.zeros(5, np.int64)
+        st = load().gdp_mesh_check(self._h, _p(c))
+        if st != OK:
+            raise GdpError(st, "gdp_mesh_check")
+        return dict(zip(("not_mutual", "edge_mismatch", "flag_mismatch", "not_ccw", "open_not_sub"),
+                        c.tolist()))
 
     def profile(self, enable=True):
         st = load().gdp_mesh_profile(self._h, 1 if enable else 0)

@@ -59,6 +59,9 @@ def test_mid_config_bit_exact(oracle):
     gdp = need_gpu()
     from paper_2007_00324_gb300 import workloads as W
     p = W.mid()
+    g = gdp.Mesh(p.xy, p.seg)
+    # the device links, not only the exported triangle list, must be consistent
+    assert all(v == 0 for v in g.check().values()), g.check()
     (gxy, gtri, gsub), (oxy, otri, _) = both(oracle, gdp, p.xy, p.seg)
     assert len(gtri) == len(otri)
     assert oracle.triangle_set(gxy, gtri) == oracle.triangle_set(oxy, otri)

@@ -13,7 +13,9 @@ pytestmark = pytest.mark.gpu
 
 def refine_both(oracle, gdp, p, B, **kw):
     g = gdp.Mesh(p.xy, p.seg)
+    assert all(v == 0 for v in g.check().values())
     stats = g.refine(B, **kw)
+    assert all(v == 0 for v in g.check().values()), g.check()
     xy, tri, sub = g.export()
     o = oracle.Mesh(p.xy, p.seg)
     assert o.refine(B) == 0
