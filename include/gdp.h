@@ -43,7 +43,8 @@ typedef enum {
     GDP_ERR_WALK_LIMIT = 4,  /* a point-location walk exceeded its step bound */
     GDP_ERR_CUDA = 5,        /* CUDA runtime error or no device */
     GDP_ERR_INTERNAL = 6,    /* an invariant check inside a kernel failed */
-    GDP_ERR_CAPACITY = 7     /* a per-element work buffer (cavity, segment region) overflowed */
+    GDP_ERR_CAPACITY = 7     /* a per-element work buffer overflowed: a cavity above 65536
+                                triangles, or a segment crossing more than 32768 edges */
 } gdp_status;
 
 typedef struct gdp_mesh gdp_mesh;

@@ -146,6 +146,21 @@ constexpr int BS_CAND = 64;
     (h).prof_end();                                                  \
   } while (0)
 
+// explicit launch shape (the spill-lane kernels: one thread per lane)
+#define LAUNCH_B(h, kern, grid, block, ...)                          \
+  do {                                                               \
+    (h).prof_begin(#kern);                                           \
+    kern<<<(grid), (block), 0, (h).stream>>>(__VA_ARGS__);           \
+    (h).prof_end();                                                  \
+  } while (0)
+// candidate cavities: own slots, then the two spill tiers
+#define LAUNCH_GROW(h, MODE, P)                                      \
+  do {                                                               \
+    LAUNCH_C(h, k_grow<MODE>, P);                                    \
+    LAUNCH_B(h, k_grow_big<MODE>, LANES_A / 32, 32, P, 0);           \
+    LAUNCH_B(h, k_grow_big<MODE>, LANES_B, 1, P, 1);                 \
+  } while (0)
+
 double env_double(const char* name, double def) {
   const char* s = std::getenv(name);
   return s ? std::atof(s) : def;
@@ -211,7 +226,7 @@ struct PoolHost {
   // per-kernel timing (profiling mode) and launch counting
   bool prof = false;
   long long launches = 0;
-  int kernels_per_iter = 8;
+  int kernels_per_iter = 10;   // launch_iteration
   struct Pending { const char* name; cudaEvent_t a, b; };
   std::vector<Pending> pend;
   std::vector<std::pair<std::string, std::pair<double, long long>>> ktimes;
@@ -370,6 +385,8 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   AL(P.c_elem, C, 0); AL(P.c_loc, C, 0); AL(P.c_vid, C, 0); AL(P.c_mesh, C, 0);
   AL(P.c_vseg, C, 0); AL(P.c_sub, C, 0); AL(P.c_pt, C, 0); AL(P.c_ptf, C, 0); AL(P.c_key, C, 0);
   AL(P.c_ncav, C, 0); AL(P.c_nbnd, C, 0); AL(P.c_cav, C * CMAX, 0); AL(P.c_bnd, C * BMAX, 0);
+  AL(P.c_big, C, 0xff); AL(P.big_cav, BIG_ENTRIES, 0); AL(P.big_bnd, BIG_ENTRIES, 0);
+  AL(P.big_hash, BIG_HASH, 0xff); AL(P.lane, LANES_A + LANES_B, 0x7f);
   AL(P.c_state, C, 0); AL(P.c_final, C, 0); AL(P.c_extra, C, 0); AL(P.c_offT, C, 0);
   AL(P.c_offV, C, 0); AL(P.c_base, C, 0);
   AL(P.blk, 2 * G, 0);
@@ -437,7 +454,7 @@ int PoolHost::insert_rounds(int stop_cons, int* rounds_out) {
     LAUNCH(*this, k_cdt_locate, G, P, rounds, stop_cons);
     LAUNCH(*this, k_cdt_pick_count, G, P, rounds);
     LAUNCH(*this, k_cdt_pick_write, G, P, rounds);
-    LAUNCH_C(*this, k_grow<1>, P);
+    LAUNCH_GROW(*this, 1, P);
     LAUNCH_C(*this, k_survive, P);
     LAUNCH(*this, k_depend, G, P);
     LAUNCH(*this, k_offsets, G, P);
@@ -593,7 +610,7 @@ int PoolHost::build_cdt() {
 int PoolHost::launch_iteration() {
   LAUNCH(*this, k_scan_count, G, P);
   LAUNCH(*this, k_scan_write, G, P);
-  LAUNCH_C(*this, k_grow<0>, P);
+  LAUNCH_GROW(*this, 0, P);
   LAUNCH_C(*this, k_survive, P);
   LAUNCH(*this, k_depend, G, P);
   LAUNCH(*this, k_offsets, G, P);
@@ -939,7 +956,7 @@ int gdp_mesh_split_subsegments(gdp_mesh* g, const double* abxy, int64_t n) {
     CK(cudaMemcpyAsync(&h.P.ctrl->n_cand, &nc, sizeof(int), cudaMemcpyHostToDevice, h.stream));
     CK(cudaMemcpyAsync(&h.P.ctrl->prev_cand, &nc, sizeof(int), cudaMemcpyHostToDevice, h.stream));
     for (auto& Mi : h.hmi) Mi.active = 1;
-    LAUNCH_C(h, k_grow<0>, h.P);
+    LAUNCH_GROW(h, 0, h.P);
     LAUNCH_C(h, k_survive, h.P);
     LAUNCH(h, k_depend, h.G, h.P);
     LAUNCH(h, k_offsets, h.G, h.P);

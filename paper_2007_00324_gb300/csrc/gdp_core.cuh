@@ -12,6 +12,10 @@
 // Per-candidate scratch (one candidate = one splitting point, Algorithm 1 line 5):
 //   c_cav[i*CMAX + j]   cavity triangles;  c_bnd[i*BMAX + j]  cavity boundary edges
 //   as int4 (u, v, outside ref, inside ref | subsegment << 31).
+//   A cavity that outgrows its slot is grown again in a lane of a spill tier
+//   (big_cav / big_bnd at offset c_big[i]): LANES_A lanes of CAP_A triangles,
+//   then LANES_B lanes of CAP_B = CMAX_BIG; each lane has a hash set of twice
+//   its capacity in big_hash.
 #pragma once
 #include <cstdint>
 
@@ -19,6 +23,12 @@ namespace gdp {
 
 constexpr int CMAX = 32;            // cavity triangles per splitting point
 constexpr int BMAX = CMAX + 2;      // boundary edges per cavity
+constexpr int CMAX_BIG = 1 << 16;   // largest cavity
+constexpr int LANES_A = 4096, CAP_A = 512;       // spill tier A (powers of two)
+constexpr int LANES_B = 16, CAP_B = CMAX_BIG;    // spill tier B
+constexpr long long BIG_ENTRIES = (long long)LANES_A * (CAP_A + 2) + (long long)LANES_B * (CAP_B + 2);
+constexpr long long BIG_HASH = 2ll * LANES_A * CAP_A + 2ll * LANES_B * CAP_B;
+constexpr int LANE_FREE = 0x7f7f7f7f;            // byte fill 0x7f
 constexpr int WALK_MAX = 1 << 16;   // point-location steps
 constexpr int BS = 256;             // threads per block
 constexpr int INFO_DEAD = 8;
@@ -101,6 +111,11 @@ struct Pool {
   int32_t* c_nbnd;
   int32_t* c_cav;
   int4* c_bnd;
+  int32_t* c_big;        // offset of the cavity in the spill tiers, -1 = own slot
+  int32_t* big_cav;      // BIG_ENTRIES
+  int4* big_bnd;         // BIG_ENTRIES
+  int32_t* big_hash;     // BIG_HASH
+  int32_t* lane;         // LANES_A + LANES_B owners (smallest candidate index)
   uint8_t* c_state;
   uint8_t* c_final;
   int32_t* c_extra;

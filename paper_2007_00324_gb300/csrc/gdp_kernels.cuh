@@ -248,12 +248,24 @@ __device__ int eval_tri(const Pool& P, int t) {
   return 0;
 }
 
+// cavity work space of candidate i: its own slot, or its spill arena region
+__device__ __forceinline__ int* cav_of(const Pool& P, int i) {
+  const int o = P.c_big[i];
+  return o < 0 ? P.c_cav + (size_t)i * CMAX : P.big_cav + o;
+}
+
+__device__ __forceinline__ int4* bnd_of(const Pool& P, int i) {
+  const int o = P.c_big[i];
+  return o < 0 ? P.c_bnd + (size_t)i * BMAX : P.big_bnd + o;
+}
+
 __global__ void __launch_bounds__(BS) k_clear_marks(Pool P) {
   const int prev = P.ctrl->prev_cand;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int i = gt; i < prev; i += gs) {
     const int n = P.c_ncav[i];
-    for (int j = 0; j < n; ++j) P.mark[P.c_cav[(size_t)i * CMAX + j]] = 0ull;
+    const int* cav = cav_of(P, i);
+    for (int j = 0; j < n; ++j) P.mark[cav[j]] = 0ull;
   }
 }
 
@@ -263,7 +275,8 @@ __global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int i = gt; i < prev; i += gs) {
     const int n = P.c_ncav[i];
-    for (int j = 0; j < n; ++j) P.mark[P.c_cav[(size_t)i * CMAX + j]] = 0ull;
+    const int* cav = cav_of(P, i);
+    for (int j = 0; j < n; ++j) P.mark[cav[j]] = 0ull;
   }
   for (int m = gt; m < P.n_mesh; m += gs) {
     P.mi[m].first_cand = -1;
@@ -379,27 +392,65 @@ enum { G_OK = 0, G_OVF = 1, G_CONV = 2 };
 // (u, v, outside ref, inside ref | subsegment bit).  With conv, meeting a
 // subsegment that p encroaches stops the growth (G_CONV) so that the
 // subsegment is split instead (Sec. 4.2: such a circumcentre is redundant).
-__device__ int grow(const Pool& P, int i, const P2& p, int t0, int t1, bool conv, int& nc, int& nb,
-                    int& ct, int& ce) {
-  int* cav = P.c_cav + (size_t)i * CMAX;
-  int4* bnd = P.c_bnd + (size_t)i * BMAX;
+// Cavity work space.  Every candidate first grows in its own slot (CMAX
+// triangles, linear membership test).  One that outgrows it asks for a lane
+// of spill tier A (CAP_A triangles), and from there for a lane of tier B
+// (CMAX_BIG); a lane carries an open-addressing hash set for the membership
+// test.  A lane goes, for one round, to the smallest candidate index mapped
+// to it, so which candidates get one never depends on timing; the others
+// fail this round and are retried in a later one.
+struct CavBuf {
+  int* cav;
+  int4* bnd;     // capacity cap + 2
+  int* hash;     // nullptr: linear membership test
+  int cap;
+  int hmask;     // hash set size - 1 (at least 2 cap - 1)
+};
+
+// is t in the cavity?  With a hash set a miss leaves in h the empty entry
+// where t goes.  The set is never more than half full, so the probe always
+// meets an empty entry; the loop is bounded all the same.
+__device__ __forceinline__ bool cav_has(const CavBuf& B, int k, int t, int& h) {
+  if (!B.hash) {
+    for (int r = 0; r < k; ++r)
+      if (B.cav[r] == t) return true;
+    return false;
+  }
+  h = (int)(hash32((uint32_t)t) & (uint32_t)B.hmask);
+  for (int s = 0; s <= B.hmask; ++s) {
+    const int x = B.hash[h];
+    if (x == t) return true;
+    if (x < 0) return false;
+    h = (h + 1) & B.hmask;
+  }
+  return true;   // unreachable: treat as present so nothing is overwritten
+}
+
+__device__ __forceinline__ bool cav_add(const CavBuf& B, int& k, int t) {
+  int h = 0;
+  if (cav_has(B, k, t, h)) return true;
+  if (k == B.cap) return false;
+  B.cav[k++] = t;
+  if (B.hash) B.hash[h] = t;
+  return true;
+}
+
+__device__ int grow(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1, bool conv, int& nc,
+                    int& nb, int& ct, int& ce) {
+  if (B.hash)
+    for (int j = 0; j <= B.hmask; ++j) B.hash[j] = -1;
   int k = 0, b = 0;
-  cav[k++] = t0;
-  if (t1 >= 0) cav[k++] = t1;
+  cav_add(B, k, t0);
+  if (t1 >= 0) cav_add(B, k, t1);
   for (int q = 0; q < k; ++q) {
-    const int t = cav[q];
+    const int t = B.cav[q];
     const int4 T4 = P.T[t];
     const int4 N4 = P.N[t];
     for (int e = 0; e < 3; ++e) {
       const int ref = comp(N4, e);
       const int cons = (T4.w >> e) & 1;
-      if (ref >= 0) {
-        const int tn = ref >> 2;
-        bool in = false;
-        for (int r = 0; r < k; ++r)
-          if (cav[r] == tn) { in = true; break; }
-        if (in) continue;
-      }
+      int h = 0;
+      if (ref >= 0 && cav_has(B, k, ref >> 2, h)) continue;
       const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
       bool inside = false;
       if (!cons && ref >= 0) {
@@ -411,11 +462,12 @@ __device__ int grow(const Pool& P, int i, const P2& p, int t0, int t1, bool conv
         return G_CONV;
       }
       if (inside) {
-        if (k == CMAX) return G_OVF;
-        cav[k++] = ref >> 2;
+        if (k == B.cap) return G_OVF;
+        B.cav[k++] = ref >> 2;
+        if (B.hash) B.hash[h] = ref >> 2;
       } else {
-        if (b == BMAX) return G_OVF;
-        bnd[b++] = make_int4(u, v, ref, (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
+        if (b == B.cap + 2) return G_OVF;
+        B.bnd[b++] = make_int4(u, v, ref, (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
       }
     }
   }
@@ -429,112 +481,146 @@ __device__ __forceinline__ bool is_split_edge(const int4& rec, int2 sub) {
          ((rec.x == sub.x && rec.y == sub.y) || (rec.x == sub.y && rec.y == sub.x));
 }
 
+// One candidate: its splitting point, its cavity in B, and its priority marks.
 // MODE 0: refinement candidates (element = triangle << 2 | edge, 3 = the triangle);
 // MODE 1: given points (element = vertex id, c_loc = located triangle).
+// Returns G_OVF when the cavity does not fit B, else G_OK (c_state tells
+// whether the candidate was grown).
+template <int MODE>
+__device__ int grow_cand(const Pool& P, int i, const CavBuf& B) {
+  P.c_ncav[i] = 0;
+  P.c_nbnd[i] = 0;
+  P.c_state[i] = C_FAIL;
+  P.c_final[i] = 0;
+  const int elem = P.c_elem[i];
+  double2 p;
+  unsigned long long key;
+  int t0, t1 = -1, m, vid = -1;
+  bool conv = false;
+  int2 sub = make_int2(-1, -1);
+  if (MODE == 1) {
+    vid = elem;
+    t0 = P.c_loc[i];
+    m = P.T[t0].w >> 4;
+    p = P.V[vid];
+    key = ((unsigned long long)insert_prio(P.mi[m], vid) << 32) | (unsigned)i;
+  } else {
+    const int t = elem >> 2, k = elem & 3;
+    const int4 T4 = P.T[t];
+    m = T4.w >> 4;
+    const MeshInfo& M = P.mi[m];
+    if (k == 3) {
+      const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
+      p = circumcenter(tt);
+      key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
+      int bt = -1, be = -1;
+      const int r = walk(P, t, P2{p, to_f(p, M.org)}, true, bt, be);
+      if (r == -2) {
+        P.c_mesh[i] = m;
+        set_err(P.ctrl, S_WALK);
+        return G_OK;
+      }
+      if (r == -1) {
+        // the walk meets a subsegment: split it instead (Sec. 4.3)
+        const int4 B4 = P.T[bt];
+        const int u = comp(B4, mod3(be + 1)), v = comp(B4, mod3(be + 2));
+        p = split_point(P, M, u, v);
+        key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+              (unsigned)i;
+        t0 = bt;
+        const int nr = comp(P.N[bt], be);
+        t1 = nr >= 0 ? nr >> 2 : -1;
+        sub = make_int2(u, v);
+      } else {
+        t0 = r;
+        conv = true;
+      }
+    } else {
+      const int u = comp(T4, mod3(k + 1)), v = comp(T4, mod3(k + 2));
+      p = split_point(P, M, u, v);
+      key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+            (unsigned)i;
+      t0 = t;
+      const int nr = comp(P.N[t], k);
+      t1 = nr >= 0 ? nr >> 2 : -1;
+      sub = make_int2(u, v);
+    }
+  }
+  P.c_mesh[i] = m;
+  P2 pp{p, MODE == 1 ? P.Vf[vid] : to_f(p, P.mi[m].org)};
+  int nc = 0, nb = 0, ct = -1, ce = -1;
+#ifdef GDP_DIAG
+  const long long gc0 = clock64();
+#endif
+  int g = grow(P, B, pp, t0, t1, conv, nc, nb, ct, ce);
+#ifdef GDP_DIAG
+  atomicMax(&g_diag[6], (unsigned long long)(clock64() - gc0));
+#endif
+  if (g == G_CONV) {
+    const int4 B4 = P.T[ct];
+    const int u = comp(B4, mod3(ce + 1)), v = comp(B4, mod3(ce + 2));
+    p = split_point(P, P.mi[m], u, v);
+    key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+          (unsigned)i;
+    sub = make_int2(u, v);
+    const int nr = comp(P.N[ct], ce);
+    pp = P2{p, to_f(p, P.mi[m].org)};
+    g = grow(P, B, pp, ct, nr >= 0 ? nr >> 2 : -1, false, nc, nb, ct, ce);
+  }
+  if (g == G_OVF) return G_OVF;
+  bool ok = true;
+  for (int r = 0; r < nb && ok; ++r) {
+    const int4 rec = B.bnd[r];
+    if (is_split_edge(rec, sub)) continue;
+    if (orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) ok = false;
+  }
+  if (!ok) return G_OK;
+  for (int j = 0; j < nc; ++j) atomicMax(&P.mark[B.cav[j]], key);
+  P.c_pt[i] = p;
+  P.c_ptf[i] = pp.f;
+  P.c_key[i] = key;
+  P.c_ncav[i] = nc;
+  P.c_nbnd[i] = nb;
+  P.c_sub[i] = sub;
+  P.c_vid[i] = vid;
+  P.c_vseg[i] = (sub.x >= 0) ? seg_of_sub(P, P.mi[m], sub.x, sub.y) : -1;
+  P.c_state[i] = C_GROWN;
+  return G_OK;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(BS) k_grow(Pool P) {
   const int n = P.ctrl->n_cand;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int i = gt; i < n; i += gs) {
-    P.c_ncav[i] = 0;
-    P.c_nbnd[i] = 0;
-    P.c_state[i] = C_FAIL;
-    P.c_final[i] = 0;
-    const int elem = P.c_elem[i];
-    double2 p;
-    unsigned long long key;
-    int t0, t1 = -1, m, vid = -1;
-    bool conv = false;
-    int2 sub = make_int2(-1, -1);
-    if (MODE == 1) {
-      vid = elem;
-      t0 = P.c_loc[i];
-      m = P.T[t0].w >> 4;
-      p = P.V[vid];
-      key = ((unsigned long long)insert_prio(P.mi[m], vid) << 32) | (unsigned)i;
-    } else {
-      const int t = elem >> 2, k = elem & 3;
-      const int4 T4 = P.T[t];
-      m = T4.w >> 4;
-      const MeshInfo& M = P.mi[m];
-      if (k == 3) {
-        const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
-        p = circumcenter(tt);
-        key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
-        int bt = -1, be = -1;
-        const int r = walk(P, t, P2{p, to_f(p, M.org)}, true, bt, be);
-        if (r == -2) {
-          P.c_mesh[i] = m;
-          set_err(P.ctrl, S_WALK);
-          continue;
-        }
-        if (r == -1) {
-          // the walk meets a subsegment: split it instead (Sec. 4.3)
-          const int4 B4 = P.T[bt];
-          const int u = comp(B4, mod3(be + 1)), v = comp(B4, mod3(be + 2));
-          p = split_point(P, M, u, v);
-          key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
-                (unsigned)i;
-          t0 = bt;
-          const int nr = comp(P.N[bt], be);
-          t1 = nr >= 0 ? nr >> 2 : -1;
-          sub = make_int2(u, v);
-        } else {
-          t0 = r;
-          conv = true;
-        }
-      } else {
-        const int u = comp(T4, mod3(k + 1)), v = comp(T4, mod3(k + 2));
-        p = split_point(P, M, u, v);
-        key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
-              (unsigned)i;
-        t0 = t;
-        const int nr = comp(P.N[t], k);
-        t1 = nr >= 0 ? nr >> 2 : -1;
-        sub = make_int2(u, v);
-      }
-    }
-    P.c_mesh[i] = m;
-    P2 pp{p, MODE == 1 ? P.Vf[vid] : to_f(p, P.mi[m].org)};
-    int nc = 0, nb = 0, ct = -1, ce = -1;
-#ifdef GDP_DIAG
-    const long long gc0 = clock64();
-#endif
-    int g = grow(P, i, pp, t0, t1, conv, nc, nb, ct, ce);
-#ifdef GDP_DIAG
-    atomicMax(&g_diag[6], (unsigned long long)(clock64() - gc0));
-#endif
-    if (g == G_CONV) {
-      const int4 B4 = P.T[ct];
-      const int u = comp(B4, mod3(ce + 1)), v = comp(B4, mod3(ce + 2));
-      p = split_point(P, P.mi[m], u, v);
-      key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
-            (unsigned)i;
-      sub = make_int2(u, v);
-      const int nr = comp(P.N[ct], ce);
-      pp = P2{p, to_f(p, P.mi[m].org)};
-      g = grow(P, i, pp, ct, nr >= 0 ? nr >> 2 : -1, false, nc, nb, ct, ce);
-    }
-    if (g != G_OK) continue;   // buffer overflow: retried in a later iteration (Rule 3)
-    const int4* bnd = P.c_bnd + (size_t)i * BMAX;
-    bool ok = true;
-    for (int r = 0; r < nb && ok; ++r) {
-      const int4 rec = bnd[r];
-      if (is_split_edge(rec, sub)) continue;
-      if (orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) ok = false;
-    }
-    if (!ok) continue;
-    const int* cav = P.c_cav + (size_t)i * CMAX;
-    for (int j = 0; j < nc; ++j) atomicMax(&P.mark[cav[j]], key);
-    P.c_pt[i] = p;
-    P.c_ptf[i] = pp.f;
-    P.c_key[i] = key;
-    P.c_ncav[i] = nc;
-    P.c_nbnd[i] = nb;
-    P.c_sub[i] = sub;
-    P.c_vid[i] = vid;
-    P.c_vseg[i] = (sub.x >= 0) ? seg_of_sub(P, P.mi[m], sub.x, sub.y) : -1;
-    P.c_state[i] = C_GROWN;
+    P.c_big[i] = -1;
+    const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
+    if (grow_cand<MODE>(P, i, B) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+  }
+}
+
+// Cavities that outgrew their slot (tier 0) or their tier-A lane (tier 1):
+// one thread per lane; the lane is freed for the next round as it is read.
+template <int MODE>
+__global__ void k_grow_big(Pool P, int TIER) {
+  const int lanes = TIER ? LANES_B : LANES_A;
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= lanes) return;
+  int* lane = P.lane + (TIER ? LANES_A : 0) + l;
+  const int i = *lane;
+  if (i == LANE_FREE) return;
+  *lane = LANE_FREE;
+  const int cap = TIER ? CAP_B : CAP_A;
+  const size_t off = TIER ? (size_t)LANES_A * (CAP_A + 2) + (size_t)l * (CAP_B + 2)
+                          : (size_t)l * (CAP_A + 2);
+  const size_t hoff = TIER ? (size_t)LANES_A * 2 * CAP_A + (size_t)l * 2 * CAP_B
+                           : (size_t)l * 2 * CAP_A;
+  P.c_big[i] = (int)off;
+  const CavBuf B{P.big_cav + off, P.big_bnd + off, P.big_hash + hoff, cap, 2 * cap - 1};
+  if (grow_cand<MODE>(P, i, B) == G_OVF) {
+    P.c_big[i] = -1;
+    if (TIER == 0) atomicMin(&P.lane[LANES_A + (i & (LANES_B - 1))], i);
+    else set_err(P.ctrl, S_CAPACITY);
   }
 }
 
@@ -548,7 +634,7 @@ __global__ void __launch_bounds__(BS) k_survive(Pool P) {
     if (i == n - 1 || P.c_mesh[i + 1] != m) P.mi[m].last_cand = i;
     if (P.c_state[i] != C_GROWN) continue;
     const unsigned long long key = P.c_key[i];
-    const int* cav = P.c_cav + (size_t)i * CMAX;
+    const int* cav = cav_of(P, i);
     const int nc = P.c_ncav[i];
     bool own = true;
     for (int j = 0; j < nc && own; ++j) own = P.mark[cav[j]] == key;
@@ -576,7 +662,7 @@ __global__ void __launch_bounds__(BS) k_depend(Pool P) {
       const unsigned long long key = P.c_key[i];
       const P2 p{P.c_pt[i], P.c_ptf[i]};
       const int nb = P.c_nbnd[i];
-      const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+      const int4* bnd = bnd_of(P, i);
       const int2 sub = P.c_sub[i];
       int eff = 0;
       for (int r = 0; r < nb; ++r) {
@@ -671,8 +757,8 @@ __global__ void __launch_bounds__(BS) k_insert(Pool P) {
     P.Vf[vid] = P.c_ptf[i];
     P.vseg[vid] = P.c_vseg[i];
     if (MODE == 1) P.loc[vid] = -1;
-    const int4* bnd = P.c_bnd + (size_t)i * BMAX;
-    const int* cav = P.c_cav + (size_t)i * CMAX;
+    const int4* bnd = bnd_of(P, i);
+    const int* cav = cav_of(P, i);
     const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
     const int2 sub = P.c_sub[i];
     const bool is_mid = sub.x >= 0;
@@ -723,8 +809,8 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
     const bool ok = M.ins_ok;
     if (P.c_final[i] && ok) {
       ++ins;
-      const int4* bnd = P.c_bnd + (size_t)i * BMAX;
-      const int* cav = P.c_cav + (size_t)i * CMAX;
+      const int4* bnd = bnd_of(P, i);
+      const int* cav = cav_of(P, i);
       const int nc = P.c_ncav[i], nb = P.c_nbnd[i], base = P.c_base[i];
       const int2 sub = P.c_sub[i];
       int j = 0;
