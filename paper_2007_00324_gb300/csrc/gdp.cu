@@ -222,6 +222,18 @@ struct PoolHost {
   gdp_stats stats{};
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
+  // construction rounds replayed from CUDA graphs, each captured for the
+  // pool layout it was recorded with (key) and a variant tag
+  struct Cached {
+    cudaGraphExec_t g = nullptr;
+    Pool key{};
+    int tag = -1;
+    int kernels = 0;
+  };
+  Cached g_bw, g_split[2], g_flip;
+  int cdt_round = 0;              // last construction round used (device keys)
+  int32_t* flA = nullptr;         // flip lists (construction only)
+  int32_t* flB = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-kernel timing (profiling mode) and launch counting
   bool prof = false;
@@ -266,6 +278,8 @@ struct PoolHost {
   ~PoolHost() {
     prof_flush();
     if (graph) cudaGraphExecDestroy(graph);
+    for (Cached* c : {&g_bw, &g_split[0], &g_split[1], &g_flip})
+      if (c->g) cudaGraphExecDestroy(c->g);
     for (void* p : allocs) cudaFree(p);
     if (hctrl) cudaFreeHost(hctrl);
     if (ev0) cudaEventDestroy(ev0);
@@ -317,7 +331,52 @@ struct PoolHost {
   int setup(const double* xy, const long long* pt_off, const int32_t* seg, const long long* seg_off,
             int nm, bool on_device, void* s);
   int build_cdt();
-  int insert_rounds(int stop_cons, int* rounds_out);
+  int insert_rounds(int stop_cons, int* rounds_out, bool split);
+  int launch_cdt_round(const Pool& Q, int stop_cons);
+  int launch_split_round(const Pool& Q);
+  int launch_flip_passes();
+  Pool flip_pool(bool a_to_b) const {
+    Pool Q = P;
+    Q.fl_cur = a_to_b ? flA : flB;
+    Q.fl_nxt = a_to_b ? flB : flA;
+    return Q;
+  }
+  // replays c, capturing body() first when the pool layout or tag changed
+  template <class F>
+  int replay(Cached& c, int tag, F&& body) {
+    if (!c.g || c.tag != tag || std::memcmp(&c.key, &P, sizeof(Pool)) != 0) {
+      if (c.g) cudaGraphExecDestroy(c.g);
+      c.g = nullptr;
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaStream_t saved = stream;
+      const long long saved_launches = launches;
+      stream = cs;
+      int st = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? GDP_OK
+                                                                                           : GDP_ERR_CUDA;
+      if (st == GDP_OK) st = body();
+      c.kernels = (int)(launches - saved_launches);
+      launches = saved_launches;
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(cs, &g);
+      stream = saved;
+      if (st == GDP_OK && e == cudaSuccess && cudaGraphInstantiate(&c.g, g, 0) != cudaSuccess) {
+        c.g = nullptr;
+        st = GDP_ERR_CUDA;
+      }
+      if (g) cudaGraphDestroy(g);
+      cudaStreamDestroy(cs);
+      if (st != GDP_OK || e != cudaSuccess || !c.g) {
+        cudaGetLastError();
+        return GDP_ERR_CUDA;
+      }
+      c.key = P;
+      c.tag = tag;
+    }
+    CK(cudaGraphLaunch(c.g, stream));
+    launches += c.kernels;
+    return GDP_OK;
+  }
   int refine(const double* B, const gdp_refine_opts* o);
   int launch_iteration();
   int export_mesh(int m, double* xy, int64_t cap_pts, int32_t* tri, int64_t cap_tri, int32_t* sub,
@@ -440,43 +499,155 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   return GDP_OK;
 }
 
-// Parallel insertion rounds of the points in P.pts (Algorithm 1 line 1 uses
-// them for the input points; the fixed-batch test hook for extra points).
-int PoolHost::insert_rounds(int stop_cons, int* rounds_out) {
-  int rounds = 0;
+// One parallel insertion round of the pending points in Q.pts (Algorithm 1
+// line 1 builds the CDT from them; the fixed-batch test hook inserts extra
+// points the same way): locate, one point per triangle, cavities, marks,
+// dependence, re-triangulation, and the points left go to Q.pts2.
+int PoolHost::launch_cdt_round(const Pool& Q, int stop_cons) {
+  CK(cudaMemsetAsync(&Q.ctrl->n_ins, 0, 2 * sizeof(unsigned long long), stream));
+  LAUNCH(*this, k_clear_marks, G, Q);
+  LAUNCH(*this, k_cdt_locate, G, Q, stop_cons, 0);
+  LAUNCH(*this, k_cdt_pick_count, G, Q);
+  LAUNCH(*this, k_cdt_pick_write, G, Q);
+  LAUNCH_GROW(*this, 1, Q);
+  LAUNCH_C(*this, k_survive, Q);
+  LAUNCH(*this, k_depend, G, Q);
+  LAUNCH(*this, k_offsets, G, Q);
+  LAUNCH_C(*this, k_insert<1>, Q);
+  LAUNCH_C(*this, k_link<1>, Q);
+  LAUNCH(*this, k_cdt_keep_count, G, Q);
+  LAUNCH(*this, k_cdt_keep_write, G, Q);
+  LAUNCH_B(*this, k_cdt_next, 1, 1, Q);
+  CK(cudaGetLastError());
+  return GDP_OK;
+}
+
+constexpr int CDT_GRAPH_ROUNDS = 8;   // even: the pending list is back in P.pts after a launch
+constexpr int CDT_FLIP_PASSES = 6;    // even: the flip list is back in flA after a launch
+
+int PoolHost::launch_flip_passes() {
+  for (int k = 0; k < CDT_FLIP_PASSES; ++k) {
+    const Pool Q = flip_pool((k & 1) == 0);
+    LAUNCH_C(*this, k_flip_propose, Q);
+    LAUNCH_C(*this, k_flip_do, Q);
+    LAUNCH_C(*this, k_flip_link, Q);
+    LAUNCH_B(*this, k_fl_next, 1, 1, Q);
+  }
+  CK(cudaGetLastError());
+  return GDP_OK;
+}
+
+// one split round on the pending points in Q.pts (the points left go to
+// Q.pts2), then flip passes; the split triangles are listed in flA
+int PoolHost::launch_split_round(const Pool& Q) {
+  Pool S = Q;
+  S.fl_nxt = flA;
+  CK(cudaMemsetAsync(&S.ctrl->n_ins, 0, 2 * sizeof(unsigned long long), stream));
+  LAUNCH(*this, k_cdt_locate, G, S, 0, 1);
+  LAUNCH(*this, k_cdt_pick_count, G, S);
+  LAUNCH(*this, k_cdt_pick_write, G, S);
+  LAUNCH(*this, k_split_prep, G, S);
+  LAUNCH(*this, k_offsets, G, S);
+  LAUNCH_C(*this, k_split, S);
+  LAUNCH_C(*this, k_split_link, S);
+  LAUNCH(*this, k_cdt_keep_count, G, S);
+  LAUNCH(*this, k_cdt_keep_write, G, S);
+  LAUNCH_B(*this, k_cdt_next, 1, 1, S);
+  LAUNCH_B(*this, k_fl_next, 1, 1, S);
+  CK(cudaGetLastError());
+  return launch_flip_passes();
+}
+
+// Rounds until every pending point is in.  With split, the rounds first
+// split triangles and flip (points strictly inside a triangle), and the
+// cavity rounds take whatever is left (points on edges).  Rounds run from
+// CUDA graphs (empty rounds and passes after the last point cost only their
+// launches), one at a time when kernels are timed or traced.  The round
+// number lives on the device and keeps counting across calls, so
+// per-triangle pick keys left by earlier rounds always compare lower.
+int PoolHost::insert_rounds(int stop_cons, int* rounds_out, bool split) {
+  if (cdt_round + 4096 / 2 >= 4095) {   // round numbers have 12 bits in the pick keys
+    CK(cudaMemsetAsync(P.tbest, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
+    cdt_round = 0;
+  }
+  if (set_ctrl_field(offsetof(Ctrl, round), cdt_round + 1) != GDP_OK) return GDP_ERR_CUDA;
   if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+  const int first = hctrl->round;
+  const bool trace = std::getenv("GDP_TRACE") != nullptr;
+  const bool use_graph = !prof && !trace;
   int last = hctrl->n_pts, stall = 0;
-  while (hctrl->n_pts > 0) {
-    ++rounds;
-    if (rounds >= 4000) return GDP_ERR_INTERNAL;
-    CK(cudaMemsetAsync(&P.ctrl->n_ins, 0, 2 * sizeof(unsigned long long), stream));
-    LAUNCH(*this, k_clear_marks, G, P);
-    LAUNCH(*this, k_cdt_locate, G, P, rounds, stop_cons);
-    LAUNCH(*this, k_cdt_pick_count, G, P, rounds);
-    LAUNCH(*this, k_cdt_pick_write, G, P, rounds);
-    LAUNCH_GROW(*this, 1, P);
-    LAUNCH_C(*this, k_survive, P);
-    LAUNCH(*this, k_depend, G, P);
-    LAUNCH(*this, k_offsets, G, P);
-    LAUNCH_C(*this, k_insert<1>, P);
-    LAUNCH_C(*this, k_link<1>, P);
-    LAUNCH(*this, k_cdt_keep_count, G, P);
-    LAUNCH(*this, k_cdt_keep_write, G, P);
-    CK(cudaGetLastError());
-    std::swap(P.pts, P.pts2);
+  if (split && hctrl->n_pts > 0) {
+    if (set_ctrl_field(offsetof(Ctrl, n_fl), 0) != GDP_OK ||
+        set_ctrl_field(offsetof(Ctrl, n_fl_next), 0) != GDP_OK ||
+        set_ctrl_field(offsetof(Ctrl, step), 1) != GDP_OK)
+      return GDP_ERR_CUDA;
+    int parity = 0;
+    while (hctrl->n_pts > 0) {
+      Pool Q = P;
+      if (parity) std::swap(Q.pts, Q.pts2);
+      int st;
+      if (use_graph) st = replay(g_split[parity], 0, [&] { return launch_split_round(Q); });
+      else st = launch_split_round(Q);
+      if (st != GDP_OK) return st;
+      parity ^= 1;
+      if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      for (int guard = 0; hctrl->n_fl > 0 && !hctrl->err; ++guard) {
+        if (guard > 4096) return GDP_ERR_INTERNAL;
+        st = use_graph ? replay(g_flip, 0, [&] { return launch_flip_passes(); }) : launch_flip_passes();
+        if (st != GDP_OK) return st;
+        if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      }
+      if (trace)
+        std::fprintf(stderr, "split round %d: pending %d cand %d inserted %llu flip passes %d\n",
+                     hctrl->round - first, last, hctrl->n_cand, hctrl->n_ins, hctrl->step);
+      if (hctrl->err) return hctrl->err;
+      if (hctrl->round - first >= 4096 / 2 - CDT_GRAPH_ROUNDS) return GDP_ERR_INTERNAL;
+      if (hctrl->n_cand == 0) break;   // the points left lie on edges
+      stall = hctrl->n_pts == last ? stall + 1 : 0;
+      if (stall > 64) return GDP_ERR_INTERNAL;
+      last = hctrl->n_pts;
+    }
+    if (parity) std::swap(P.pts, P.pts2);
+    // the cavity rounds start from clean marks and an empty candidate list
+    CK(cudaMemsetAsync(P.mark, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
+    if (set_ctrl_field(offsetof(Ctrl, prev_cand), 0) != GDP_OK) return GDP_ERR_CUDA;
     if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
-    if (std::getenv("GDP_TRACE"))
-      std::fprintf(stderr, "round %d: pending %d cand %d marks-ok %llu inserted %llu\n", rounds,
-                   last, hctrl->n_cand, hctrl->n_surv, hctrl->n_ins);
+  }
+  Pool Q = P;   // the odd rounds read pts2 and write pts
+  std::swap(Q.pts, Q.pts2);
+  int host_rounds = 0;
+  stall = 0;
+  while (hctrl->n_pts > 0) {
+    int st;
+    if (use_graph) {
+      st = replay(g_bw, stop_cons, [&] {
+        for (int k = 0; k < CDT_GRAPH_ROUNDS / 2; ++k) {
+          int r = launch_cdt_round(P, stop_cons);
+          if (r == GDP_OK) r = launch_cdt_round(Q, stop_cons);
+          if (r != GDP_OK) return r;
+        }
+        return (int)GDP_OK;
+      });
+    } else {
+      st = launch_cdt_round((host_rounds & 1) ? Q : P, stop_cons);
+      ++host_rounds;
+    }
+    if (st != GDP_OK) return st;
+    if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+    if (trace)
+      std::fprintf(stderr, "round %d: pending %d cand %d marks-ok %llu inserted %llu\n",
+                   hctrl->round - first, last, hctrl->n_cand, hctrl->n_surv, hctrl->n_ins);
     if (hctrl->err) return hctrl->err;
+    if (hctrl->round - first >= 4096 / 2 - CDT_GRAPH_ROUNDS) return GDP_ERR_INTERNAL;
     if (hctrl->n_pts == last) {
-      if (++stall > 64) return GDP_ERR_INTERNAL;
+      if (++stall > (use_graph ? 8 : 64)) return GDP_ERR_INTERNAL;
     } else {
       stall = 0;
     }
     last = hctrl->n_pts;
   }
-  if (rounds_out) *rounds_out = rounds;
+  cdt_round = hctrl->round;
+  if (rounds_out) *rounds_out = hctrl->round - first;
   return GDP_OK;
 }
 
@@ -488,8 +659,22 @@ int PoolHost::build_cdt() {
   hctrl->n_pts = (int)(tot_in + 4 * n_mesh);
   CK(cudaMemcpyAsync(P.ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
   int rounds = 0;
-  int st = insert_rounds(0, &rounds);
+  int st;
+  if ((st = alloc(&P.tstamp, (size_t)P.n_slots)) != GDP_OK) return st;
+  if ((st = alloc(&P.lstamp, (size_t)P.n_slots)) != GDP_OK) return st;
+  if ((st = alloc(&P.fprop, (size_t)P.n_slots)) != GDP_OK) return st;
+  if ((st = alloc(&flA, (size_t)P.n_slots)) != GDP_OK) return st;
+  if ((st = alloc(&flB, (size_t)P.n_slots)) != GDP_OK) return st;
+  st = insert_rounds(0, &rounds, true);
   if (st != GDP_OK) return st;
+  release(P.tstamp);
+  release(P.lstamp);
+  release(P.fprop);
+  release(flA);
+  release(flB);
+  P.tstamp = P.lstamp = P.fprop = nullptr;
+  flA = flB = nullptr;
+  LAUNCH(*this, k_vtri, G, P);
   stats.cdt_rounds = rounds;
   trace_check(P, stream, G, "points");
   // segment recovery: short segments with a small work space per segment,
@@ -897,7 +1082,7 @@ int gdp_mesh_insert_points(gdp_mesh* g, const double* xy, int64_t n) {
   std::memset(h.hctrl, 0, sizeof(Ctrl));
   h.hctrl->n_pts = (int)n;
   CK(cudaMemcpyAsync(h.P.ctrl, h.hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, h.stream));
-  st = h.insert_rounds(1, nullptr);
+  st = h.insert_rounds(1, nullptr, false);
   h.release(dids);
   if (st != GDP_OK) return st;
   if (h.pull_mi() != GDP_OK) return GDP_ERR_CUDA;

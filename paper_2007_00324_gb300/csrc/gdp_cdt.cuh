@@ -92,8 +92,30 @@ __global__ void k_cdt_init(Pool P) {
 }
 
 // every pending point walks to its triangle and bids for it
-__global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int round, int stop_cons) {
+// Which pending point a triangle takes this round (20 bits, larger first):
+// the frame vertices, then the point nearest the triangle's circumcentre.
+// A point there tends to lie in no neighbour's circumcircle, so its cavity
+// is often the triangle alone and neighbouring candidates rarely collide.
+// Any deterministic choice gives the same triangulation; FP32 is enough.
+__device__ __forceinline__ uint32_t pick_measure(const Pool& P, const MeshInfo& M, int v,
+                                                 const int4& T4) {
+  if (is_aux(M, v)) return 0xfffffu;
+  const float2 a = P.Vf[T4.x], b = P.Vf[T4.y], c = P.Vf[T4.z], q = P.Vf[v];
+  const float dx = b.x - a.x, dy = b.y - a.y, ex = c.x - a.x, ey = c.y - a.y;
+  const float d2 = dx * dx + dy * dy, e2 = ex * ex + ey * ey;
+  const float D = 2.0f * (dx * ey - dy * ex);
+  const float rx = q.x - a.x - (ey * d2 - dy * e2) / D;
+  const float ry = q.y - a.y - (dx * e2 - ex * d2) / D;
+  const float r2 = rx * rx + ry * ry;
+  const uint32_t bits = (r2 >= 0.0f && r2 < INFINITY) ? __float_as_uint(r2) : 0x7f800000u;
+  return 0xffffeu - min(bits >> 11, 0xffffeu);
+}
+
+// split: points on an edge of their triangle take no part in the pick (the
+// split rounds insert only points strictly inside a triangle)
+__global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int stop_cons, int split) {
   const int n = P.ctrl->n_pts;
+  const int round = P.ctrl->round;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int k = gt; k < n; k += gs) {
     const int v = P.pts[k];
@@ -124,16 +146,24 @@ __global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int round, int stop_c
       set_err(P.ctrl, S_INPUT);
       continue;
     }
+    if (split) {
+      const P2 q = pt(P, v);
+      bool edge = false;
+      for (int e = 0; e < 3; ++e)
+        edge |= orient(pt(P, comp(T4, mod3(e + 1))), pt(P, comp(T4, mod3(e + 2))), q) == 0;
+      if (edge) continue;
+    }
     const unsigned long long key = ((unsigned long long)round << 52) |
-                                   ((unsigned long long)(insert_prio(P.mi[m], v) >> 12) << 32) |
+                                   ((unsigned long long)pick_measure(P, P.mi[m], v, T4) << 32) |
                                    (unsigned)v;
     atomicMax(&P.tbest[t], key);
   }
 }
 
 // stable compaction of the winners of their triangle into the candidate list
-__global__ void __launch_bounds__(BS) k_cdt_pick_count(Pool P, int round) {
+__global__ void __launch_bounds__(BS) k_cdt_pick_count(Pool P) {
   __shared__ int sm[33];
+  const int round = P.ctrl->round;
   const Chunk ch = chunk_of(P.ctrl->n_pts);
   int cnt = 0;
   for (int k = ch.b0 + threadIdx.x; k < ch.b1; k += BS) {
@@ -145,8 +175,9 @@ __global__ void __launch_bounds__(BS) k_cdt_pick_count(Pool P, int round) {
   if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
 }
 
-__global__ void __launch_bounds__(BS) k_cdt_pick_write(Pool P, int round) {
+__global__ void __launch_bounds__(BS) k_cdt_pick_write(Pool P) {
   __shared__ int sm[33];
+  const int round = P.ctrl->round;
   const Chunk ch = chunk_of(P.ctrl->n_pts);
   int off = block_prefix(P.blk, blockIdx.x, sm);
   const int cap = P.cap_cand;
@@ -199,7 +230,255 @@ __global__ void __launch_bounds__(BS) k_cdt_keep_write(Pool P) {
     if (keep) P.pts2[off + r] = v;
     off += tot;
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) P.ctrl->n_pts = off;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) P.ctrl->n_pts_next = off;
+}
+
+// end of a round (one thread): the next round's count and number.  Every
+// block of the round's kernels read n_pts and round at its start, so they
+// change only here, between kernels.
+__global__ void k_cdt_next(Pool P) {
+  if (P.ctrl->n_pts > 0) ++P.ctrl->round;
+  P.ctrl->n_pts = P.ctrl->n_pts_next;
+}
+
+// ---------------------------------------------------------------- split + flip rounds
+// Point insertion for the initial CDT, before any segment is inserted: every
+// triangle that holds pending points is split in three at one of them (no
+// two splits touch the same triangle, so all candidates go in), and parallel
+// Lawson flips of edges that fail the incircle test (with simulation of
+// simplicity) restore the Delaunay triangulation, which is unique.  Each
+// pass rewrites whole triangles in place and records where every outer edge
+// went (newref, indexed by the old slot and edge); a link kernel then
+// repairs the neighbour references across edges whose other side was also
+// rewritten (tstamp == pass) and writes back the others.
+
+// push t for the next flip pass once (pass = the pass that will read it)
+__device__ __forceinline__ void fl_push(const Pool& P, int t, int pass) {
+  if (atomicMax(&P.lstamp[t], pass) < pass) P.fl_nxt[atomicAdd(&P.ctrl->n_fl_next, 1)] = t;
+}
+
+// per-mesh candidate ranges and slot counts (two new triangles per split),
+// laid out like k_depend's block sums so that k_offsets can scan them
+__global__ void __launch_bounds__(BS) k_split_prep(Pool P) {
+  __shared__ int sm[33];
+  const int n = P.ctrl->n_cand;
+  const Chunk ch = chunk_of(n);
+  int se = 0;
+  for (int i = ch.b0 + threadIdx.x; i < ch.b1; i += BS) {
+    const int v = P.c_elem[i], t = P.c_loc[i];
+    const int4 T4 = P.T[t];
+    const int m = T4.w >> 4;
+    const P2 q = pt(P, v);
+    const bool in = orient(pt(P, T4.y), pt(P, T4.z), q) > 0 && orient(pt(P, T4.z), pt(P, T4.x), q) > 0 &&
+                    orient(pt(P, T4.x), pt(P, T4.y), q) > 0;
+    P.c_mesh[i] = m;
+    P.c_vid[i] = v;
+    P.c_final[i] = in;
+    P.c_extra[i] = in ? 2 : 0;
+    if (i == 0 || (P.T[P.c_loc[i - 1]].w >> 4) != m) P.mi[m].first_cand = i;
+    if (i == n - 1 || (P.T[P.c_loc[i + 1]].w >> 4) != m) P.mi[m].last_cand = i;
+    se += in ? 2 : 0;
+  }
+  se = block_sum(se, sm);
+  if (threadIdx.x == 0) {
+    P.blk[blockIdx.x] = se;
+    P.blk[gridDim.x + blockIdx.x] = 0;
+  }
+}
+
+// triangle t = (a0, a1, a2) split at p: T_e = (p, a[e+1], a[e+2]) keeps the
+// old edge e as its edge 0; T_0 reuses the slot of t
+__global__ void __launch_bounds__(BS) k_split(Pool P) {
+  const int n = P.ctrl->n_cand;
+  const int step = P.ctrl->step;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int i = gt; i < n; i += gs) {
+    const int m = P.c_mesh[i];
+    const MeshInfo& M = P.mi[m];
+    const int f = M.first_cand, l = M.last_cand;
+    int totE, totV;
+    mesh_totals(P, f, l, totE, totV);
+    const bool ok = M.tri_count + totE <= M.tri_cap;
+    if (i == f) {
+      P.mi[m].ins_ok = ok ? 1 : 0;
+      if (!ok) P.mi[m].status = S_NOMEM;
+    }
+    if (!P.c_final[i] || !ok) continue;
+    const int t = P.c_loc[i], v = P.c_vid[i];
+    const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
+    const int4 T4 = P.T[t];
+    const int4 N4 = P.N[t];
+    const int s[3] = {t, base, base + 1};
+    for (int e = 0; e < 3; ++e) {
+      P.T[s[e]] = make_int4(v, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), m << 4);
+      P.N[s[e]] = make_int4(comp(N4, e), (s[mod3(e + 1)] << 2) | 2, (s[mod3(e + 2)] << 2) | 1, 0);
+      P.newref[(t << 2) | e] = s[e] << 2;
+      P.tstamp[s[e]] = step;
+      fl_push(P, s[e], step + 1);
+    }
+    P.loc[v] = -1;
+  }
+}
+
+// outer neighbours of the split triangles, then per-mesh counts
+__global__ void __launch_bounds__(BS) k_split_link(Pool P) {
+  const int n = P.ctrl->n_cand;
+  const int step = P.ctrl->step;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  int ins = 0;
+  for (int i = gt; i < n; i += gs) {
+    const int m = P.c_mesh[i];
+    const MeshInfo& M = P.mi[m];
+    const bool ok = M.ins_ok;
+    if (P.c_final[i] && ok) {
+      ++ins;
+      const int t = P.c_loc[i];
+      const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[M.first_cand]);
+      for (int e = 0; e < 3; ++e) {
+        const int s = e == 0 ? t : base + e - 1;
+        const int r = P.N[s].x;
+        if (r < 0) continue;
+        if (P.tstamp[r >> 2] == step) P.N[s].x = P.newref[r];
+        else *comp_ptr(&P.N[r >> 2], r & 3) = s << 2;
+      }
+    }
+    if (i == M.last_cand && ok) {
+      int totE, totV;
+      mesh_totals(P, M.first_cand, i, totE, totV);
+      P.mi[m].tri_count = M.tri_count + totE;
+    }
+  }
+  for (int o = 16; o; o >>= 1) ins += __shfl_xor_sync(0xffffffffu, ins, o);
+  if ((threadIdx.x & 31) == 0 && ins) atomicAdd(&P.ctrl->n_ins, (unsigned long long)ins);
+}
+
+// flip priority from mesh-local slot numbers, so that a mesh flips the same
+// way alone and in a batch (keys of earlier passes compare lower)
+__device__ __forceinline__ unsigned long long flip_key(const Pool& P, int step, int t, int prop) {
+  const int lt = t - P.mi[P.T[t].w >> 4].tri_base;   // the mesh bits of a slot never change
+  return ((unsigned long long)step << 44) | ((unsigned long long)(hash32((uint32_t)lt) & 0xfffu) << 32) |
+         (unsigned)((lt << 2) | (prop & 3));
+}
+
+// each listed triangle proposes its first edge whose opposite vertex lies in
+// its circumcircle; the proposal marks both triangles (atomicMax)
+__global__ void __launch_bounds__(BS) k_flip_propose(Pool P) {
+  const int n = P.ctrl->n_fl;
+  const int step = P.ctrl->step;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int k = gt; k < n; k += gs) {
+    const int t = P.fl_cur[k];
+    const int4 T4 = P.T[t];
+    const int4 N4 = P.N[t];
+    int prop = -1, t2 = -1;
+    const P2 a = pt(P, T4.x), b = pt(P, T4.y), c = pt(P, T4.z);
+    for (int e = 0; e < 3 && prop < 0; ++e) {
+      const int r = comp(N4, e);
+      if (r < 0) continue;
+      const int d = comp(P.T[r >> 2], r & 3);
+      if (incircle(a, b, c, pt(P, d)) > 0) {
+        prop = (t << 2) | e;
+        t2 = r >> 2;
+      }
+    }
+    P.fprop[k] = prop;
+    if (prop >= 0) {
+      const unsigned long long key = flip_key(P, step, t, prop);
+      atomicMax(&P.mark[t], key);
+      atomicMax(&P.mark[t2], key);
+    }
+  }
+}
+
+// proposals that own both marks flip; the others try again next pass
+__global__ void __launch_bounds__(BS) k_flip_do(Pool P) {
+  const int n = P.ctrl->n_fl;
+  const int step = P.ctrl->step;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int k = gt; k < n; k += gs) {
+    const int prop = P.fprop[k];
+    if (prop < 0) continue;
+    const int t = prop >> 2, e = prop & 3;
+    const unsigned long long key = flip_key(P, step, t, prop);
+    // t and t2 are read only once this proposal owns them: a triangle whose
+    // mark another proposal holds may be rewritten by it meanwhile
+    if (P.mark[t] != key) {
+      fl_push(P, t, step + 1);
+      continue;
+    }
+    const int4 T4 = P.T[t];
+    const int4 N4 = P.N[t];
+    const int r = comp(N4, e);
+    const int t2 = r >> 2, e2 = r & 3;
+    if (P.mark[t2] != key) {
+      fl_push(P, t, step + 1);
+      continue;
+    }
+    const int4 U4 = P.T[t2];
+    const int4 M4 = P.N[t2];
+    const int a = comp(T4, e), b = comp(T4, mod3(e + 1)), c = comp(T4, mod3(e + 2));
+    const int d = comp(U4, e2);
+    const int nab = comp(N4, mod3(e + 2)), nca = comp(N4, mod3(e + 1));
+    const int nbd = comp(M4, mod3(e2 + 1)), ndc = comp(M4, mod3(e2 + 2));
+    const int info = T4.w & ~15;
+    // (a, b, c) + (d, c, b) -> (a, b, d) + (a, d, c)
+    P.T[t] = make_int4(a, b, d, info);
+    P.N[t] = make_int4(nbd, (t2 << 2) | 2, nab, 0);
+    P.T[t2] = make_int4(a, d, c, info);
+    P.N[t2] = make_int4(ndc, nca, (t << 2) | 1, 0);
+    P.newref[(t << 2) | mod3(e + 2)] = (t << 2) | 2;      // ab
+    P.newref[(t << 2) | mod3(e + 1)] = (t2 << 2) | 1;     // ca
+    P.newref[(t2 << 2) | mod3(e2 + 1)] = t << 2;          // bd
+    P.newref[(t2 << 2) | mod3(e2 + 2)] = t2 << 2;         // dc
+    P.tstamp[t] = step;
+    P.tstamp[t2] = step;
+    P.fprop[k] = -2 - prop;
+    fl_push(P, t, step + 1);
+    fl_push(P, t2, step + 1);
+  }
+}
+
+__device__ __forceinline__ void flip_fix(const Pool& P, int x, int idx, int step) {
+  const int r = comp(P.N[x], idx);
+  if (r < 0) return;
+  if (P.tstamp[r >> 2] == step) *comp_ptr(&P.N[x], idx) = P.newref[r];
+  else *comp_ptr(&P.N[r >> 2], r & 3) = (x << 2) | idx;
+}
+
+// outer neighbours of the flipped pairs
+__global__ void __launch_bounds__(BS) k_flip_link(Pool P) {
+  const int n = P.ctrl->n_fl;
+  const int step = P.ctrl->step;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int k = gt; k < n; k += gs) {
+    const int f = P.fprop[k];
+    if (f > -2) continue;
+    const int t = (-2 - f) >> 2;
+    const int t2 = P.N[t].y >> 2;
+    flip_fix(P, t, 0, step);
+    flip_fix(P, t, 2, step);
+    flip_fix(P, t2, 0, step);
+    flip_fix(P, t2, 1, step);
+  }
+}
+
+// between passes (one thread): the list just built becomes the current one
+__global__ void k_fl_next(Pool P) {
+  P.ctrl->n_fl = P.ctrl->n_fl_next;
+  P.ctrl->n_fl_next = 0;
+  ++P.ctrl->step;
+}
+
+// a triangle at every vertex (the segment walks start there)
+__global__ void __launch_bounds__(BS) k_vtri(Pool P) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int t = gt; t < P.n_slots; t += gs) {
+    const int4 T4 = P.T[t];
+    if (T4.w < 0 || (T4.w & INFO_DEAD) || T4.x < 0) continue;
+    P.vtri[T4.x] = t;
+    P.vtri[T4.y] = t;
+    P.vtri[T4.z] = t;
+  }
 }
 
 // ---------------------------------------------------------------- segment recovery

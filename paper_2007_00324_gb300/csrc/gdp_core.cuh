@@ -68,10 +68,14 @@ struct Ctrl {
   int32_t prev_cand;     // candidates whose marks must be cleared
   int32_t n_raw;         // elements found by the last scan
   int32_t n_pts;         // CDT: points not yet inserted
+  int32_t n_pts_next;    // CDT: points left after this round (moved to n_pts between rounds)
   int32_t n_segs;        // CDT: segments not yet recovered
   int32_t changed;       // flood fill progress
   int32_t err;           // first hard error (status code)
-  int32_t round;
+  int32_t round;         // CDT: insertion round (keys of earlier rounds compare lower)
+  int32_t n_fl;          // CDT: triangles whose edges the current flip pass checks
+  int32_t n_fl_next;     // CDT: triangles pushed for the next flip pass
+  int32_t step;          // CDT: split / flip pass number (stamps, flip keys)
   unsigned long long tot_cand, tot_ins, iters, n_ins, n_surv;
 };
 
@@ -129,6 +133,12 @@ struct Pool {
   int32_t* pts2;
   int32_t* loc;          // per vertex: containing triangle, -1 once inserted
   unsigned long long* tbest;
+  // split + flip construction rounds
+  int32_t* tstamp;       // per slot: the split / flip pass that last rewrote it
+  int32_t* lstamp;       // per slot: the flip pass whose list holds it
+  int32_t* fl_cur;       // triangles checked by this flip pass (ctrl->n_fl)
+  int32_t* fl_nxt;       // triangles pushed for the next pass (ctrl->n_fl_next)
+  int32_t* fprop;        // per list entry: proposed flip t << 2 | e, -1 none, -2 - prop done
   int32_t* segq;         // segments still to recover
   unsigned long long* segmark;
   uint8_t* ext;
