@@ -34,20 +34,46 @@ CONFIG = {"workload": "mid: unit square + 100,000 uniform FP64 points + 1,000 ra
                       "segments, B=sqrt(2)", "points": 100_004, "segments": 1_004, "B": SQ2,
           "l2": "flushed between steps (512 MB write)"}
 
-# Algorithmic bytes per unit of work of each kernel ("Roofline"):
-# the bytes one unit must read and write given the data layout, counted once.
-# unit: "cand" = one splitting point / construction point handled by the launch,
-#       "slot" = one triangle slot scanned, "pt" = one pending construction point.
-KERNEL_BYTES = {
-    # element triangle (16) + 3 vertices (48) + ~1.5 walk steps x 64 + cavity of ~4
-    # triangles (T+N 32 each) + ~6 tested neighbours (T 16 + 3 vertices 48) + list
-    # writes (4 per cavity triangle, 16 per boundary edge) + marks (8 per cavity
-    # triangle) + the candidate record (48)
-    "k_grow<0>": ("cand", 16 + 48 + 96 + 4 * 32 + 6 * 64 + 4 * 4 + 6 * 16 + 4 * 8 + 48),
-    "k_grow<1>": ("cand", 16 + 4 * 32 + 6 * 64 + 4 * 4 + 6 * 16 + 4 * 8 + 48),
-    # walk of a pending point: its vertex (16) + loc (4) + ~2 steps x 64 + tbest atomic (8)
-    "k_cdt_locate": ("pt", 16 + 4 + 2 * 64 + 8),
-}
+# Algorithmic bytes of the dominant kernel, k_grow<0> (cavity growth of the
+# refinement, Sec. 5.2): what each grown candidate must read and write once,
+# from the device layout (triangle T/N 16 B each, vertex 16 B FP64 + 8 B FP32
+# copy, marks 8 B), with the work counters the library reports:
+#   per candidate  134 = element id 4 + element triangle 16 + its 3 vertices 48
+#                        + candidate record written 66
+#   per walk step   56 = T 16 + N 16 + one new vertex 24
+#   per cavity tri  84 = T + N 32 + neighbour test (T 16 + apex 24) + list 4 + mark 8
+#   per boundary edge 56 = neighbour test 40 + boundary record 16
+GROW_BYTES = {"candidate": 134, "walk_step": 56, "cavity_tri": 84, "boundary_edge": 56}
+GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_grow0_mid_traffic.md")
+
+
+def grow_bytes(st) -> float:
+    return (GROW_BYTES["candidate"] * st["grown"] + GROW_BYTES["walk_step"] * st["walk_steps"] +
+            GROW_BYTES["cavity_tri"] * st["cavity_tris"] + GROW_BYTES["boundary_edge"] * st["cavity_edges"])
+
+
+def grow_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in GROW_SOURCES:
+        with open(os.path.join(ROOT, "paper_2007_00324_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per k_grow<0> launch from the committed ncu summary, or None
+    when the kernel's sources changed since it was captured."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            kv = dict(line.split(":", 1) for line in f
+                      if line.startswith(("source-hash:", "dram-bytes-per-launch:")))
+        if kv["source-hash"].strip() != grow_source_hash():
+            return None
+        return float(kv["dram-bytes-per-launch"])
+    except Exception:
+        return None
 
 
 def parse():
@@ -192,7 +218,7 @@ def main():
 
     def step():
         m = gdp.Mesh(xy_d, seg_d, stream=stream, device=True)
-        s = m.refine(args.B)
+        s = m.refine(args.B, flags=gdp.REFINE_TIME_GROW)
         return m, s
 
     for _ in range(max(args.warmup, 3)):
@@ -206,6 +232,8 @@ def main():
 
     times, steiner, launches = [], 0, 0
     stats = None
+    grow = {"grow_ms": 0.0, "grow_launches": 0, "grown": 0, "walk_steps": 0, "cavity_tris": 0,
+            "cavity_edges": 0}
     barrier()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -219,6 +247,8 @@ def main():
             times.append(e0.elapsed_time(e1))
             steiner += stats["n_steiner"]
             launches += stats["launches"]
+            for k in grow:
+                grow[k] += stats[k]
             del m
         barrier()
     tot_ms = sum(times)
@@ -263,25 +293,22 @@ def main():
     tot_k = sum(v[0] for v in kt.values())
     top = max(kt.items(), key=lambda kv: kv[1][0])
     peak, peak_kind = peaks()
-    roof = None
-    if top[0] in KERNEL_BYTES:
-        unit, per = KERNEL_BYTES[top[0]]
-        units = ps["candidates"] if top[0] == "k_grow<0>" else None
-        if top[0] == "k_grow<1>":
-            units = ps["n_in_pts"] + 4     # every construction point is a candidate at least once
-        if top[0] == "k_cdt_locate":
-            units = None
-        if units:
-            ms = top[1][0]
-            gbs = units * per / (ms / 1000.0) / 1e9
-            roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                    "frac": gbs / peak, "traffic": None, "kernel": top[0],
-                    "kernel_ms_per_launch": ms / top[1][1], "share": top[1][0] / tot_k,
-                    "peak_source": peak_kind}
-    if roof is None:
-        roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-                "traffic": None, "kernel": top[0], "share": top[1][0] / tot_k,
-                "peak_source": peak_kind}
+    # roofline of k_grow<0> over the timed steps: algorithmic bytes from the
+    # work counters / device time from the events recorded around each launch
+    n_l = max(grow["grow_launches"], 1)
+    by = grow_bytes(grow)
+    gbs = by / (grow["grow_ms"] / 1000.0) / 1e9 if grow["grow_ms"] > 0 else None
+    tr = measured_traffic()
+    roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": (gbs / peak) if gbs else None, "traffic": tr,
+            "kernel": "k_grow<0>", "algorithmic_bytes_per_launch": by / n_l,
+            "kernel_ms_per_launch": grow["grow_ms"] / n_l, "launches": grow["grow_launches"],
+            "share_of_kernel_time": kt.get("k_grow<0>", (0.0, 0))[0] / tot_k,
+            "largest_kernel": top[0],
+            "peak_source": "measured (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "mean_cavity_tris": grow["cavity_tris"] / max(grow["grown"], 1),
+            "mean_boundary_edges": grow["cavity_edges"] / max(grow["grown"], 1),
+            "mean_walk_steps": grow["walk_steps"] / max(grow["grown"], 1)}
 
     if rank != 0:
         if world > 1:

@@ -71,7 +71,20 @@ typedef struct {
     double refine_ms;     /* device time of the refinement loop */
     double cdt_ms;        /* device time of the initial CDT */
     int64_t launches;     /* kernel launches of this object since creation */
+    /* refinement work of the cavity kernel k_grow (candidates that fit in
+     * their own slot), summed over iterations:                           */
+    int64_t grown;        /* candidates whose cavity was grown */
+    int64_t cavity_tris;  /* triangles in those cavities */
+    int64_t cavity_edges; /* boundary edges of those cavities */
+    int64_t walk_steps;   /* point-location steps of circumcentres */
+    /* with GDP_REFINE_TIME_GROW: device time of every k_grow launch of the
+     * refinement, from CUDA events recorded around it inside the graph    */
+    double grow_ms;
+    int64_t grow_launches;
 } gdp_stats;
+
+/* gdp_refine_opts.flags */
+#define GDP_REFINE_TIME_GROW 1
 
 /* Build the CDT of a PSLG on the GPU (Algorithm 1 line 1).
  *   xy:  2*n_pts doubles, host;   seg: 2*n_seg int32 indices, host (may be NULL if 0)

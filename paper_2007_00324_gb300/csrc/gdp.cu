@@ -220,8 +220,6 @@ struct PoolHost {
   Ctrl* hctrl = nullptr;          // pinned
   std::vector<void*> allocs;
   gdp_stats stats{};
-  cudaGraphExec_t graph = nullptr;
-  int graph_iters = 0;
   // construction rounds replayed from CUDA graphs, each captured for the
   // pool layout it was recorded with (key) and a variant tag
   struct Cached {
@@ -230,7 +228,8 @@ struct PoolHost {
     int tag = -1;
     int kernels = 0;
   };
-  Cached g_bw, g_split[2], g_flip;
+  Cached g_bw, g_split[2], g_flip, g_refine;
+  bool capturing = false;
   int cdt_round = 0;              // last construction round used (device keys)
   int32_t* flA = nullptr;         // flip lists (construction only)
   int32_t* flB = nullptr;
@@ -238,7 +237,6 @@ struct PoolHost {
   // per-kernel timing (profiling mode) and launch counting
   bool prof = false;
   long long launches = 0;
-  int kernels_per_iter = 10;   // launch_iteration
   struct Pending { const char* name; cudaEvent_t a, b; };
   std::vector<Pending> pend;
   std::vector<std::pair<std::string, std::pair<double, long long>>> ktimes;
@@ -277,8 +275,8 @@ struct PoolHost {
 
   ~PoolHost() {
     prof_flush();
-    if (graph) cudaGraphExecDestroy(graph);
-    for (Cached* c : {&g_bw, &g_split[0], &g_split[1], &g_flip})
+    for (cudaEvent_t e : tg) cudaEventDestroy(e);
+    for (Cached* c : {&g_bw, &g_split[0], &g_split[1], &g_flip, &g_refine})
       if (c->g) cudaGraphExecDestroy(c->g);
     for (void* p : allocs) cudaFree(p);
     if (hctrl) cudaFreeHost(hctrl);
@@ -354,7 +352,9 @@ struct PoolHost {
       stream = cs;
       int st = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess ? GDP_OK
                                                                                            : GDP_ERR_CUDA;
+      capturing = true;
       if (st == GDP_OK) st = body();
+      capturing = false;
       c.kernels = (int)(launches - saved_launches);
       launches = saved_launches;
       cudaGraph_t g = nullptr;
@@ -378,7 +378,11 @@ struct PoolHost {
     return GDP_OK;
   }
   int refine(const double* B, const gdp_refine_opts* o);
-  int launch_iteration();
+  int launch_iteration(int k);
+  // GDP_REFINE_TIME_GROW: an event pair around k_grow<0> per iteration slot of the graph
+  bool time_grow = false;
+  std::vector<cudaEvent_t> tg;
+  int add_grow_times(int iters);
   int export_mesh(int m, double* xy, int64_t cap_pts, int32_t* tri, int64_t cap_tri, int32_t* sub,
                   int64_t cap_seg, int64_t* n_pts, int64_t* n_tri, int64_t* n_seg);
 };
@@ -792,16 +796,34 @@ int PoolHost::build_cdt() {
   return worst;
 }
 
-int PoolHost::launch_iteration() {
+// one refinement iteration; k = its position in the graph (event pair)
+int PoolHost::launch_iteration(int k) {
   LAUNCH(*this, k_scan_count, G, P);
   LAUNCH(*this, k_scan_write, G, P);
-  LAUNCH_GROW(*this, 0, P);
+  const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k], stream, rec));
+  LAUNCH_C(*this, k_grow<0>, P);
+  if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k + 1], stream, rec));
+  LAUNCH_B(*this, k_grow_big<0>, LANES_A / 32, 32, P, 0);
+  LAUNCH_B(*this, k_grow_big<0>, LANES_B, 1, P, 1);
   LAUNCH_C(*this, k_survive, P);
   LAUNCH(*this, k_depend, G, P);
   LAUNCH(*this, k_offsets, G, P);
   LAUNCH_C(*this, k_insert<0>, P);
   LAUNCH_C(*this, k_link<0>, P);
   return cudaGetLastError() == cudaSuccess ? GDP_OK : GDP_ERR_CUDA;
+}
+
+// after a synchronised replay of `iters` iterations: accumulate k_grow times
+int PoolHost::add_grow_times(int iters) {
+  if (!time_grow) return GDP_OK;
+  for (int k = 0; k < iters; ++k) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, tg[2 * k], tg[2 * k + 1]));
+    stats.grow_ms += ms;
+    stats.grow_launches += 1;
+  }
+  return GDP_OK;
 }
 
 int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
@@ -826,41 +848,38 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   CK(cudaMemcpyAsync(P.ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
   CK(cudaEventRecord(ev0, stream));
   int status = GDP_OK;
-  if (giters > 0 && !prof) {
-    if (!graph || graph_iters != giters) {
-      if (graph) cudaGraphExecDestroy(graph);
-      graph = nullptr;
-      cudaStream_t cs;
-      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-      cudaStream_t saved = stream;
-      stream = cs;
-      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      const long long saved_launches = launches;
-      const bool saved_prof = prof;
-      prof = false;
-      for (int k = 0; k < giters; ++k) launch_iteration();
-      prof = saved_prof;
-      launches = saved_launches;
-      cudaGraph_t g;
-      CK(cudaStreamEndCapture(cs, &g));
-      CK(cudaGraphInstantiate(&graph, g, 0));
-      CK(cudaGraphDestroy(g));
-      stream = saved;
-      CK(cudaStreamDestroy(cs));
-      graph_iters = giters;
+  time_grow = (d.flags & GDP_REFINE_TIME_GROW) != 0;
+  stats.grow_ms = 0;
+  stats.grow_launches = 0;
+  if (time_grow) {
+    const size_t need = 2 * (size_t)std::max(giters, 1);
+    while (tg.size() < need) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      tg.push_back(e);
     }
+  }
+  if (giters > 0 && !prof) {
     for (;;) {
-      CK(cudaGraphLaunch(graph, stream));
-      launches += (long long)kernels_per_iter * graph_iters;
+      const int st = replay(g_refine, 2 * giters + (time_grow ? 1 : 0), [&] {
+        for (int k = 0; k < giters; ++k) {
+          const int r = launch_iteration(k);
+          if (r != GDP_OK) return r;
+        }
+        return (int)GDP_OK;
+      });
+      if (st != GDP_OK) return st;
       if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (add_grow_times(giters) != GDP_OK) return GDP_ERR_CUDA;
       if (hctrl->err) { status = hctrl->err; break; }
       if (hctrl->n_cand == 0) break;
       if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
     }
   } else {
     for (;;) {
-      if (launch_iteration() != GDP_OK) return GDP_ERR_CUDA;
+      if (launch_iteration(0) != GDP_OK) return GDP_ERR_CUDA;
       if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (add_grow_times(1) != GDP_OK) return GDP_ERR_CUDA;
       if (hctrl->err) { status = hctrl->err; break; }
       if (hctrl->n_cand == 0) break;
       if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
@@ -876,6 +895,10 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   stats.iterations = (int64_t)hctrl->iters;
   stats.candidates = (int64_t)hctrl->tot_cand;
   stats.inserted = (int64_t)hctrl->tot_ins;
+  stats.grown = (int64_t)hctrl->n_grown;
+  stats.cavity_tris = (int64_t)hctrl->sum_cav;
+  stats.cavity_edges = (int64_t)hctrl->sum_bnd;
+  stats.walk_steps = (int64_t)hctrl->sum_walk;
   long long st = 0, nt = 0;
   for (auto& M : hmi) {
     st += M.steiner;

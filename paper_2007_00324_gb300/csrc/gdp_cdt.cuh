@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int stop_cons, int sp
     const int v = P.pts[k];
     const double2 p = P.V[v];
     int bt, be;
-    const int t = walk(P, P.loc[v], pt(P, v), false, bt, be);
+    int steps = 0;
+    const int t = walk(P, P.loc[v], pt(P, v), false, bt, be, steps);
     if (t < 0) {
       set_err(P.ctrl, t == -2 ? S_WALK : S_INTERNAL);
       continue;

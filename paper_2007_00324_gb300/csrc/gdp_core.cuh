@@ -77,6 +77,8 @@ struct Ctrl {
   int32_t n_fl_next;     // CDT: triangles pushed for the next flip pass
   int32_t step;          // CDT: split / flip pass number (stamps, flip keys)
   unsigned long long tot_cand, tot_ins, iters, n_ins, n_surv;
+  // refinement work counters (algorithmic bytes of the cavity kernels)
+  unsigned long long n_grown, sum_cav, sum_bnd, sum_walk;
 };
 
 struct Pool {

@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
 // hull -- (bt, be) is that edge -- or -2 at the step limit.  In a CDT every
 // step across a locally Delaunay edge lowers the power of p with respect to
 // the current circumcircle, so the walk cannot cycle.
-__device__ int walk(const Pool& P, int t, const P2& p, bool stop_cons, int& bt, int& be) {
+__device__ int walk(const Pool& P, int t, const P2& p, bool stop_cons, int& bt, int& be, int& steps) {
   int from = -1;
 #ifdef GDP_DIAG
   const long long c0 = clock64();
@@ -369,6 +369,7 @@ __device__ int walk(const Pool& P, int t, const P2& p, bool stop_cons, int& bt, 
     if (next >= 0) {
       from = nfrom;
       t = next;
+      ++steps;
       continue;
     }
 #ifdef GDP_DIAG
@@ -486,8 +487,13 @@ __device__ __forceinline__ bool is_split_edge(const int4& rec, int2 sub) {
 // MODE 1: given points (element = vertex id, c_loc = located triangle).
 // Returns G_OVF when the cavity does not fit B, else G_OK (c_state tells
 // whether the candidate was grown).
+// work of the grown candidates, summed per thread (see k_grow)
+struct GrowAcc {
+  unsigned long long grown = 0, cav = 0, bnd = 0, walk = 0;
+};
+
 template <int MODE>
-__device__ int grow_cand(const Pool& P, int i, const CavBuf& B) {
+__device__ int grow_cand(const Pool& P, int i, const CavBuf& B, GrowAcc& acc) {
   P.c_ncav[i] = 0;
   P.c_nbnd[i] = 0;
   P.c_state[i] = C_FAIL;
@@ -514,7 +520,9 @@ __device__ int grow_cand(const Pool& P, int i, const CavBuf& B) {
       p = circumcenter(tt);
       key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
       int bt = -1, be = -1;
-      const int r = walk(P, t, P2{p, to_f(p, M.org)}, true, bt, be);
+      int steps = 0;
+      const int r = walk(P, t, P2{p, to_f(p, M.org)}, true, bt, be, steps);
+      acc.walk += steps;
       if (r == -2) {
         P.c_mesh[i] = m;
         set_err(P.ctrl, S_WALK);
@@ -585,18 +593,38 @@ __device__ int grow_cand(const Pool& P, int i, const CavBuf& B) {
   P.c_vid[i] = vid;
   P.c_vseg[i] = (sub.x >= 0) ? seg_of_sub(P, P.mi[m], sub.x, sub.y) : -1;
   P.c_state[i] = C_GROWN;
+  acc.grown += 1;
+  acc.cav += nc;
+  acc.bnd += nb;
   return G_OK;
+}
+
+__device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a) {
+  for (int o = 16; o; o >>= 1) {
+    a.grown += __shfl_xor_sync(0xffffffffu, a.grown, o);
+    a.cav += __shfl_xor_sync(0xffffffffu, a.cav, o);
+    a.bnd += __shfl_xor_sync(0xffffffffu, a.bnd, o);
+    a.walk += __shfl_xor_sync(0xffffffffu, a.walk, o);
+  }
+  if ((threadIdx.x & 31) == 0 && a.grown + a.walk) {
+    atomicAdd(&P.ctrl->n_grown, a.grown);
+    atomicAdd(&P.ctrl->sum_cav, a.cav);
+    atomicAdd(&P.ctrl->sum_bnd, a.bnd);
+    atomicAdd(&P.ctrl->sum_walk, a.walk);
+  }
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(BS) k_grow(Pool P) {
   const int n = P.ctrl->n_cand;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  GrowAcc acc;
   for (int i = gt; i < n; i += gs) {
     P.c_big[i] = -1;
     const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
-    if (grow_cand<MODE>(P, i, B) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+    if (grow_cand<MODE>(P, i, B, acc) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
   }
+  if (MODE == 0) acc_flush(P, acc);   // every thread of the block reaches this
 }
 
 // Cavities that outgrew their slot (tier 0) or their tier-A lane (tier 1):
@@ -617,7 +645,8 @@ __global__ void k_grow_big(Pool P, int TIER) {
                            : (size_t)l * 2 * CAP_A;
   P.c_big[i] = (int)off;
   const CavBuf B{P.big_cav + off, P.big_bnd + off, P.big_hash + hoff, cap, 2 * cap - 1};
-  if (grow_cand<MODE>(P, i, B) == G_OVF) {
+  GrowAcc acc;   // the work counters cover k_grow only
+  if (grow_cand<MODE>(P, i, B, acc) == G_OVF) {
     P.c_big[i] = -1;
     if (TIER == 0) atomicMin(&P.lane[LANES_A + (i & (LANES_B - 1))], i);
     else set_err(P.ctrl, S_CAPACITY);

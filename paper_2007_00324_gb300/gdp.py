@@ -36,7 +36,9 @@ class Stats(C.Structure):
     _fields_ = [("n_in_pts", C.c_int64), ("n_steiner", C.c_int64), ("n_tris", C.c_int64),
                 ("n_subsegs", C.c_int64), ("iterations", C.c_int64), ("candidates", C.c_int64),
                 ("inserted", C.c_int64), ("cdt_rounds", C.c_int64), ("refine_ms", C.c_double),
-                ("cdt_ms", C.c_double), ("launches", C.c_int64)]
+                ("cdt_ms", C.c_double), ("launches", C.c_int64), ("grown", C.c_int64),
+                ("cavity_tris", C.c_int64), ("cavity_edges", C.c_int64), ("walk_steps", C.c_int64),
+                ("grow_ms", C.c_double), ("grow_launches", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -105,9 +107,12 @@ def _p(a):
     return C.c_void_p(a.ctypes.data) if a is not None else None
 
 
-def _opts(B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0):
+REFINE_TIME_GROW = 1   # gdp_refine_opts.flags: time every k_grow launch with CUDA events
+
+
+def _opts(B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, flags=0):
     return RefineOpts(B=B, max_len=0.0, max_iter=max_iter, cand_cap=cand_cap,
-                      graph_iters=graph_iters, flags=0)
+                      graph_iters=graph_iters, flags=flags)
 
 
 def _stream_handle(stream):
@@ -150,9 +155,9 @@ class Mesh:
         except Exception:
             pass
 
-    def refine(self, B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, check=True):
+    def refine(self, B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0):
         s = Stats()
-        o = _opts(B, max_iter, cand_cap, graph_iters)
+        o = _opts(B, max_iter, cand_cap, graph_iters, flags)
         st = load().gdp_mesh_refine(self._h, C.byref(o), C.byref(s))
         if check and st != OK:
             raise GdpError(st, "gdp_mesh_refine")
@@ -268,10 +273,10 @@ class Batch:
         except Exception:
             pass
 
-    def refine(self, B, max_iter=0, cand_cap=0, graph_iters=0, check=True):
+    def refine(self, B, max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0):
         Bs = np.ascontiguousarray(np.broadcast_to(np.asarray(B, np.float64), (self.n,)))
         s = Stats()
-        o = _opts(float(Bs[0]), max_iter, cand_cap, graph_iters)
+        o = _opts(float(Bs[0]), max_iter, cand_cap, graph_iters, flags)
         st = load().gdp_batch_refine(self._h, _p(Bs), C.byref(o), C.byref(s))
         if check and st != OK:
             raise GdpError(st, "gdp_batch_refine")
