@@ -56,7 +56,9 @@ typedef struct {
     int32_t max_iter;     /* parallel iterations (Algorithm 1 loop), 0 = 100000 */
     int32_t cand_cap;     /* candidates per iteration and mesh; 0 = no cap (Rule 2) */
     int32_t graph_iters;  /* iterations per CUDA-graph replay; 0 = 8, < 0 = no graph */
-    int32_t flags;        /* reserved, 0 */
+    int32_t flags;        /* GDP_REFINE_* bits, 0 = none */
+    int32_t cand_block;   /* threads per block of the per-candidate kernels:
+                             32, 64, 128 or 256; 0 = 64 */
 } gdp_refine_opts;
 
 typedef struct {
@@ -181,6 +183,68 @@ int gdp_batch_export(gdp_batch* b, int32_t mesh, double* xy, int64_t cap_pts, in
                      int64_t cap_tri, int32_t* subseg, int64_t cap_seg, int64_t* n_pts,
                      int64_t* n_tri, int64_t* n_seg);
 void gdp_batch_destroy(gdp_batch* b);
+
+/* ---------------- autotuning (Rule 2) ----------------
+ * Not a step of Algorithm 1: picks the launch parameters of the refinement
+ * for a workload.  For the PSLGs given (layout of gdp_batch_create; a sample
+ * of the workload) it builds their CDT once per trial and refines with every
+ * pair of cand_block in {32, 64, 128, 256} and cand_cap in
+ * {0, 16384, 4096, 1024, 256}, starting from *base (may be NULL), and writes
+ * to *best the options with the most Steiner points per second of refinement
+ * device time.  trials (may be NULL): 4 doubles per trial (cand_block,
+ * cand_cap, refine ms, Steiner points), up to trials_cap trials (20 in all).
+ * B: one bound per mesh (NULL: base->B).  Errors as gdp_batch_create /
+ * gdp_batch_refine. */
+int gdp_autotune(const double* xy, const int64_t* pt_off, const int32_t* seg,
+                 const int64_t* seg_off, int32_t n_meshes, const double* B,
+                 const gdp_refine_opts* base, void* cuda_stream, gdp_refine_opts* best,
+                 double* trials, int32_t trials_cap);
+
+/* ---------------- serving (continuous batching) ----------------
+ * Not in the paper: a request loop around Algorithm 1.  A server keeps one
+ * resident device pool with room for tri_slots triangles, vert_slots vertices,
+ * seg_slots input segments and max_meshes meshes (admission is by this
+ * device memory).  Each gdp_server_step
+ *   1. launches opts->graph_iters (0: 8) refinement iterations (lines 2-9)
+ *      over every resident mesh at once (one CUDA-graph replay);
+ *   2. while they run, builds the initial CDT (line 1) of the oldest waiting
+ *      requests in staging pools on a second stream, as long as a region of
+ *      the resident pool is free for them (first come, first served);
+ *   3. retires the meshes that finished (no candidate in the last iteration,
+ *      nothing deferred), copying each result to host memory and freeing its
+ *      region, and moves the new CDTs into their regions so that they join
+ *      the next replay.
+ * A request's result does not depend on the other requests: it is the same
+ * mesh gdp_mesh_create + gdp_mesh_refine give for it alone.
+ * The stream (may be NULL) is the one the refinement runs on.  opts: B is
+ * unused (each request has its own), cand_cap / cand_block as for refine.
+ * tri_slots < 2^29, vert_slots < 2^30, max_meshes <= 2^20.
+ * Errors: GDP_ERR_INPUT, GDP_ERR_NOMEM (pool allocation), GDP_ERR_CUDA; on
+ * error *out may still be set and must be destroyed. */
+typedef struct gdp_server gdp_server;
+typedef struct {
+    int64_t ticket;        /* from gdp_server_submit */
+    int32_t status;        /* gdp_status of this request */
+    int64_t n_in_pts, n_steiner, n_pts, n_tri, n_subseg;
+    double t_submit_ms;    /* server clock (ms since creation): submitted, */
+    double t_admit_ms;     /* joined the resident pool, */
+    double t_done_ms;      /* copied out */
+} gdp_result_info;
+int gdp_server_create(int64_t tri_slots, int64_t vert_slots, int64_t seg_slots, int32_t max_meshes,
+                      const gdp_refine_opts* opts, void* cuda_stream, gdp_server** out);
+/* Queue a request (host buffers, copied; same layout as gdp_mesh_create) with
+ * bound B.  GDP_ERR_NOMEM when it could never fit the pool. */
+int gdp_server_submit(gdp_server* s, const double* xy, int64_t n_pts, const int32_t* seg,
+                      int64_t n_seg, double B, int64_t* ticket);
+/* One scheduling step (blocking); counts after it (NULL to skip). */
+int gdp_server_step(gdp_server* s, int32_t* n_waiting, int32_t* n_live, int32_t* n_done);
+/* The oldest finished request.  With all buffers NULL: fills *info and keeps
+ * it (sizes for the buffers); with buffers (layout of gdp_mesh_export): copies
+ * it out and removes it.  GDP_ERR_INPUT when none is finished or a buffer is
+ * too small. */
+int gdp_server_result(gdp_server* s, gdp_result_info* info, double* xy, int64_t cap_pts,
+                      int32_t* tri, int64_t cap_tri, int32_t* subseg, int64_t cap_seg);
+void gdp_server_destroy(gdp_server* s);
 
 /* ---------------- scan without device allocation ----------------
  * The paper has no counterpart to this entry point: it exists for callers

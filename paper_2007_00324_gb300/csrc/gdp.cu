@@ -138,11 +138,11 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
   } while (0)
 // per-candidate kernels: small blocks over a wide grid, so that a few
 // thousand latency-bound threads land on every SM instead of a few blocks
-constexpr int BS_CAND = 64;
+// (h).bs_cand threads per block (tunable), 1024 threads per SM in all
 #define LAUNCH_C(h, kern, ...)                                       \
   do {                                                               \
     (h).prof_begin(#kern);                                           \
-    kern<<<(h).Gc, BS_CAND, 0, (h).stream>>>(__VA_ARGS__);           \
+    kern<<<(h).Gc, (h).bs_cand, 0, (h).stream>>>(__VA_ARGS__);       \
     (h).prof_end();                                                  \
   } while (0)
 
@@ -379,6 +379,12 @@ struct PoolHost {
   }
   int refine(const double* B, const gdp_refine_opts* o);
   int launch_iteration(int k);
+  int bs_cand = 64;               // per-candidate kernels: threads per block
+  bool capped = false;            // some mesh has a per-iteration candidate cap
+  void set_cand_block(int b) {
+    bs_cand = (b == 32 || b == 128 || b == 256) ? b : 64;
+    Gc = n_sm * (1024 / bs_cand);
+  }
   // GDP_REFINE_TIME_GROW: an event pair around k_grow<0> per iteration slot of the graph
   bool time_grow = false;
   std::vector<cudaEvent_t> tg;
@@ -394,7 +400,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return GDP_ERR_CUDA; }
   CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   G = 4 * n_sm;
-  Gc = 16 * n_sm;
+  set_cand_block(64);
   prof = std::getenv("GDP_PROFILE") != nullptr;
   CK(cudaMallocHost(&hctrl, sizeof(Ctrl)));
   CK(cudaEventCreate(&ev0));
@@ -440,6 +446,9 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   AL(P.newref, 4 * tb, 0xff);
   AL(P.dirty, tb, 0);
   AL(P.flag, tb, 0);
+  AL(P.cbucket, tb, 0);
+  AL(P.cap_hist, (size_t)nm * CAP_BUCKETS, 0);
+  AL(P.cap_thr, nm, 0);
   AL(P.mi, nm, 0);
   AL(P.seg, sb, 0);
   AL(P.adj_off, ab + 1, 0);
@@ -799,6 +808,10 @@ int PoolHost::build_cdt() {
 // one refinement iteration; k = its position in the graph (event pair)
 int PoolHost::launch_iteration(int k) {
   LAUNCH(*this, k_scan_count, G, P);
+  if (capped) {
+    LAUNCH(*this, k_cap_select, G, P);
+    LAUNCH(*this, k_cap_count, G, P);
+  }
   LAUNCH(*this, k_scan_write, G, P);
   const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k], stream, rec));
@@ -849,6 +862,8 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   CK(cudaEventRecord(ev0, stream));
   int status = GDP_OK;
   time_grow = (d.flags & GDP_REFINE_TIME_GROW) != 0;
+  capped = d.cand_cap > 0;
+  set_cand_block(d.cand_block);
   stats.grow_ms = 0;
   stats.grow_launches = 0;
   if (time_grow) {
@@ -861,7 +876,8 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   }
   if (giters > 0 && !prof) {
     for (;;) {
-      const int st = replay(g_refine, 2 * giters + (time_grow ? 1 : 0), [&] {
+      const int tag = ((giters * 2 + (time_grow ? 1 : 0)) * 2 + (capped ? 1 : 0)) * 512 + bs_cand;
+      const int st = replay(g_refine, tag, [&] {
         for (int k = 0; k < giters; ++k) {
           const int r = launch_iteration(k);
           if (r != GDP_OK) return r;
@@ -1310,3 +1326,6 @@ int gdp_batch_export(gdp_batch* b, int32_t mesh, double* xy, int64_t cap_pts, in
 void gdp_batch_destroy(gdp_batch* b) { delete b; }
 
 }  // extern "C"
+
+#include "gdp_server.cuh"
+#include "gdp_tune.cuh"

@@ -29,6 +29,7 @@ constexpr int LANES_B = 16, CAP_B = CMAX_BIG;    // spill tier B
 constexpr long long BIG_ENTRIES = (long long)LANES_A * (CAP_A + 2) + (long long)LANES_B * (CAP_B + 2);
 constexpr long long BIG_HASH = 2ll * LANES_A * CAP_A + 2ll * LANES_B * CAP_B;
 constexpr int LANE_FREE = 0x7f7f7f7f;            // byte fill 0x7f
+constexpr int CAP_BUCKETS = 1024;   // per-mesh priority histogram (candidate cap)
 constexpr int WALK_MAX = 1 << 16;   // point-location steps
 constexpr int BS = 256;             // threads per block
 constexpr int INFO_DEAD = 8;
@@ -76,6 +77,7 @@ struct Ctrl {
   int32_t n_fl;          // CDT: triangles whose edges the current flip pass checks
   int32_t n_fl_next;     // CDT: triangles pushed for the next flip pass
   int32_t step;          // CDT: split / flip pass number (stamps, flip keys)
+  int32_t scan_hi;       // refinement scans slots [0, scan_hi); 0 = all slots
   unsigned long long tot_cand, tot_ins, iters, n_ins, n_surv;
   // refinement work counters (algorithmic bytes of the cavity kernels)
   unsigned long long n_grown, sum_cav, sum_bnd, sum_walk;
@@ -117,6 +119,11 @@ struct Pool {
   int32_t* c_nbnd;
   int32_t* c_cav;
   int4* c_bnd;
+  // per-mesh candidate cap (Rule 2): priority bucket of each flagged slot,
+  // per-mesh bucket histograms and the lowest bucket taken this iteration
+  uint16_t* cbucket;
+  int32_t* cap_hist;
+  int32_t* cap_thr;
   int32_t* c_big;        // offset of the cavity in the spill tiers, -1 = own slot
   int32_t* big_cav;      // BIG_ENTRIES
   int4* big_bnd;         // BIG_ENTRIES

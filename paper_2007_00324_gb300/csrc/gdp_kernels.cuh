@@ -248,6 +248,30 @@ __device__ int eval_tri(const Pool& P, int t) {
   return 0;
 }
 
+// Priority bucket of a flagged element for the per-mesh cap: [class bit |
+// the top 9 bits (exponent + 1 mantissa bit) of float32 length^2 (subsegment)
+// or |2A| (triangle)], from the float copies -- a scheduling heuristic, so
+// FP32 is enough; it only has to be deterministic.
+__device__ __forceinline__ int cap_bucket(const Pool& P, const int4& T4, int code) {
+  float v;
+  if (code == 4) {
+    const float2 a = P.Vf[T4.x], b = P.Vf[T4.y], c = P.Vf[T4.z];
+    v = fabsf((b.x - a.x) * (c.y - a.y) - (b.y - a.y) * (c.x - a.x));
+  } else {
+    const float2 u = P.Vf[comp(T4, mod3(code))], w = P.Vf[comp(T4, mod3(code + 1))];
+    v = (w.x - u.x) * (w.x - u.x) + (w.y - u.y) * (w.y - u.y);
+  }
+  const uint32_t b = (v >= 0.0f && v < INFINITY) ? (__float_as_uint(v) >> 22) : 0x1ffu;
+  return (code == 4 ? 0 : 512) | (int)min(b, 0x1ffu);
+}
+
+// slots the refinement scan covers (a resident pool scans up to its highest
+// occupied region only)
+__device__ __forceinline__ int scan_slots(const Pool& P) {
+  const int h = P.ctrl->scan_hi;
+  return (h > 0 && h < P.n_slots) ? h : P.n_slots;
+}
+
 // cavity work space of candidate i: its own slot, or its spill arena region
 __device__ __forceinline__ int* cav_of(const Pool& P, int i) {
   const int o = P.c_big[i];
@@ -283,7 +307,7 @@ __global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
     P.mi[m].last_cand = -1;
     P.mi[m].pending = 0;
   }
-  const Chunk ch = chunk_of(P.n_slots);
+  const Chunk ch = chunk_of(scan_slots(P));
   int cnt = 0;
   for (int base = ch.b0; base < ch.b1; base += BS) {
     const int t = base + threadIdx.x;
@@ -292,6 +316,15 @@ __global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
       if (P.dirty[t]) {
         P.dirty[t] = 0;
         code = eval_tri(P, t);
+        if (code) {
+          const int4 T4 = P.T[t];
+          const int m = T4.w >> 4;
+          if (P.mi[m].cand_cap > 0) {
+            const int b = cap_bucket(P, T4, code);
+            P.cbucket[t] = (uint16_t)b;
+            atomicAdd(&P.cap_hist[(size_t)m * CAP_BUCKETS + b], 1);
+          }
+        }
       }
       P.flag[t] = (uint8_t)code;
       cnt += code != 0;
@@ -301,9 +334,54 @@ __global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
   if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
 }
 
+// per mesh with a cap: the lowest bucket such that all flagged elements at or
+// above it fit in the cap (the top non-empty bucket is always taken); the
+// histogram is cleared for the next iteration
+__global__ void __launch_bounds__(BS) k_cap_select(Pool P) {
+  for (int m = blockIdx.x; m < P.n_mesh; m += gridDim.x) {
+    const int K = P.mi[m].cand_cap;
+    if (K <= 0) continue;
+    int* h = P.cap_hist + (size_t)m * CAP_BUCKETS;
+    if (threadIdx.x == 0) {
+      int acc = 0, thr = CAP_BUCKETS;
+      for (int b = CAP_BUCKETS - 1; b >= 0; --b) {
+        if (!h[b]) continue;
+        if (thr < CAP_BUCKETS && acc + h[b] > K) break;
+        acc += h[b];
+        thr = b;
+      }
+      P.cap_thr[m] = thr;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < CAP_BUCKETS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+  }
+}
+
+// capped meshes: flagged elements below the threshold wait for a later
+// iteration (flag cleared, slot dirty again); block counts for k_scan_write
+__global__ void __launch_bounds__(BS) k_cap_count(Pool P) {
+  __shared__ int sm[33];
+  const Chunk ch = chunk_of(scan_slots(P));
+  int cnt = 0;
+  for (int t = ch.b0 + threadIdx.x; t < ch.b1; t += BS) {
+    if (!P.flag[t]) continue;
+    const int m = P.T[t].w >> 4;
+    if (P.mi[m].cand_cap > 0 && P.cbucket[t] < P.cap_thr[m]) {
+      P.flag[t] = 0;
+      P.dirty[t] = 1;
+      P.mi[m].pending = 1;
+      continue;
+    }
+    ++cnt;
+  }
+  cnt = block_sum(cnt, sm);
+  if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
+}
+
 __global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
   __shared__ int sm[33];
-  const Chunk ch = chunk_of(P.n_slots);
+  const Chunk ch = chunk_of(scan_slots(P));
   int off = block_prefix(P.blk, blockIdx.x, sm);
   const int cap = P.cap_cand;
   for (int base = ch.b0; base < ch.b1; base += BS) {

@@ -29,7 +29,8 @@ class GdpError(RuntimeError):
 
 class RefineOpts(C.Structure):
     _fields_ = [("B", C.c_double), ("max_len", C.c_double), ("max_iter", C.c_int32),
-                ("cand_cap", C.c_int32), ("graph_iters", C.c_int32), ("flags", C.c_int32)]
+                ("cand_cap", C.c_int32), ("graph_iters", C.c_int32), ("flags", C.c_int32),
+                ("cand_block", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -49,7 +50,8 @@ SYMBOLS = ["gdp_mesh_create", "gdp_mesh_create_device", "gdp_mesh_refine", "gdp_
            "gdp_mesh_stats", "gdp_mesh_check", "gdp_mesh_profile", "gdp_mesh_kernel_time", "gdp_mesh_destroy",
            "gdp_batch_create", "gdp_batch_refine",
            "gdp_batch_info", "gdp_batch_export", "gdp_batch_destroy", "gdp_scan_noalloc",
-           "gdp_status_str"]
+           "gdp_autotune", "gdp_server_create", "gdp_server_submit", "gdp_server_step", "gdp_server_result",
+           "gdp_server_destroy", "gdp_status_str"]
 
 
 def load(build_if_missing: bool = True):
@@ -87,10 +89,18 @@ def load(build_if_missing: bool = True):
             L.gdp_batch_destroy.restype = None
             L.gdp_scan_noalloc.argtypes = [vp, i64, vp, i64, d, vp, vp, vp, vp, i64,
                                            C.POINTER(i64), vp]
+            L.gdp_autotune.argtypes = [vp, vp, vp, vp, i32, vp, C.POINTER(RefineOpts), vp,
+                                       C.POINTER(RefineOpts), vp, i32]
+            L.gdp_server_create.argtypes = [i64, i64, i64, i32, C.POINTER(RefineOpts), vp, C.POINTER(vp)]
+            L.gdp_server_submit.argtypes = [vp, vp, i64, vp, i64, d, C.POINTER(i64)]
+            L.gdp_server_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+            L.gdp_server_result.argtypes = [vp, C.POINTER(ResultInfo), vp, i64, vp, i64, vp, i64]
+            L.gdp_server_destroy.argtypes = [vp]
+            L.gdp_server_destroy.restype = None
             L.gdp_status_str.argtypes = [C.c_int]
             L.gdp_status_str.restype = C.c_char_p
             for n in SYMBOLS:
-                if n not in ("gdp_mesh_destroy", "gdp_batch_destroy", "gdp_status_str"):
+                if n not in ("gdp_mesh_destroy", "gdp_batch_destroy", "gdp_server_destroy", "gdp_status_str"):
                     getattr(L, n).restype = C.c_int
             _lib = L
     return _lib
@@ -110,9 +120,9 @@ def _p(a):
 REFINE_TIME_GROW = 1   # gdp_refine_opts.flags: time every k_grow launch with CUDA events
 
 
-def _opts(B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, flags=0):
+def _opts(B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, flags=0, cand_block=0):
     return RefineOpts(B=B, max_len=0.0, max_iter=max_iter, cand_cap=cand_cap,
-                      graph_iters=graph_iters, flags=flags)
+                      graph_iters=graph_iters, flags=flags, cand_block=cand_block)
 
 
 def _stream_handle(stream):
@@ -155,9 +165,10 @@ class Mesh:
         except Exception:
             pass
 
-    def refine(self, B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0):
+    def refine(self, B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0,
+               cand_block=0):
         s = Stats()
-        o = _opts(B, max_iter, cand_cap, graph_iters, flags)
+        o = _opts(B, max_iter, cand_cap, graph_iters, flags, cand_block)
         st = load().gdp_mesh_refine(self._h, C.byref(o), C.byref(s))
         if check and st != OK:
             raise GdpError(st, "gdp_mesh_refine")
@@ -273,10 +284,10 @@ class Batch:
         except Exception:
             pass
 
-    def refine(self, B, max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0):
+    def refine(self, B, max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0, cand_block=0):
         Bs = np.ascontiguousarray(np.broadcast_to(np.asarray(B, np.float64), (self.n,)))
         s = Stats()
-        o = _opts(float(Bs[0]), max_iter, cand_cap, graph_iters, flags)
+        o = _opts(float(Bs[0]), max_iter, cand_cap, graph_iters, flags, cand_block)
         st = load().gdp_batch_refine(self._h, _p(Bs), C.byref(o), C.byref(s))
         if check and st != OK:
             raise GdpError(st, "gdp_batch_refine")
@@ -307,6 +318,105 @@ class Batch:
         if st != OK:
             raise GdpError(st, "gdp_batch_export")
         return xy, tri, sub
+
+
+def _concat(pslgs):
+    xys = [np.ascontiguousarray(p[0], np.float64).reshape(-1, 2) for p in pslgs]
+    segs = [np.ascontiguousarray(p[1], np.int32).reshape(-1, 2) for p in pslgs]
+    pt_off = np.zeros(len(pslgs) + 1, np.int64)
+    seg_off = np.zeros(len(pslgs) + 1, np.int64)
+    pt_off[1:] = np.cumsum([len(x) for x in xys])
+    seg_off[1:] = np.cumsum([len(s) for s in segs])
+    xy = np.ascontiguousarray(np.concatenate(xys))
+    seg = np.ascontiguousarray(np.concatenate(segs)) if seg_off[-1] else np.zeros((1, 2), np.int32)
+    return xy, pt_off, seg, seg_off
+
+
+def autotune(pslgs, B, stream=None):
+    """gdp_autotune on a sample [(xy, seg)]: returns ({"cand_block", "cand_cap"},
+    [(cand_block, cand_cap, refine_ms, steiner) per trial])"""
+    xy, pt_off, seg, seg_off = _concat(pslgs)
+    Bs = np.ascontiguousarray(np.broadcast_to(np.asarray(B, np.float64), (len(pslgs),)))
+    best = RefineOpts()
+    trials = np.zeros((32, 4), np.float64)
+    st = load().gdp_autotune(_p(xy), _p(pt_off), _p(seg), _p(seg_off), len(pslgs), _p(Bs),
+                             C.byref(_opts(float(Bs[0]))), _stream_handle(stream), C.byref(best),
+                             _p(trials), 32)
+    if st != OK:
+        raise GdpError(st, "gdp_autotune")
+    n = 20
+    return ({"cand_block": best.cand_block, "cand_cap": best.cand_cap},
+            [tuple(trials[k]) for k in range(n)])
+
+
+class ResultInfo(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("status", C.c_int32), ("n_in_pts", C.c_int64),
+                ("n_steiner", C.c_int64), ("n_pts", C.c_int64), ("n_tri", C.c_int64),
+                ("n_subseg", C.c_int64), ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double),
+                ("t_done_ms", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Server:
+    """gdp_server: continuous batching of refinement requests in one resident
+    pool (capacities in triangle slots, vertices, segments and meshes)."""
+
+    def __init__(self, tri_slots, vert_slots, seg_slots, max_meshes, cand_cap=0, cand_block=0,
+                 graph_iters=0, stream=None):
+        o = _opts(math.sqrt(2.0), 0, cand_cap, graph_iters, 0, cand_block)
+        self._h = C.c_void_p()
+        st = load().gdp_server_create(int(tri_slots), int(vert_slots), int(seg_slots), int(max_meshes),
+                                      C.byref(o), _stream_handle(stream), C.byref(self._h))
+        if st != OK:
+            self.close()
+            raise GdpError(st, "gdp_server_create")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().gdp_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, xy, seg, B):
+        xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+        seg = np.ascontiguousarray(seg, np.int32).reshape(-1, 2)
+        t = C.c_int64()
+        st = load().gdp_server_submit(self._h, _p(xy), len(xy), _p(seg) if len(seg) else None, len(seg),
+                                      float(B), C.byref(t))
+        if st != OK:
+            raise GdpError(st, "gdp_server_submit")
+        return t.value
+
+    def step(self):
+        w, l, d = C.c_int32(), C.c_int32(), C.c_int32()
+        st = load().gdp_server_step(self._h, C.byref(w), C.byref(l), C.byref(d))
+        if st != OK:
+            raise GdpError(st, "gdp_server_step")
+        return w.value, l.value, d.value
+
+    def results(self):
+        """every finished request: [(info dict, xy, tri, subseg)], oldest first"""
+        L = load()
+        out = []
+        while True:
+            info = ResultInfo()
+            if L.gdp_server_result(self._h, C.byref(info), None, 0, None, 0, None, 0) != OK:
+                return out
+            xy = np.zeros((info.n_pts, 2), np.float64)
+            tri = np.zeros((info.n_tri, 3), np.int32)
+            sub = np.zeros((info.n_subseg, 3), np.int32)
+            st = L.gdp_server_result(self._h, C.byref(info), _p(xy), len(xy), _p(tri), len(tri),
+                                     _p(sub), len(sub))
+            if st != OK:
+                raise GdpError(st, "gdp_server_result")
+            out.append((info.as_dict(), xy, tri, sub))
 
 
 def scan_noalloc(xy, tri4, B, kind, verts, pt, meas, stream=None):

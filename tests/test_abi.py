@@ -50,3 +50,16 @@ def test_no_device_means_an_error_not_a_fallback():
         assert e.status == gdp.ERR_CUDA
     else:
         raise AssertionError("mesh creation succeeded without a GPU")
+
+
+def test_server_without_device_is_an_error():
+    import torch
+    if torch.cuda.is_available():
+        return
+    from paper_2007_00324_gb300 import gdp
+    try:
+        gdp.Server(1 << 16, 1 << 16, 1024, 8)
+    except gdp.GdpError as e:
+        assert e.status == gdp.ERR_CUDA
+    else:
+        raise AssertionError("server created without a device")
