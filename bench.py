@@ -84,7 +84,254 @@ def parse():
     ap.add_argument("--impl", default="gdp", choices=["gdp", "reference"])
     ap.add_argument("--B", type=float, default=SQ2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served"],
+                    help="mid: the headline line; batched / served: the batching and "
+                         "serving configurations (one JSON line each)")
+    ap.add_argument("--count", type=int, default=4096, help="batched: number of PSLGs")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
+    ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
     return ap.parse_args()
+
+
+# ---------------------------------------------------------------- batched / served
+def _gen_square(job):
+    from paper_2007_00324_gb300 import workloads
+    n, m, seed = job
+    p = workloads.square_pslg(n, m, seed)
+    return p.xy, p.seg
+
+
+def _generate(jobs, workers=None):
+    """square PSLGs in a spawn process pool (before any GPU call)"""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = workers or max(1, min(len(jobs), os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_square, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
+
+
+def _oracle_run(job):
+    from oracle import oracle
+    xy, seg, B = job
+    t0 = time.perf_counter()
+    m = oracle.Mesh(xy, seg)
+    st = m.refine(B)
+    return st, m.n_steiner, time.perf_counter() - t0
+
+
+def _oracle_pool(jobs):
+    """the oracle as independent processes over all host cores"""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from oracle import oracle
+    oracle.build()
+    workers = max(1, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        out = list(ex.map(_oracle_run, jobs))
+    return out, time.perf_counter() - t0, workers
+
+
+def _pct(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))
+    return v[k]
+
+
+def run_batched(args):
+    """4,096 PSLGs (log-uniform 200-50,000 uniform points, 2% segments,
+    B = sqrt 2): the plain per-mesh loop against one batch (default launch
+    parameters and autotuned ones) on the same GPU."""
+    from paper_2007_00324_gb300 import workloads
+    sizes = workloads.batched_sizes(args.count)
+    seed = workloads.SEED_BASE + 3
+    jobs = [(int(n), int(round(0.02 * n)), seed * 7919 + i) for i, n in enumerate(sizes)]
+    t_gen = time.perf_counter()
+    pslgs = _generate(jobs)
+    t_gen = time.perf_counter() - t_gen
+    cpu = None
+    if not args.no_cpu_baseline:
+        sample = pslgs[::max(1, len(pslgs) // 64)][:64]
+        out, dt, workers = _oracle_pool([(xy, seg, args.B) for xy, seg in sample])
+        cpu = {"value": len(sample) / dt, "unit": "meshes/s", "cores": workers, "kind": "oracle",
+               "sample": f"{len(sample)} PSLGs of the batch (every {max(1, len(pslgs) // 64)}th), "
+                         f"one process per core, {dt:.1f} s",
+               "steiner_per_s": sum(o[1] for o in out) / dt}
+    import torch
+    from paper_2007_00324_gb300 import gdp
+    gdp.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    tot_pts = int(sum(len(xy) for xy, _ in pslgs))
+    # autotune on a sample (every 32nd PSLG)
+    sample = pslgs[::32]
+    t_tune = time.perf_counter()
+    best, trials = gdp.autotune(sample, args.B, stream=stream)
+    t_tune = time.perf_counter() - t_tune
+
+    def batch_run(opts):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b = gdp.Batch(pslgs, stream=stream)
+        s = b.refine(args.B, **opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        info = b.info()
+        ok = int((info["status"] == 0).sum())
+        b.close()
+        return {"ms": 1000 * dt, "meshes_per_s": len(pslgs) / dt, "steiner": int(s["n_steiner"]),
+                "steiner_per_s": s["n_steiner"] / dt, "cdt_ms": s["cdt_ms"], "refine_ms": s["refine_ms"],
+                "iterations": s["iterations"], "ok": ok}
+
+    batch_run({})   # warm-up (allocator, graph paths)
+    default = batch_run({})
+    tuned = batch_run(best)
+    # the plain per-mesh loop: one gdp_mesh per PSLG, one after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st_plain = 0
+    for xy, seg in pslgs:
+        m = gdp.Mesh(xy, seg, stream=stream)
+        st_plain += m.refine(args.B)["n_steiner"]
+        m.close()
+    torch.cuda.synchronize()
+    dt_plain = time.perf_counter() - t0
+    plain = {"ms": 1000 * dt_plain, "meshes_per_s": len(pslgs) / dt_plain, "steiner": st_plain,
+             "steiner_per_s": st_plain / dt_plain}
+    line = {"metric": "batched meshes/s (CDT + refine, host inputs, wall clock)",
+            "value": tuned["meshes_per_s"], "unit": "meshes/s", "n_gpus": 1, "steps": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batched: {len(pslgs)} PSLGs, uniform points log-uniform in "
+                                   f"[200, 50000] ({tot_pts} points), 2% segments, B=sqrt(2)"},
+            "batched_tuned": tuned, "batched_default": default, "plain_loop": plain,
+            "speedup_vs_plain_loop": tuned["meshes_per_s"] / plain["meshes_per_s"],
+            "autotune": {"best": best, "seconds": t_tune, "sample_meshes": len(sample),
+                         "trials": [{"cand_block": int(t[0]), "cand_cap": int(t[1]),
+                                     "refine_ms": round(t[2], 3), "steiner": int(t[3])} for t in trials]},
+            "generate_s": t_gen}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    """Poisson arrivals (seeded, --rate per second for --duration s) of PSLGs
+    with log-uniform 1,000-500,000 points, 1-5% segments, B in {1.5, sqrt 2}:
+    the continuous-batching server against the plain loop (one request at a
+    time, in arrival order) on the same trace and GPU."""
+    from paper_2007_00324_gb300 import workloads
+    trace = workloads.served_trace(rate=args.rate, duration=args.duration, build=False)
+    # the same per-request draws as served_trace(build=True), generated in parallel
+    rng_jobs = []
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(workloads.SEED_BASE + 4))
+    t = 0.0
+    i = 0
+    meta = []
+    while True:
+        t += float(rng.exponential(1.0 / args.rate))
+        if t > args.duration:
+            break
+        n = int(math.exp(rng.uniform(math.log(1000), math.log(500_000))))
+        frac = int(rng.integers(1, 6)) / 100.0
+        B = 1.5 if rng.random() < 0.5 else SQ2
+        rng_jobs.append((n, int(round(frac * n)), (workloads.SEED_BASE + 4) * 104729 + i))
+        meta.append((t, B))
+        i += 1
+    assert len(meta) == len(trace) and all(abs(a[0] - r.t_arrival) < 1e-12 for a, r in zip(meta, trace))
+    t_gen = time.perf_counter()
+    pslgs = _generate(rng_jobs)
+    t_gen = time.perf_counter() - t_gen
+    tot_pts = int(sum(len(xy) for xy, _ in pslgs))
+    cpu = None
+    if not args.no_cpu_baseline:
+        k = min(len(pslgs), 32)
+        out, dt, workers = _oracle_pool([(pslgs[j][0], pslgs[j][1], meta[j][1]) for j in range(k)])
+        cpu = {"value": k / dt, "unit": "meshes/s", "cores": workers, "kind": "oracle",
+               "sample": f"the first {k} requests of the trace, one process per core, all at once, "
+                         f"{dt:.1f} s", "steiner_per_s": sum(o[1] for o in out) / dt}
+    import torch
+    from paper_2007_00324_gb300 import gdp
+    gdp.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    # warm-up of both paths on a small request
+    w = workloads.square_pslg(2000, 40, 1)
+    gdp.Mesh(w.xy, w.seg, stream=stream).refine(SQ2)
+    free, _ = torch.cuda.mem_get_info()
+    tri_slots = int(min((1 << 29) - 1, 0.35 * free / 64))
+
+    def serve():
+        srv = gdp.Server(tri_slots, tri_slots // 2, 1 << 23, 2048, stream=stream)
+        srv.submit(w.xy, w.seg, SQ2)
+        while True:
+            nw, nl, _ = srv.step()
+            if nw == 0 and nl == 0:
+                break
+        srv.results()
+        lat, steiner, done_at = {}, 0, {}
+        nxt = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = {}
+        while len(done_at) < len(pslgs):
+            now = time.perf_counter() - t0
+            while nxt < len(pslgs) and meta[nxt][0] <= now:
+                tickets[srv.submit(pslgs[nxt][0], pslgs[nxt][1], meta[nxt][1])] = nxt
+                nxt += 1
+            if nxt < len(pslgs) and not tickets.keys() - done_at.keys():
+                time.sleep(max(0.0, min(0.002, meta[nxt][0] - now)))
+            srv.step()
+            for info, xy, tri, sub in srv.results():
+                j = tickets[info["ticket"]]
+                done_at[info["ticket"]] = time.perf_counter() - t0
+                lat[j] = 1000 * (done_at[info["ticket"]] - meta[j][0])
+                steiner += info["n_steiner"]
+                assert info["status"] == 0, info
+        span = max(done_at.values())
+        srv.close()
+        return lat, steiner, span
+
+    def plain():
+        lat, steiner = {}, 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j, (xy, seg) in enumerate(pslgs):
+            now = time.perf_counter() - t0
+            if meta[j][0] > now:
+                time.sleep(meta[j][0] - now)
+            m = gdp.Mesh(xy, seg, stream=stream)
+            steiner += m.refine(meta[j][1])["n_steiner"]
+            m.export()
+            m.close()
+            lat[j] = 1000 * (time.perf_counter() - t0 - meta[j][0])
+        return lat, steiner, time.perf_counter() - t0
+
+    lat_s, st_s, span_s = serve()
+    lat_p, st_p, span_p = plain()
+
+    def summary(lat, steiner, span):
+        v = list(lat.values())
+        return {"p50_ms": _pct(v, 50), "p99_ms": _pct(v, 99), "mean_ms": sum(v) / len(v),
+                "meshes_per_s": len(v) / span, "steiner_per_s": steiner / span, "makespan_s": span}
+
+    served, pl = summary(lat_s, st_s, span_s), summary(lat_p, st_p, span_p)
+    line = {"metric": "served meshes/s and p50/p99 latency (Poisson arrivals, wall clock)",
+            "value": served["meshes_per_s"], "unit": "meshes/s", "n_gpus": 1, "steps": 1,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"served: {len(pslgs)} requests, Poisson {args.rate:g}/s for "
+                                   f"{args.duration:g} s, 1,000-500,000 points ({tot_pts} in all), "
+                                   f"1-5% segments, B in {{1.5, sqrt 2}}",
+                       "pool_tri_slots": tri_slots},
+            "served": served, "plain_loop": pl,
+            "p99_speedup_vs_plain": pl["p99_ms"] / served["p99_ms"],
+            "throughput_speedup_vs_plain": served["meshes_per_s"] / pl["meshes_per_s"],
+            "generate_s": t_gen}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
 
 
 def peaks():
@@ -198,6 +445,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     import numpy as np
     import torch
     import torch.distributed as dist

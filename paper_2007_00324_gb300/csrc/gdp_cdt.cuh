@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(BS) k_split(Pool P) {
     if (!P.c_final[i] || !ok) continue;
     const int t = P.c_loc[i], v = P.c_vid[i];
     const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
+    P.c_base[i] = base;   // k_split_link must not recompute it: tri_count moves there
     const int4 T4 = P.T[t];
     const int4 N4 = P.N[t];
     const int s[3] = {t, base, base + 1};
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(BS) k_split_link(Pool P) {
     if (P.c_final[i] && ok) {
       ++ins;
       const int t = P.c_loc[i];
-      const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[M.first_cand]);
+      const int base = P.c_base[i];
       for (int e = 0; e < 3; ++e) {
         const int s = e == 0 ? t : base + e - 1;
         const int r = P.N[s].x;
