@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -208,6 +209,62 @@ static void trace_check(const Pool& P, cudaStream_t st, int G, const char* where
   }
 }
 
+// ---------------------------------------------------------------- memory
+// Device buffers come from one stream-ordered memory pool per device that the
+// library owns and never trims: a mesh's buffers are allocated and freed in
+// stream order (no device-wide synchronisation on free), and later meshes
+// reuse the same memory instead of going back to the driver.  The control
+// blocks read by the host every round are pinned and recycled the same way.
+namespace {
+std::mutex g_mem_lock;
+cudaMemPool_t g_pools[64] = {};
+std::vector<Ctrl*> g_ctrl_free;
+
+cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(g_mem_lock);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    unsigned long long keep = ~0ull;   // keep freed memory for reuse
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = p;
+  }
+  return g_pools[dev];
+}
+
+Ctrl* ctrl_get() {
+  {
+    std::lock_guard<std::mutex> g(g_mem_lock);
+    if (!g_ctrl_free.empty()) {
+      Ctrl* c = g_ctrl_free.back();
+      g_ctrl_free.pop_back();
+      return c;
+    }
+  }
+  Ctrl* c = nullptr;
+  if (cudaMallocHost(&c, sizeof(Ctrl)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return c;
+}
+
+void ctrl_put(Ctrl* c) {
+  if (!c) return;
+  std::lock_guard<std::mutex> g(g_mem_lock);
+  g_ctrl_free.push_back(c);
+}
+}  // namespace
+
 // ---------------------------------------------------------------- the pool
 struct PoolHost {
   cudaStream_t stream = nullptr;
@@ -278,8 +335,9 @@ struct PoolHost {
     for (cudaEvent_t e : tg) cudaEventDestroy(e);
     for (Cached* c : {&g_bw, &g_split[0], &g_split[1], &g_flip, &g_refine})
       if (c->g) cudaGraphExecDestroy(c->g);
-    for (void* p : allocs) cudaFree(p);
-    if (hctrl) cudaFreeHost(hctrl);
+    for (void* p : allocs) cudaFreeAsync(p, stream);
+    if (!allocs.empty()) cudaStreamSynchronize(stream);   // hctrl may still be written
+    ctrl_put(hctrl);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
   }
@@ -287,7 +345,8 @@ struct PoolHost {
   template <class X>
   int alloc(X** p, size_t n, int fill = 0) {
     void* q = nullptr;
-    if (cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(X)) != cudaSuccess) {
+    cudaMemPool_t mp = device_pool();
+    if (!mp || cudaMallocFromPoolAsync(&q, std::max<size_t>(n, 1) * sizeof(X), mp, stream) != cudaSuccess) {
       cudaGetLastError();
       return GDP_ERR_NOMEM;
     }
@@ -300,7 +359,7 @@ struct PoolHost {
   void release(void* p) {
     auto it = std::find(allocs.begin(), allocs.end(), p);
     if (it != allocs.end()) {
-      cudaFree(p);
+      cudaFreeAsync(p, stream);
       allocs.erase(it);
     }
   }
@@ -402,7 +461,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   G = 4 * n_sm;
   set_cand_block(64);
   prof = std::getenv("GDP_PROFILE") != nullptr;
-  CK(cudaMallocHost(&hctrl, sizeof(Ctrl)));
+  if (!(hctrl = ctrl_get())) return GDP_ERR_NOMEM;
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   n_mesh = nm;

@@ -196,7 +196,7 @@ static int server_setup(gdp_server* s, long long tb, long long vb, long long sb,
   h.G = 4 * h.n_sm;
   h.set_cand_block(s->opts.cand_block);
   h.prof = false;
-  CK(cudaMallocHost(&h.hctrl, sizeof(Ctrl)));
+  if (!(h.hctrl = ctrl_get())) return GDP_ERR_NOMEM;
   CK(cudaEventCreate(&h.ev0));
   CK(cudaEventCreate(&h.ev1));
   CK(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
