@@ -22,10 +22,13 @@ using namespace gdp;
 namespace {
 
 // ---------------------------------------------------------------- setup kernels
+// per-mesh kernels over a 2D grid (x: blocks of one mesh, y: meshes)
 __global__ void k_scatter_points(Pool P, const double2* src, const long long* pt_off) {
-  const int m = blockIdx.x;
-  const MeshInfo& M = P.mi[m];
-  for (int k = threadIdx.x; k < M.n_in; k += blockDim.x) P.V[M.vert_base + k] = src[pt_off[m] + k];
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    const MeshInfo& M = P.mi[m];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M.n_in; k += gridDim.x * blockDim.x)
+      P.V[M.vert_base + k] = src[pt_off[m] + k];
+  }
 }
 
 __global__ void k_scatter_segs(Pool P, const int2* src, const long long* seg_off, int* seg_mesh) {
@@ -90,18 +93,17 @@ __global__ void __launch_bounds__(BS) k_iscan_write(int* a, int n, const int* bl
 
 // input vertices where two segments meet at less than 60 degrees
 __global__ void k_apex(Pool P) {
-  const int m = blockIdx.x;
-  MeshInfo& M = P.mi[m];
-  int any = 0;
-  for (int l = threadIdx.x; l < M.n_in; l += blockDim.x) {
-    const int v = M.vert_base + l;
-    P.apex[v] = 0;
-    const int a0 = P.adj_off[M.adj_base + l], a1 = P.adj_off[M.adj_base + l + 1];
-    for (int i = a0; i < a1 && !P.apex[v]; ++i)
-      for (int j = i + 1; j < a1; ++j)
-        if (small_pair(P, P.adj[i], P.adj[j])) { P.apex[v] = 1; any = 1; break; }
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    MeshInfo& M = P.mi[m];
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M.n_in; l += gridDim.x * blockDim.x) {
+      const int v = M.vert_base + l;
+      P.apex[v] = 0;
+      const int a0 = P.adj_off[M.adj_base + l], a1 = P.adj_off[M.adj_base + l + 1];
+      for (int i = a0; i < a1 && !P.apex[v]; ++i)
+        for (int j = i + 1; j < a1; ++j)
+          if (small_pair(P, P.adj[i], P.adj[j])) { P.apex[v] = 1; M.has_apex = 1; break; }
+    }
   }
-  if (any) M.has_apex = 1;
 }
 
 __global__ void k_iota(int* a, int n) {
@@ -333,6 +335,7 @@ struct PoolHost {
   ~PoolHost() {
     prof_flush();
     for (cudaEvent_t e : tg) cudaEventDestroy(e);
+    if (split_graph) cudaGraphExecDestroy(split_graph);
     for (Cached* c : {&g_bw, &g_split[0], &g_split[1], &g_flip, &g_refine})
       if (c->g) cudaGraphExecDestroy(c->g);
     for (void* p : allocs) cudaFreeAsync(p, stream);
@@ -391,6 +394,10 @@ struct PoolHost {
   int insert_rounds(int stop_cons, int* rounds_out, bool split);
   int launch_cdt_round(const Pool& Q, int stop_cons);
   int launch_split_round(const Pool& Q);
+  int launch_split_kernels(const Pool& Q);
+  int build_split_graph(cudaGraphExec_t* out);
+  cudaGraphExec_t split_graph = nullptr;   // captured for split_key
+  Pool split_key{};
   int launch_flip_passes();
   Pool flip_pool(bool a_to_b) const {
     Pool Q = P;
@@ -438,6 +445,7 @@ struct PoolHost {
   }
   int refine(const double* B, const gdp_refine_opts* o);
   int launch_iteration(int k);
+  dim3 mesh_grid = dim3(1, 1);    // per-mesh kernels: (blocks per mesh, meshes)
   int bs_cand = 64;               // per-candidate kernels: threads per block
   bool capped = false;            // some mesh has a per-iteration candidate cap
   void set_cand_block(int b) {
@@ -543,7 +551,13 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   if (tot_seg) CK(cudaMemcpyAsync(sseg, seg, sizeof(int2) * tot_seg, kind, stream));
   CK(cudaMemcpyAsync(dpo, pt_off, sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice, stream));
   CK(cudaMemcpyAsync(dso, seg_off, sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice, stream));
-  LAUNCH(*this, k_scatter_points, nm, P, sxy, dpo);
+  {
+    long long mx = 3;
+    for (int m = 0; m < nm; ++m) mx = std::max<long long>(mx, hmi[m].n_in);
+    const int bx = (int)std::min<long long>(64, std::max<long long>(1, (mx + 4095) / 4096));
+    mesh_grid = dim3(bx, std::min(nm, 65535));
+  }
+  LAUNCH(*this, k_scatter_points, mesh_grid, P, sxy, dpo);
   LAUNCH(*this, k_scatter_segs, nm, P, sseg, dso, seg_mesh);
   if (tot_seg) {
     LAUNCH(*this, k_adj_count, G, P, seg_mesh, (int)tot_seg, P.adj_off);
@@ -553,7 +567,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
     AL(cursor, ab + 1, 0);
     CK(cudaMemcpyAsync(cursor, P.adj_off, sizeof(int) * (ab + 1), cudaMemcpyDeviceToDevice, stream));
     LAUNCH(*this, k_adj_fill, G, P, seg_mesh, (int)tot_seg, cursor);
-    LAUNCH(*this, k_apex, nm, P);
+    LAUNCH(*this, k_apex, mesh_grid, P);
     CK(cudaStreamSynchronize(stream));
     release(cursor);
   }
@@ -600,9 +614,9 @@ constexpr int CDT_FLIP_PASSES = 6;    // even: the flip list is back in flA afte
 int PoolHost::launch_flip_passes() {
   for (int k = 0; k < CDT_FLIP_PASSES; ++k) {
     const Pool Q = flip_pool((k & 1) == 0);
-    LAUNCH_C(*this, k_flip_propose, Q);
-    LAUNCH_C(*this, k_flip_do, Q);
-    LAUNCH_C(*this, k_flip_link, Q);
+    LAUNCH(*this, k_flip_propose, G, Q);
+    LAUNCH(*this, k_flip_do, G, Q);
+    LAUNCH(*this, k_flip_link, G, Q);
     LAUNCH_B(*this, k_fl_next, 1, 1, Q);
   }
   CK(cudaGetLastError());
@@ -611,10 +625,10 @@ int PoolHost::launch_flip_passes() {
 
 // one split round on the pending points in Q.pts (the points left go to
 // Q.pts2), then flip passes; the split triangles are listed in flA
-int PoolHost::launch_split_round(const Pool& Q) {
+int PoolHost::launch_split_kernels(const Pool& Q) {
   Pool S = Q;
   S.fl_nxt = flA;
-  CK(cudaMemsetAsync(&S.ctrl->n_ins, 0, 2 * sizeof(unsigned long long), stream));
+  LAUNCH_B(*this, k_round_begin, 1, 1, S);
   LAUNCH(*this, k_cdt_locate, G, S, 0, 1);
   LAUNCH(*this, k_cdt_pick_count, G, S);
   LAUNCH(*this, k_cdt_pick_write, G, S);
@@ -627,7 +641,122 @@ int PoolHost::launch_split_round(const Pool& Q) {
   LAUNCH_B(*this, k_cdt_next, 1, 1, S);
   LAUNCH_B(*this, k_fl_next, 1, 1, S);
   CK(cudaGetLastError());
-  return launch_flip_passes();
+  return GDP_OK;
+}
+
+int PoolHost::launch_split_round(const Pool& Q) {
+  const int st = launch_split_kernels(Q);
+  return st != GDP_OK ? st : launch_flip_passes();
+}
+
+// The split rounds as one CUDA graph with device-side loops (conditional
+// WHILE nodes), so that the host waits once for the whole phase:
+//   while (points pending and some triangle took one) {
+//     split round (pts -> pts2); while (flip list) { two flip passes }
+//     split round (pts2 -> pts); while (flip list) { two flip passes }
+//   }
+// The pending list is back in P.pts after every iteration.
+int PoolHost::build_split_graph(cudaGraphExec_t* out) {
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  cudaStream_t saved = stream;
+  const long long saved_launches = launches;
+  int st = GDP_OK;
+  auto fail = [&](int code) {
+    if (st == GDP_OK) st = code;
+  };
+  auto add_while = [&](cudaGraph_t parent, cudaGraphConditionalHandle h, const cudaGraphNode_t* deps,
+                       const cudaGraphEdgeData* ed, size_t nd, cudaGraphNode_t* node) -> cudaGraph_t {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(node, parent, deps, ed, nd, &cp) != cudaSuccess) {
+      fail(GDP_ERR_CUDA);
+      return nullptr;
+    }
+    return cp.conditional.phGraph_out[0];
+  };
+  cudaGraphConditionalHandle hr;
+  cudaGraphNode_t wr;
+  cudaGraph_t body = nullptr;
+  if (cudaGraphConditionalHandleCreate(&hr, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) fail(GDP_ERR_CUDA);
+  if (st == GDP_OK) body = add_while(g, hr, nullptr, nullptr, 0, &wr);
+  if (st == GDP_OK && (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess))
+    fail(GDP_ERR_CUDA);
+  if (st == GDP_OK &&
+      cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    fail(GDP_ERR_CUDA);
+  if (st == GDP_OK) {
+    capturing = true;
+    stream = cs;
+    Pool Q = P;
+    std::swap(Q.pts, Q.pts2);
+    for (int half = 0; half < 2 && st == GDP_OK; ++half) {
+      st = launch_split_kernels(half ? Q : P);
+      if (st != GDP_OK) break;
+      cudaStreamCaptureStatus cst;
+      cudaGraph_t cg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* ed = nullptr;
+      size_t nd = 0;
+      cudaGraphConditionalHandle hf;
+      if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &ed, &nd) != cudaSuccess ||
+          cudaGraphConditionalHandleCreate(&hf, cg, 0, 0) != cudaSuccess) {
+        fail(GDP_ERR_CUDA);
+        break;
+      }
+      LAUNCH_B(*this, k_flip_cond, 1, 1, P, hf);
+      if (cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, &ed, &nd) != cudaSuccess) {
+        fail(GDP_ERR_CUDA);
+        break;
+      }
+      cudaGraphNode_t wf;
+      cudaGraph_t fbody = add_while(cg, hf, deps, ed, nd, &wf);
+      if (st != GDP_OK ||
+          cudaStreamUpdateCaptureDependencies(cs, &wf, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess) {
+        fail(GDP_ERR_CUDA);
+        break;
+      }
+      // the flip loop's body: two passes (the list ends in flA again) and the condition
+      stream = cs2;
+      if (cudaStreamBeginCaptureToGraph(cs2, fbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+          cudaSuccess) {
+        stream = cs;
+        fail(GDP_ERR_CUDA);
+        break;
+      }
+      for (int k = 0; k < 2; ++k) {
+        const Pool F = flip_pool(k == 0);
+        LAUNCH(*this, k_flip_propose, G, F);
+        LAUNCH(*this, k_flip_do, G, F);
+        LAUNCH(*this, k_flip_link, G, F);
+        LAUNCH_B(*this, k_fl_next, 1, 1, F);
+      }
+      LAUNCH_B(*this, k_flip_cond, 1, 1, P, hf);
+      if (cudaStreamEndCapture(cs2, &fbody) != cudaSuccess) fail(GDP_ERR_CUDA);
+      stream = cs;
+    }
+    LAUNCH_B(*this, k_round_cond, 1, 1, P, hr);
+    if (cudaGetLastError() != cudaSuccess) fail(GDP_ERR_CUDA);
+    if (cudaStreamEndCapture(cs, &body) != cudaSuccess) fail(GDP_ERR_CUDA);
+    capturing = false;
+  }
+  stream = saved;
+  launches = saved_launches;
+  if (st == GDP_OK && cudaGraphInstantiate(out, g, 0) != cudaSuccess) {
+    *out = nullptr;
+    fail(GDP_ERR_CUDA);
+  }
+  cudaGetLastError();
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  if (cs2) cudaStreamDestroy(cs2);
+  return st;
 }
 
 // Rounds until every pending point is in.  With split, the rounds first
@@ -654,7 +783,25 @@ int PoolHost::insert_rounds(int stop_cons, int* rounds_out, bool split) {
         set_ctrl_field(offsetof(Ctrl, step), 1) != GDP_OK)
       return GDP_ERR_CUDA;
     int parity = 0;
-    while (hctrl->n_pts > 0) {
+    if (use_graph) {
+      if (!split_graph || std::memcmp(&split_key, &P, sizeof(Pool)) != 0) {
+        if (split_graph) cudaGraphExecDestroy(split_graph);
+        split_graph = nullptr;
+        const int st = build_split_graph(&split_graph);
+        if (st != GDP_OK) return st;
+        split_key = P;
+      }
+      if (set_ctrl_field(offsetof(Ctrl, guard_r), 0) != GDP_OK ||
+          set_ctrl_field(offsetof(Ctrl, guard_f), 0) != GDP_OK)
+        return GDP_ERR_CUDA;
+      CK(cudaGraphLaunch(split_graph, stream));
+      if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (hctrl->err) return hctrl->err;
+      // kernels run: 27 per round pair, 9 per flip loop iteration
+      launches += 27LL * (hctrl->guard_r + 1) + 9LL * hctrl->guard_f;
+      last = hctrl->n_pts;
+    }
+    while (!use_graph && hctrl->n_pts > 0) {
       Pool Q = P;
       if (parity) std::swap(Q.pts, Q.pts2);
       int st;
@@ -725,7 +872,15 @@ int PoolHost::insert_rounds(int stop_cons, int* rounds_out, bool split) {
 
 int PoolHost::build_cdt() {
   CK(cudaEventRecord(ev0, stream));
-  LAUNCH(*this, k_cdt_init, n_mesh, P);
+  double* part = nullptr;
+  {
+    const int st0 = alloc(&part, 4 * (size_t)mesh_grid.x * n_mesh);
+    if (st0 != GDP_OK) return st0;
+  }
+  LAUNCH(*this, k_cdt_bbox, mesh_grid, P, part);
+  LAUNCH(*this, k_cdt_init, n_mesh, P, part, (int)mesh_grid.x);
+  LAUNCH(*this, k_cdt_vf, mesh_grid, P);
+  release(part);
   CK(cudaGetLastError());
   std::memset(hctrl, 0, sizeof(Ctrl));
   hctrl->n_pts = (int)(tot_in + 4 * n_mesh);

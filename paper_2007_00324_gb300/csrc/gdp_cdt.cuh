@@ -18,46 +18,63 @@
 
 namespace gdp {
 
-// one block per mesh: bounding box, enclosing triangle, pending point list
-__global__ void k_cdt_init(Pool P) {
-  const int m = blockIdx.x;
-  MeshInfo& M = P.mi[m];
+// Construction set-up, per mesh over a 2D grid (x: blocks of one mesh, y:
+// meshes).  k_cdt_bbox: partial bounding boxes (4 doubles per block) and the
+// pending point list; k_cdt_init (one block per mesh): the box, the enclosing
+// triangle and the frame; k_cdt_vf: the float copies of the input points.
+__global__ void __launch_bounds__(BS) k_cdt_bbox(Pool P, double* part) {
   __shared__ double sx0[BS], sx1[BS], sy0[BS], sy1[BS];
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
-  for (int k = threadIdx.x; k < M.n_in; k += blockDim.x) {
-    const int v = M.vert_base + k;
-    const double2 p = P.V[v];
-    if (!isfinite(p.x) || !isfinite(p.y)) bad = 1;
-    x0 = fmin(x0, p.x); x1 = fmax(x1, p.x);
-    y0 = fmin(y0, p.y); y1 = fmax(y1, p.y);
-    P.loc[v] = M.tri_base;
-    P.vseg[v] = -1;
-    P.pts[M.pts_base + k] = v;
-  }
-  sx0[threadIdx.x] = x0; sx1[threadIdx.x] = x1; sy0[threadIdx.x] = y0; sy1[threadIdx.x] = y1;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      sx0[threadIdx.x] = fmin(sx0[threadIdx.x], sx0[threadIdx.x + s]);
-      sx1[threadIdx.x] = fmax(sx1[threadIdx.x], sx1[threadIdx.x + s]);
-      sy0[threadIdx.x] = fmin(sy0[threadIdx.x], sy0[threadIdx.x + s]);
-      sy1[threadIdx.x] = fmax(sy1[threadIdx.x], sy1[threadIdx.x + s]);
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    MeshInfo& M = P.mi[m];
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int k = blockIdx.x * BS + threadIdx.x; k < M.n_in; k += gridDim.x * BS) {
+      const int v = M.vert_base + k;
+      const double2 p = P.V[v];
+      if (!isfinite(p.x) || !isfinite(p.y)) M.status = S_INPUT;
+      x0 = fmin(x0, p.x); x1 = fmax(x1, p.x);
+      y0 = fmin(y0, p.y); y1 = fmax(y1, p.y);
+      P.loc[v] = M.tri_base;
+      P.vseg[v] = -1;
+      P.pts[M.pts_base + k] = v;
+    }
+    sx0[threadIdx.x] = x0; sx1[threadIdx.x] = x1; sy0[threadIdx.x] = y0; sy1[threadIdx.x] = y1;
+    __syncthreads();
+    for (int s = BS / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        sx0[threadIdx.x] = fmin(sx0[threadIdx.x], sx0[threadIdx.x + s]);
+        sx1[threadIdx.x] = fmax(sx1[threadIdx.x], sx1[threadIdx.x + s]);
+        sy0[threadIdx.x] = fmin(sy0[threadIdx.x], sy0[threadIdx.x + s]);
+        sy1[threadIdx.x] = fmax(sy1[threadIdx.x], sy1[threadIdx.x + s]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double* q = part + 4 * ((size_t)m * gridDim.x + blockIdx.x);
+      q[0] = sx0[0]; q[1] = sx1[0]; q[2] = sy0[0]; q[3] = sy1[0];
     }
     __syncthreads();
   }
+}
+
+__global__ void k_cdt_init(Pool P, const double* part, int bx) {
+  const int m = blockIdx.x;
+  MeshInfo& M = P.mi[m];
   if (threadIdx.x == 0) {
-    if (bad || M.n_in < 3) {
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int b = 0; b < bx; ++b) {
+      const double* q = part + 4 * ((size_t)m * bx + b);
+      x0 = fmin(x0, q[0]); x1 = fmax(x1, q[1]);
+      y0 = fmin(y0, q[2]); y1 = fmax(y1, q[3]);
+    }
+    if (M.status == S_INPUT || M.n_in < 3) {
       M.status = S_INPUT;
       M.active = 0;
     }
-    const double cx = 0.5 * (sx0[0] + sx1[0]), cy = 0.5 * (sy0[0] + sy1[0]);
-    double D = fmax(sx1[0] - sx0[0], sy1[0] - sy0[0]);
+    const double cx = 0.5 * (x0 + x1), cy = 0.5 * (y0 + y1);
+    double D = fmax(x1 - x0, y1 - y0);
     if (!(D > 0)) D = 1.0;
-    M.lo = make_double2(sx0[0], sy0[0]);
-    M.hi = make_double2(sx1[0], sy1[0]);
+    M.lo = make_double2(x0, y0);
+    M.hi = make_double2(x1, y1);
     M.org = make_double2(cx, cy);
     const int s0 = M.vert_base + M.n_in;
     P.V[s0] = make_double2(cx - 64 * D, cy - 64 * D);
@@ -67,11 +84,14 @@ __global__ void k_cdt_init(Pool P) {
       P.vseg[s0 + k] = -1;
       P.vtri[s0 + k] = M.tri_base;
     }
-    const double d = 0.5 * D;
-    P.V[s0 + 3] = make_double2(sx0[0] - d, sy0[0] - d);
-    P.V[s0 + 4] = make_double2(sx1[0] + d, sy0[0] - d);
-    P.V[s0 + 5] = make_double2(sx1[0] + d, sy1[0] + d);
-    P.V[s0 + 6] = make_double2(sx0[0] - d, sy1[0] + d);
+    // frame 16 D out (inside the enclosing triangle): far enough that few
+    // Delaunay edges from interior points to the frame cross the input's
+    // hull, so boundary segments are mostly edges already
+    const double d = 16.0 * D;
+    P.V[s0 + 3] = make_double2(x0 - d, y0 - d);
+    P.V[s0 + 4] = make_double2(x1 + d, y0 - d);
+    P.V[s0 + 5] = make_double2(x1 + d, y1 + d);
+    P.V[s0 + 6] = make_double2(x0 - d, y1 + d);
     for (int k = 3; k < N_AUX; ++k) {
       P.vseg[s0 + k] = -1;
       P.loc[s0 + k] = M.tri_base;
@@ -83,11 +103,16 @@ __global__ void k_cdt_init(Pool P) {
     M.tri_count = 1;
     M.vert_count = M.n_in + N_AUX;
   }
-  __syncthreads();
-  const double2 org = M.org;
-  for (int k = threadIdx.x; k < M.n_in; k += blockDim.x) {
-    const int v = M.vert_base + k;
-    P.Vf[v] = to_f(P.V[v], org);
+}
+
+__global__ void __launch_bounds__(BS) k_cdt_vf(Pool P) {
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    const MeshInfo& M = P.mi[m];
+    const double2 org = M.org;
+    for (int k = blockIdx.x * BS + threadIdx.x; k < M.n_in; k += gridDim.x * BS) {
+      const int v = M.vert_base + k;
+      P.Vf[v] = to_f(P.V[v], org);
+    }
   }
 }
 
@@ -469,6 +494,38 @@ __global__ void k_fl_next(Pool P) {
   P.ctrl->n_fl = P.ctrl->n_fl_next;
   P.ctrl->n_fl_next = 0;
   ++P.ctrl->step;
+}
+
+// start of a construction round (one thread): this round's counters
+__global__ void k_round_begin(Pool P) {
+  P.ctrl->n_ins = 0ull;
+  P.ctrl->n_surv = 0ull;
+}
+
+// Conditions of the device-side loops of the construction graph (one
+// thread).  Both loops are bounded: past the limit the kernel records an
+// internal error and ends the loop.
+constexpr int GUARD_ROUND_PAIRS = 1000;   // 2000 rounds (12-bit round keys)
+constexpr int GUARD_FLIP = 1 << 17;
+
+__global__ void k_flip_cond(Pool P, cudaGraphConditionalHandle h) {
+  Ctrl* C = P.ctrl;
+  bool go = C->n_fl > 0 && C->err == 0;
+  if (go && ++C->guard_f > GUARD_FLIP) {
+    set_err(C, S_INTERNAL);
+    go = false;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_round_cond(Pool P, cudaGraphConditionalHandle h) {
+  Ctrl* C = P.ctrl;
+  bool go = C->n_pts > 0 && C->n_cand > 0 && C->err == 0;
+  if (go && ++C->guard_r > GUARD_ROUND_PAIRS) {
+    set_err(C, S_INTERNAL);
+    go = false;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 // a triangle at every vertex (the segment walks start there)

@@ -78,6 +78,8 @@ struct Ctrl {
   int32_t n_fl_next;     // CDT: triangles pushed for the next flip pass
   int32_t step;          // CDT: split / flip pass number (stamps, flip keys)
   int32_t scan_hi;       // refinement scans slots [0, scan_hi); 0 = all slots
+  int32_t guard_r;       // CDT graph loops: round pairs run (bounded)
+  int32_t guard_f;       // CDT graph loops: flip conditions evaluated (bounded)
   unsigned long long tot_cand, tot_ins, iters, n_ins, n_surv;
   // refinement work counters (algorithmic bytes of the cavity kernels)
   unsigned long long n_grown, sum_cav, sum_bnd, sum_walk;

@@ -115,7 +115,8 @@ __device__ __forceinline__ float2 to_f(double2 p, double2 org) {
 
 // ---------------------------------------------------------------- mesh queries
 // Auxiliary vertices of every mesh, right after its input points: three
-// enclosing vertices, then four frame vertices around the bounding box.  The
+// enclosing vertices, then four frame vertices around the bounding box (16
+// times its size out).  The
 // frame is inserted first, so every input point lies inside the triangulated
 // region from then on and points never queue up outside a growing hull.  All
 // seven lie outside the segment-bounded domain and are removed with the
