@@ -34,7 +34,7 @@ CONFIG = {"workload": "mid: unit square + 100,000 uniform FP64 points + 1,000 ra
                       "segments, B=sqrt(2)", "points": 100_004, "segments": 1_004, "B": SQ2,
           "l2": "flushed between steps (512 MB write)"}
 
-# Algorithmic bytes of the dominant kernel, k_grow<0> (cavity growth of the
+# Algorithmic bytes of the dominant kernel, k_grow_w<0> (cavity growth of the
 # refinement, Sec. 5.2): what each grown candidate must read and write once,
 # from the device layout (triangle T/N 16 B each, vertex 16 B FP64 + 8 B FP32
 # copy, marks 8 B), with the work counters the library reports:
@@ -45,7 +45,7 @@ CONFIG = {"workload": "mid: unit square + 100,000 uniform FP64 points + 1,000 ra
 #   per boundary edge 56 = neighbour test 40 + boundary record 16
 GROW_BYTES = {"candidate": 134, "walk_step": 56, "cavity_tri": 84, "boundary_edge": 56}
 GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_grow0_mid_traffic.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_grow_w0_mid_traffic.md")
 
 
 def grow_bytes(st) -> float:
@@ -63,7 +63,7 @@ def grow_source_hash() -> str:
 
 
 def measured_traffic():
-    """DRAM bytes per k_grow<0> launch from the committed ncu summary, or None
+    """DRAM bytes per k_grow_w<0> launch from the committed ncu summary, or None
     when the kernel's sources changed since it was captured."""
     try:
         with open(TRAFFIC_FILE) as f:
@@ -544,7 +544,7 @@ def main():
     tot_k = sum(v[0] for v in kt.values())
     top = max(kt.items(), key=lambda kv: kv[1][0])
     peak, peak_kind = peaks()
-    # roofline of k_grow<0> over the timed steps: algorithmic bytes from the
+    # roofline of k_grow_w<0> over the timed steps: algorithmic bytes from the
     # work counters / device time from the events recorded around each launch
     n_l = max(grow["grow_launches"], 1)
     by = grow_bytes(grow)
@@ -552,9 +552,9 @@ def main():
     tr = measured_traffic()
     roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
             "frac": (gbs / peak) if gbs else None, "traffic": tr,
-            "kernel": "k_grow<0>", "algorithmic_bytes_per_launch": by / n_l,
+            "kernel": "k_grow_w<0>", "algorithmic_bytes_per_launch": by / n_l,
             "kernel_ms_per_launch": grow["grow_ms"] / n_l, "launches": grow["grow_launches"],
-            "share_of_kernel_time": kt.get("k_grow<0>", (0.0, 0))[0] / tot_k,
+            "share_of_kernel_time": kt.get("k_grow_w<0>", (0.0, 0))[0] / tot_k,
             "largest_kernel": top[0],
             "peak_source": "measured (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "mean_cavity_tris": grow["cavity_tris"] / max(grow["grown"], 1),

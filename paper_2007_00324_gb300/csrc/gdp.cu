@@ -159,7 +159,7 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
 // candidate cavities: own slots, then the two spill tiers
 #define LAUNCH_GROW(h, MODE, P)                                      \
   do {                                                               \
-    LAUNCH_C(h, k_grow<MODE>, P);                                    \
+    LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P);              \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_A / 32, 32, P, 0);           \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_B, 1, P, 1);                 \
   } while (0)
@@ -180,6 +180,8 @@ static void print_diag(const char* where) {
                "[%s] orient_exact %llu incircle_exact %llu (inexact diffs %llu, max %llu cyc) sos %llu "
                "dot_exact %llu | max walk steps %llu, max walk cyc %llu, max grow cyc %llu\n",
                where, d[0], d[1], d[4], d[8], d[2], d[3], d[5], d[7], d[6]);
+  std::fprintf(stderr, "[%s] grow cycles histogram <4k %llu <8k %llu <16k %llu <32k %llu <64k %llu <128k %llu more %llu\n",
+               where, d[9], d[10], d[11], d[12], d[13], d[14], d[15]);
   unsigned long long z[16] = {};
   cudaMemcpyToSymbol(g_diag, z, sizeof(z));
 }
@@ -452,7 +454,7 @@ struct PoolHost {
     bs_cand = (b == 32 || b == 128 || b == 256) ? b : 64;
     Gc = n_sm * (1024 / bs_cand);
   }
-  // GDP_REFINE_TIME_GROW: an event pair around k_grow<0> per iteration slot of the graph
+  // GDP_REFINE_TIME_GROW: an event pair around k_grow_w<0> per iteration slot of the graph
   bool time_grow = false;
   std::vector<cudaEvent_t> tg;
   int add_grow_times(int iters);
@@ -1029,7 +1031,7 @@ int PoolHost::launch_iteration(int k) {
   LAUNCH(*this, k_scan_write, G, P);
   const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k], stream, rec));
-  LAUNCH_C(*this, k_grow<0>, P);
+  LAUNCH_B(*this, k_grow_w<0>, n_sm * 16, 128, P);
   if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k + 1], stream, rec));
   LAUNCH_B(*this, k_grow_big<0>, LANES_A / 32, 32, P, 0);
   LAUNCH_B(*this, k_grow_big<0>, LANES_B, 1, P, 1);

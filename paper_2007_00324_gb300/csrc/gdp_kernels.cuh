@@ -571,113 +571,6 @@ struct GrowAcc {
   unsigned long long grown = 0, cav = 0, bnd = 0, walk = 0;
 };
 
-template <int MODE>
-__device__ int grow_cand(const Pool& P, int i, const CavBuf& B, GrowAcc& acc) {
-  P.c_ncav[i] = 0;
-  P.c_nbnd[i] = 0;
-  P.c_state[i] = C_FAIL;
-  P.c_final[i] = 0;
-  const int elem = P.c_elem[i];
-  double2 p;
-  unsigned long long key;
-  int t0, t1 = -1, m, vid = -1;
-  bool conv = false;
-  int2 sub = make_int2(-1, -1);
-  if (MODE == 1) {
-    vid = elem;
-    t0 = P.c_loc[i];
-    m = P.T[t0].w >> 4;
-    p = P.V[vid];
-    key = ((unsigned long long)insert_prio(P.mi[m], vid) << 32) | (unsigned)i;
-  } else {
-    const int t = elem >> 2, k = elem & 3;
-    const int4 T4 = P.T[t];
-    m = T4.w >> 4;
-    const MeshInfo& M = P.mi[m];
-    if (k == 3) {
-      const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
-      p = circumcenter(tt);
-      key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
-      int bt = -1, be = -1;
-      int steps = 0;
-      const int r = walk(P, t, P2{p, to_f(p, M.org)}, true, bt, be, steps);
-      acc.walk += steps;
-      if (r == -2) {
-        P.c_mesh[i] = m;
-        set_err(P.ctrl, S_WALK);
-        return G_OK;
-      }
-      if (r == -1) {
-        // the walk meets a subsegment: split it instead (Sec. 4.3)
-        const int4 B4 = P.T[bt];
-        const int u = comp(B4, mod3(be + 1)), v = comp(B4, mod3(be + 2));
-        p = split_point(P, M, u, v);
-        key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
-              (unsigned)i;
-        t0 = bt;
-        const int nr = comp(P.N[bt], be);
-        t1 = nr >= 0 ? nr >> 2 : -1;
-        sub = make_int2(u, v);
-      } else {
-        t0 = r;
-        conv = true;
-      }
-    } else {
-      const int u = comp(T4, mod3(k + 1)), v = comp(T4, mod3(k + 2));
-      p = split_point(P, M, u, v);
-      key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
-            (unsigned)i;
-      t0 = t;
-      const int nr = comp(P.N[t], k);
-      t1 = nr >= 0 ? nr >> 2 : -1;
-      sub = make_int2(u, v);
-    }
-  }
-  P.c_mesh[i] = m;
-  P2 pp{p, MODE == 1 ? P.Vf[vid] : to_f(p, P.mi[m].org)};
-  int nc = 0, nb = 0, ct = -1, ce = -1;
-#ifdef GDP_DIAG
-  const long long gc0 = clock64();
-#endif
-  int g = grow(P, B, pp, t0, t1, conv, nc, nb, ct, ce);
-#ifdef GDP_DIAG
-  atomicMax(&g_diag[6], (unsigned long long)(clock64() - gc0));
-#endif
-  if (g == G_CONV) {
-    const int4 B4 = P.T[ct];
-    const int u = comp(B4, mod3(ce + 1)), v = comp(B4, mod3(ce + 2));
-    p = split_point(P, P.mi[m], u, v);
-    key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
-          (unsigned)i;
-    sub = make_int2(u, v);
-    const int nr = comp(P.N[ct], ce);
-    pp = P2{p, to_f(p, P.mi[m].org)};
-    g = grow(P, B, pp, ct, nr >= 0 ? nr >> 2 : -1, false, nc, nb, ct, ce);
-  }
-  if (g == G_OVF) return G_OVF;
-  bool ok = true;
-  for (int r = 0; r < nb && ok; ++r) {
-    const int4 rec = B.bnd[r];
-    if (is_split_edge(rec, sub)) continue;
-    if (orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) ok = false;
-  }
-  if (!ok) return G_OK;
-  for (int j = 0; j < nc; ++j) atomicMax(&P.mark[B.cav[j]], key);
-  P.c_pt[i] = p;
-  P.c_ptf[i] = pp.f;
-  P.c_key[i] = key;
-  P.c_ncav[i] = nc;
-  P.c_nbnd[i] = nb;
-  P.c_sub[i] = sub;
-  P.c_vid[i] = vid;
-  P.c_vseg[i] = (sub.x >= 0) ? seg_of_sub(P, P.mi[m], sub.x, sub.y) : -1;
-  P.c_state[i] = C_GROWN;
-  acc.grown += 1;
-  acc.cav += nc;
-  acc.bnd += nb;
-  return G_OK;
-}
-
 __device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a) {
   for (int o = 16; o; o >>= 1) {
     a.grown += __shfl_xor_sync(0xffffffffu, a.grown, o);
@@ -693,18 +586,316 @@ __device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a) {
   }
 }
 
+// Splitting point, priority key and start triangles of candidate i
+// (Algorithm 1 lines 5-6).  MODE 0: refinement candidates (element =
+// triangle << 2 | edge, 3 = the triangle); MODE 1: given points (element =
+// vertex id, c_loc = located triangle).  False when the walk failed.
+struct CandSetup {
+  double2 p;
+  float2 pf;
+  unsigned long long key;
+  int t0, t1, m, vid;
+  int2 sub;
+  bool conv;
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(BS) k_grow(Pool P) {
-  const int n = P.ctrl->n_cand;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  GrowAcc acc;
-  for (int i = gt; i < n; i += gs) {
-    P.c_big[i] = -1;
-    const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
-    if (grow_cand<MODE>(P, i, B, acc) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+__device__ bool cand_setup(const Pool& P, int i, CandSetup& s, GrowAcc& acc) {
+  P.c_ncav[i] = 0;
+  P.c_nbnd[i] = 0;
+  P.c_state[i] = C_FAIL;
+  P.c_final[i] = 0;
+  const int elem = P.c_elem[i];
+  s.t1 = -1;
+  s.vid = -1;
+  s.conv = false;
+  s.sub = make_int2(-1, -1);
+  if (MODE == 1) {
+    s.vid = elem;
+    s.t0 = P.c_loc[i];
+    s.m = P.T[s.t0].w >> 4;
+    s.p = P.V[s.vid];
+    s.key = ((unsigned long long)insert_prio(P.mi[s.m], s.vid) << 32) | (unsigned)i;
+  } else {
+    const int t = elem >> 2, k = elem & 3;
+    const int4 T4 = P.T[t];
+    s.m = T4.w >> 4;
+    const MeshInfo& M = P.mi[s.m];
+    if (k == 3) {
+      const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
+      s.p = circumcenter(tt);
+      s.key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
+      int bt = -1, be = -1;
+      int steps = 0;
+      const int r = walk(P, t, P2{s.p, to_f(s.p, M.org)}, true, bt, be, steps);
+      acc.walk += steps;
+      if (r == -2) {
+        P.c_mesh[i] = s.m;
+        set_err(P.ctrl, S_WALK);
+        return false;
+      }
+      if (r == -1) {
+        // the walk meets a subsegment: split it instead (Sec. 4.3)
+        const int4 B4 = P.T[bt];
+        const int u = comp(B4, mod3(be + 1)), v = comp(B4, mod3(be + 2));
+        s.p = split_point(P, M, u, v);
+        s.key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+                (unsigned)i;
+        s.t0 = bt;
+        const int nr = comp(P.N[bt], be);
+        s.t1 = nr >= 0 ? nr >> 2 : -1;
+        s.sub = make_int2(u, v);
+      } else {
+        s.t0 = r;
+        s.conv = true;
+      }
+    } else {
+      const int u = comp(T4, mod3(k + 1)), v = comp(T4, mod3(k + 2));
+      s.p = split_point(P, M, u, v);
+      s.key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
+              (unsigned)i;
+      s.t0 = t;
+      const int nr = comp(P.N[t], k);
+      s.t1 = nr >= 0 ? nr >> 2 : -1;
+      s.sub = make_int2(u, v);
+    }
   }
-  if (MODE == 0) acc_flush(P, acc);   // every thread of the block reaches this
+  P.c_mesh[i] = s.m;
+  s.pf = MODE == 1 ? P.Vf[s.vid] : to_f(s.p, P.mi[s.m].org);
+  return true;
 }
+
+// the circumcentre encroaches subsegment edge ce of triangle ct on its
+// cavity boundary: that subsegment's split point replaces it (Sec. 4.2)
+__device__ void cand_conv(const Pool& P, int i, CandSetup& s, int ct, int ce) {
+  const int4 B4 = P.T[ct];
+  const int u = comp(B4, mod3(ce + 1)), v = comp(B4, mod3(ce + 2));
+  s.p = split_point(P, P.mi[s.m], u, v);
+  s.key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) | (unsigned)i;
+  s.sub = make_int2(u, v);
+  s.pf = to_f(s.p, P.mi[s.m].org);
+  const int nr = comp(P.N[ct], ce);
+  s.t0 = ct;
+  s.t1 = nr >= 0 ? nr >> 2 : -1;
+  s.conv = false;
+}
+
+// the grown candidate's record (lines 6-7 of the candidate's state)
+__device__ void cand_record(const Pool& P, int i, const CandSetup& s, int nc, int nb, GrowAcc& acc) {
+  P.c_pt[i] = s.p;
+  P.c_ptf[i] = s.pf;
+  P.c_key[i] = s.key;
+  P.c_ncav[i] = nc;
+  P.c_nbnd[i] = nb;
+  P.c_sub[i] = s.sub;
+  P.c_vid[i] = s.vid;
+  P.c_vseg[i] = (s.sub.x >= 0) ? seg_of_sub(P, P.mi[s.m], s.sub.x, s.sub.y) : -1;
+  P.c_state[i] = C_GROWN;
+  acc.grown += 1;
+  acc.cav += nc;
+  acc.bnd += nb;
+}
+
+// One candidate, one thread (the spill tiers; any cavity size up to the
+// buffer's capacity).  Returns G_OVF when the cavity does not fit B, else
+// G_OK (c_state tells whether the candidate was grown).
+template <int MODE>
+__device__ int grow_cand(const Pool& P, int i, const CavBuf& B, GrowAcc& acc) {
+  CandSetup s;
+  if (!cand_setup<MODE>(P, i, s, acc)) return G_OK;
+  P2 pp{s.p, s.pf};
+  int nc = 0, nb = 0, ct = -1, ce = -1;
+#ifdef GDP_DIAG
+  const long long gc0 = clock64();
+#endif
+  int g = grow(P, B, pp, s.t0, s.t1, s.conv, nc, nb, ct, ce);
+#ifdef GDP_DIAG
+  atomicMax(&g_diag[6], (unsigned long long)(clock64() - gc0));
+#endif
+  if (g == G_CONV) {
+    cand_conv(P, i, s, ct, ce);
+    pp = P2{s.p, s.pf};
+    g = grow(P, B, pp, s.t0, s.t1, false, nc, nb, ct, ce);
+  }
+  if (g == G_OVF) return G_OVF;
+  bool ok = true;
+  for (int r = 0; r < nb && ok; ++r) {
+    const int4 rec = B.bnd[r];
+    if (is_split_edge(rec, s.sub)) continue;
+    if (orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) ok = false;
+  }
+  if (!ok) return G_OK;
+  for (int j = 0; j < nc; ++j) atomicMax(&P.mark[B.cav[j]], s.key);
+  cand_record(P, i, s, nc, nb, acc);
+  return G_OK;
+}
+
+// ---------------------------------------------------------------- warp-cooperative growth
+// The cavity of one candidate grown by one warp, level by level: the lanes
+// test the (cavity triangle, edge) tuples of a level in parallel (the
+// tuple-list expansion of Sec. 5.3).  New triangles and boundary records
+// are appended in (parent, edge) order, and a tuple sees the triangles that
+// tuples before it added as cavity members, so the cavity list, the boundary
+// records, the first encroached subsegment and the overflow point are those
+// of the sequential breadth-first growth (grow) above.  Capacity CMAX = 32
+// triangles (the warp width), BMAX boundary edges; the list of the cavity so
+// far sits in shared memory (wc).
+__device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, int t0, int t1,
+                     bool conv, int& nc, int& nb, int& ct, int& ce) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  int k = 1, b = 0;
+  if (lane == 0) {
+    wc[0] = t0;
+    cav[0] = t0;
+  }
+  if (t1 >= 0 && t1 != t0) {
+    if (lane == 0) {
+      wc[1] = t1;
+      cav[1] = t1;
+    }
+    k = 2;
+  }
+  __syncwarp();
+  int lb = 0;
+  while (lb < k) {
+    const int le = k;
+    for (int base = 3 * lb; base < 3 * le; base += 32) {
+      const int slot = base + lane;
+      const bool act = slot < 3 * le;
+      int e = 0, ref = -1, cons = 0, u = -1, v = -1, tn = -1, t = -1;
+      if (act) {
+        const int q = slot / 3;
+        e = slot - 3 * q;
+        t = wc[q];
+        const int4 T4 = P.T[t];
+        const int4 N4 = P.N[t];
+        ref = comp(N4, e);
+        cons = (T4.w >> e) & 1;
+        u = comp(T4, mod3(e + 1));
+        v = comp(T4, mod3(e + 2));
+        tn = ref >= 0 ? ref >> 2 : -1;
+      }
+      bool member = false;
+      for (int j = 0; j < k; ++j) member |= (wc[j] == tn);
+      // one incircle test per distinct neighbour (the lowest lane's)
+      const bool test = act && !member && tn >= 0 && !cons;
+      const unsigned same = __match_any_sync(FULL, test ? tn : -2 - lane);
+      const int leader = __ffs(same) - 1;
+      bool in = false;
+      if (test && lane == leader) {
+        const int4 Tn = P.T[tn];
+        in = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
+      }
+      in = __shfl_sync(FULL, in, leader);
+      const unsigned adders = __ballot_sync(FULL, test && lane == leader && in);
+      // a triangle added by an earlier tuple of this chunk is a cavity member
+      const unsigned same_all = __match_any_sync(FULL, (act && tn >= 0) ? tn : -2 - lane);
+      if (act && tn >= 0 && (same_all & adders & lt_mask)) member = true;
+      // 1 add, 2 boundary record, 3 encroached subsegment (the circumcentre gives way)
+      int ev = 0;
+      if (act && !member) {
+        if (test) ev = (lane == leader && in) ? 1 : (in ? 0 : 2);
+        else if (cons && conv && dot_sign(pt(P, u), pt(P, v), p) < 0) ev = 3;
+        else ev = 2;
+      }
+      const unsigned am = __ballot_sync(FULL, ev == 1);
+      const unsigned rm = __ballot_sync(FULL, ev == 2);
+      const unsigned cm = __ballot_sync(FULL, ev == 3);
+      const int ar = __popc(am & lt_mask), rr = __popc(rm & lt_mask);
+      const unsigned ovf = __ballot_sync(FULL, (ev == 1 && k + ar >= CMAX) || (ev == 2 && b + rr >= BMAX));
+      const int first_conv = cm ? __ffs(cm) - 1 : 32;
+      const int first_ovf = ovf ? __ffs(ovf) - 1 : 32;
+      if (first_conv < first_ovf) {
+        ct = __shfl_sync(FULL, t, first_conv);
+        ce = __shfl_sync(FULL, e, first_conv);
+        return G_CONV;
+      }
+      if (first_ovf < 32) return G_OVF;
+      if (ev == 1) {
+        wc[k + ar] = tn;
+        cav[k + ar] = tn;
+      } else if (ev == 2) {
+        bnd[b + rr] = make_int4(u, v, ref, (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
+      }
+      k += __popc(am);
+      b += __popc(rm);
+      __syncwarp();
+    }
+    lb = le;
+  }
+  nc = k;
+  nb = b;
+  return G_OK;
+}
+
+// Cavity growth of the candidates in their own slots of CMAX triangles
+// (larger cavities go to the spill tiers).  Up to WARP_GROW_MAX candidates
+// -- the usual, latency-bound case -- one warp grows each cavity (wgrow);
+// beyond that the launch is throughput-bound and one thread per candidate
+// does less total work (grow).  Both give the same cavities.
+constexpr int WARP_GROW_MAX = 32768;
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_grow_w(Pool P) {
+  __shared__ int wcs[4][32];
+  __shared__ CandSetup ws[4];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n = P.ctrl->n_cand;
+  int* wc = wcs[wib];
+  GrowAcc acc;
+  if (n > WARP_GROW_MAX) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (int i = gt; i < n; i += gs) {
+      P.c_big[i] = -1;
+      const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
+      if (grow_cand<MODE>(P, i, B, acc) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+    }
+    if (MODE == 0) acc_flush(P, acc);
+    return;
+  }
+  for (int i = gw; i < n; i += nw) {
+    int ok = 1;
+    if (lane == 0) {
+      P.c_big[i] = -1;
+      ok = cand_setup<MODE>(P, i, ws[wib], acc) ? 1 : 0;
+    }
+    __syncwarp();
+    if (!__shfl_sync(FULL, ok, 0)) continue;
+    CandSetup s = ws[wib];
+    int* cav = P.c_cav + (size_t)i * CMAX;
+    int4* bnd = P.c_bnd + (size_t)i * BMAX;
+    int nc = 0, nb = 0, ct = -1, ce = -1;
+    int g = wgrow(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, s.conv, nc, nb, ct, ce);
+    if (g == G_CONV) {
+      if (lane == 0) cand_conv(P, i, ws[wib], ct, ce);
+      __syncwarp();
+      s = ws[wib];
+      g = wgrow(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, false, nc, nb, ct, ce);
+    }
+    if (g == G_OVF) {
+      if (lane == 0) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+      __syncwarp();
+      continue;
+    }
+    __syncwarp();
+    const P2 pp{s.p, s.pf};
+    bool bad = false;
+    for (int r = lane; r < nb; r += 32) {
+      const int4 rec = bnd[r];
+      if (!is_split_edge(rec, s.sub) && orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) bad = true;
+    }
+    if (__any_sync(FULL, bad)) continue;
+    for (int j = lane; j < nc; j += 32) atomicMax(&P.mark[cav[j]], s.key);
+    if (lane == 0) cand_record(P, i, s, nc, nb, acc);
+    __syncwarp();
+  }
+  if (MODE == 0) acc_flush(P, acc);
+}
+
 
 // Cavities that outgrew their slot (tier 0) or their tier-A lane (tier 1):
 // one thread per lane; the lane is freed for the next round as it is read.
