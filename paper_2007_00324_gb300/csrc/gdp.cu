@@ -160,6 +160,7 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
 #define LAUNCH_GROW(h, MODE, P)                                      \
   do {                                                               \
     LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P);              \
+    LAUNCH_C(h, k_grow_t<MODE>, P);                                  \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_A / 32, 32, P, 0);           \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_B, 1, P, 1);                 \
   } while (0)
@@ -1032,6 +1033,7 @@ int PoolHost::launch_iteration(int k) {
   const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k], stream, rec));
   LAUNCH_B(*this, k_grow_w<0>, n_sm * 16, 128, P);
+  LAUNCH_C(*this, k_grow_t<0>, P);
   if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k + 1], stream, rec));
   LAUNCH_B(*this, k_grow_big<0>, LANES_A / 32, 32, P, 0);
   LAUNCH_B(*this, k_grow_big<0>, LANES_B, 1, P, 1);

@@ -832,13 +832,14 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
 
 // Cavity growth of the candidates in their own slots of CMAX triangles
 // (larger cavities go to the spill tiers).  Up to WARP_GROW_MAX candidates
-// -- the usual, latency-bound case -- one warp grows each cavity (wgrow);
-// beyond that the launch is throughput-bound and one thread per candidate
-// does less total work (grow).  Both give the same cavities.
+// -- the usual, latency-bound case -- one warp grows each cavity (wgrow,
+// k_grow_w); beyond that the launch is throughput-bound and one thread per
+// candidate does less total work (grow, k_grow_t).  Both give the same
+// cavities.
 constexpr int WARP_GROW_MAX = 32768;
 
 template <int MODE>
-__global__ void __launch_bounds__(128) k_grow_w(Pool P) {
+__global__ void __maxnreg__(128) k_grow_w(Pool P) {
   __shared__ int wcs[4][32];
   __shared__ CandSetup ws[4];
   const unsigned FULL = 0xffffffffu;
@@ -846,17 +847,8 @@ __global__ void __launch_bounds__(128) k_grow_w(Pool P) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n = P.ctrl->n_cand;
   int* wc = wcs[wib];
+  if (n > WARP_GROW_MAX) return;   // k_grow_t's case
   GrowAcc acc;
-  if (n > WARP_GROW_MAX) {
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-    for (int i = gt; i < n; i += gs) {
-      P.c_big[i] = -1;
-      const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
-      if (grow_cand<MODE>(P, i, B, acc) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
-    }
-    if (MODE == 0) acc_flush(P, acc);
-    return;
-  }
   for (int i = gw; i < n; i += nw) {
     int ok = 1;
     if (lane == 0) {
@@ -896,6 +888,23 @@ __global__ void __launch_bounds__(128) k_grow_w(Pool P) {
   if (MODE == 0) acc_flush(P, acc);
 }
 
+
+// the same, one thread per candidate, when there are more than
+// WARP_GROW_MAX candidates (a separate kernel keeps each version's register
+// allocation to itself)
+template <int MODE>
+__global__ void __launch_bounds__(BS) k_grow_t(Pool P) {
+  const int n = P.ctrl->n_cand;
+  if (n <= WARP_GROW_MAX) return;   // k_grow_w's case
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  GrowAcc acc;
+  for (int i = gt; i < n; i += gs) {
+    P.c_big[i] = -1;
+    const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
+    if (grow_cand<MODE>(P, i, B, acc) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+  }
+  if (MODE == 0) acc_flush(P, acc);   // every thread of the block reaches this
+}
 
 // Cavities that outgrew their slot (tier 0) or their tier-A lane (tier 1):
 // one thread per lane; the lane is freed for the next round as it is read.
