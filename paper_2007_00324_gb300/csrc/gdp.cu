@@ -394,6 +394,7 @@ struct PoolHost {
   int setup(const double* xy, const long long* pt_off, const int32_t* seg, const long long* seg_off,
             int nm, bool on_device, void* s);
   int build_cdt();
+  bool cdt_done = false;          // build_cdt ran to the end (mesh statuses are final)
   int insert_rounds(int stop_cons, int* rounds_out, bool split);
   int launch_cdt_round(const Pool& Q, int stop_cons);
   int launch_split_round(const Pool& Q);
@@ -1015,6 +1016,7 @@ int PoolHost::build_cdt() {
   // marks and the candidate list start empty
   if (set_ctrl_field(offsetof(Ctrl, prev_cand), 0) != GDP_OK) return GDP_ERR_CUDA;
   stats.n_in_pts = tot_in;
+  cdt_done = true;
   print_diag("cdt");
   int worst = GDP_OK;
   for (auto& M : hmi)

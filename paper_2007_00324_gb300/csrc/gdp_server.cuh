@@ -20,41 +20,45 @@
 #include <map>
 #include <memory>
 
-// Copy the single mesh of a staging pool S (construction done, compacted) into
-// the region of the resident pool D that starts at triangle dt, vertex dv,
+// Copy mesh ms of a staging pool S (construction done, compacted) into the
+// region of the resident pool D that starts at triangle dt, vertex dv,
 // segment ds, adjacency row da, as mesh md.  Triangle and vertex ids, segment
-// ids and CSR offsets are shifted; every triangle is marked dirty so that the
-// first scan evaluates it.
-__global__ void __launch_bounds__(BS) k_relocate(Pool D, Pool S, int md, int dt, int dv, int ds, int da) {
-  const MeshInfo& Ms = S.mi[0];
+// ids and CSR offsets are rebased; every triangle is marked dirty so that
+// the first scan evaluates it.
+__global__ void __launch_bounds__(BS) k_relocate(Pool D, Pool S, int ms, int md, int dt, int dv, int ds,
+                                                 int da) {
+  const MeshInfo& Ms = S.mi[ms];
+  const int st = Ms.tri_base, sv0 = Ms.vert_base, ss = Ms.seg_base, sa = Ms.adj_base;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int t = gt; t < Ms.tri_count; t += gs) {
-    const int4 T4 = S.T[t];
-    const int4 N4 = S.N[t];
-    D.T[dt + t] = make_int4(T4.x + dv, T4.y + dv, T4.z + dv, (md << 4) | (T4.w & 15));
+    const int4 T4 = S.T[st + t];
+    const int4 N4 = S.N[st + t];
+    const int sh = dv - sv0;
+    D.T[dt + t] = make_int4(T4.x + sh, T4.y + sh, T4.z + sh, (md << 4) | (T4.w & 15));
     int r[3] = {N4.x, N4.y, N4.z};
     for (int e = 0; e < 3; ++e)
-      if (r[e] >= 0) r[e] = (((r[e] >> 2) + dt) << 2) | (r[e] & 3);
+      if (r[e] >= 0) r[e] = (((r[e] >> 2) - st + dt) << 2) | (r[e] & 3);
     D.N[dt + t] = make_int4(r[0], r[1], r[2], 0);
     D.dirty[dt + t] = 1;
     D.flag[dt + t] = 0;
     D.mark[dt + t] = 0ull;
   }
   for (int v = gt; v < Ms.vert_count; v += gs) {
-    D.V[dv + v] = S.V[v];
-    D.Vf[dv + v] = S.Vf[v];
-    const int sv = S.vseg[v];
-    D.vseg[dv + v] = sv >= 0 ? sv + ds : -1;
-    const int tv = S.vtri[v];
-    D.vtri[dv + v] = tv >= 0 ? tv + dt : -1;
-    D.apex[dv + v] = S.apex[v];
+    D.V[dv + v] = S.V[sv0 + v];
+    D.Vf[dv + v] = S.Vf[sv0 + v];
+    const int sg = S.vseg[sv0 + v];
+    D.vseg[dv + v] = sg >= 0 ? sg - ss + ds : -1;
+    const int tv = S.vtri[sv0 + v];
+    D.vtri[dv + v] = tv >= 0 ? tv - st + dt : -1;
+    D.apex[dv + v] = S.apex[sv0 + v];
   }
   for (int g = gt; g < Ms.n_seg; g += gs) {
-    const int2 sg = S.seg[g];
-    D.seg[ds + g] = make_int2(sg.x + dv, sg.y + dv);
+    const int2 sg = S.seg[ss + g];
+    D.seg[ds + g] = make_int2(sg.x - sv0 + dv, sg.y - sv0 + dv);
   }
-  for (int k = gt; k <= Ms.n_in; k += gs) D.adj_off[da + k] = S.adj_off[k] + 2 * ds;
-  for (int j = gt; j < 2 * Ms.n_seg; j += gs) D.adj[2 * ds + j] = S.adj[j] + ds;
+  // the staging CSR is global: this mesh's entries start at 2 * its first segment
+  for (int k = gt; k <= Ms.n_in; k += gs) D.adj_off[da + k] = S.adj_off[sa + k] - 2 * ss + 2 * ds;
+  for (int j = gt; j < 2 * Ms.n_seg; j += gs) D.adj[2 * ds + j] = S.adj[2 * ss + j] - ss + ds;
 }
 
 // first-fit allocator of index ranges (triangle slots, vertices, segments,
@@ -127,12 +131,12 @@ struct gdp_server {
     long long t, v, s, a;          // offsets
     long long nt, nv, ns, na;      // sizes
   };
+  // the CDTs of several waiting requests, built together in one staging pool
   struct Staged {
-    Req r;
     std::unique_ptr<PoolHost> S;
-    int status = GDP_OK;
-    Region g{};
-    double t_admit = 0;
+    std::vector<Req> r;
+    std::vector<Region> g;
+    int status = GDP_OK;           // of the whole build (CUDA, internal errors)
   };
   struct Live {
     int64_t ticket;
@@ -259,75 +263,123 @@ static int server_setup(gdp_server* s, long long tb, long long vb, long long sb,
   return GDP_OK;
 }
 
-// builds the CDT of the oldest waiting requests that fit (side stream)
-static void server_stage(gdp_server* s, int max_builds) {
-  while (!s->waiting.empty() && max_builds-- > 0 && !s->free_ids.empty()) {
+// builds, in one staging pool on the side stream, the CDTs of the oldest
+// waiting requests that fit in the resident pool (first come, first served;
+// at most max_reqs requests or max_pts points per build)
+static void server_stage(gdp_server* s, int max_reqs, long long max_pts) {
+  gdp_server::Staged st;
+  long long pts = 0;
+  while (!s->waiting.empty() && (int)st.r.size() < max_reqs && (int)st.r.size() < (int)s->free_ids.size()) {
     gdp_server::Req& r = s->waiting.front();
-    gdp_server::Staged st;
-    region_sizes((long long)r.xy.size() / 2, (long long)r.seg.size() / 2, st.g);
-    if (!region_alloc(s, st.g)) break;   // first in, first served: wait for room
-    st.r = std::move(r);
+    const long long n = (long long)r.xy.size() / 2, m = (long long)r.seg.size() / 2;
+    if (!st.r.empty() && pts + n > max_pts) break;
+    gdp_server::Region g;
+    region_sizes(n, m, g);
+    if (!region_alloc(s, g)) break;   // wait for room
+    pts += n;
+    st.g.push_back(g);
+    st.r.push_back(std::move(r));
     s->waiting.pop_front();
-    st.S.reset(new PoolHost());
-    const long long n = (long long)st.r.xy.size() / 2, m = (long long)st.r.seg.size() / 2;
-    st.status = create_common(*st.S, st.r.xy.data(), n, st.r.seg.data(), m, false, s->side);
-    if (st.status == GDP_OK && st.S->pull_mi() != GDP_OK) st.status = GDP_ERR_CUDA;
-    s->staged.push_back(std::move(st));
   }
+  if (st.r.empty()) return;
+  const int k = (int)st.r.size();
+  std::vector<long long> po(k + 1, 0), so(k + 1, 0);
+  for (int i = 0; i < k; ++i) {
+    po[i + 1] = po[i] + (long long)st.r[i].xy.size() / 2;
+    so[i + 1] = so[i] + (long long)st.r[i].seg.size() / 2;
+  }
+  std::vector<double> xy((size_t)po[k] * 2);
+  std::vector<int32_t> sg((size_t)std::max<long long>(so[k], 1) * 2);
+  for (int i = 0; i < k; ++i) {
+    std::copy(st.r[i].xy.begin(), st.r[i].xy.end(), xy.begin() + 2 * po[i]);
+    std::copy(st.r[i].seg.begin(), st.r[i].seg.end(), sg.begin() + 2 * so[i]);
+  }
+  st.S.reset(new PoolHost());
+  int rc = st.S->setup(xy.data(), po.data(), sg.data(), so.data(), k, false, s->side);
+  if (rc == GDP_OK) rc = st.S->build_cdt();
+  // a build that ran to the end reports per-mesh errors in the mesh statuses
+  if (st.S->cdt_done) rc = GDP_OK;
+  if (rc == GDP_OK && st.S->pull_mi() != GDP_OK) rc = GDP_ERR_CUDA;
+  if (rc == GDP_ERR_INPUT && k > 1) {
+    // an invalid input stopped the whole build (e.g. crossing segments):
+    // build the requests one by one so that only the invalid ones fail
+    st.S.reset();
+    for (int i = 0; i < k; ++i) {
+      gdp_server::Staged one;
+      one.r.push_back(std::move(st.r[i]));
+      one.g.push_back(st.g[i]);
+      one.S.reset(new PoolHost());
+      const gdp_server::Req& q = one.r[0];
+      int r1 = create_common(*one.S, q.xy.data(), (long long)q.xy.size() / 2, q.seg.data(),
+                             (long long)q.seg.size() / 2, false, s->side);
+      if (one.S->cdt_done) r1 = GDP_OK;
+      if (r1 == GDP_OK && one.S->pull_mi() != GDP_OK) r1 = GDP_ERR_CUDA;
+      one.status = r1;
+      s->staged.push_back(std::move(one));
+    }
+    return;
+  }
+  st.status = rc;
+  s->staged.push_back(std::move(st));
 }
 
-static void server_fail(gdp_server* s, gdp_server::Staged& st) {
+static void server_fail(gdp_server* s, const gdp_server::Req& r, const gdp_server::Region& g, int status) {
   gdp_server::Done d{};
-  d.info.ticket = st.r.ticket;
-  d.info.status = st.status;
-  d.info.n_in_pts = (int64_t)st.r.xy.size() / 2;
-  d.info.t_submit_ms = st.r.t_submit;
+  d.info.ticket = r.ticket;
+  d.info.status = status;
+  d.info.n_in_pts = (int64_t)r.xy.size() / 2;
+  d.info.t_submit_ms = r.t_submit;
   d.info.t_admit_ms = d.info.t_done_ms = s->now_ms();
   s->done.push_back(std::move(d));
-  region_release(s, st.g);
+  region_release(s, g);
 }
 
 // staged CDTs into their regions of the resident pool (main stream)
 static int server_admit(gdp_server* s) {
   PoolHost& h = s->h;
-  bool any = false;
   for (auto& st : s->staged) {
-    if (st.status != GDP_OK) {
-      server_fail(s, st);
-      continue;
+    for (size_t q = 0; q < st.r.size(); ++q) {
+      const gdp_server::Req& r = st.r[q];
+      const gdp_server::Region& g = st.g[q];
+      if (st.status != GDP_OK) {
+        server_fail(s, r, g, st.status);
+        continue;
+      }
+      const MeshInfo& Ms = st.S->hmi[q];
+      if (Ms.status != S_OK) {
+        server_fail(s, r, g, Ms.status);
+        continue;
+      }
+      const int md = s->free_ids.back();
+      s->free_ids.pop_back();
+      MeshInfo M = Ms;
+      M.tri_base = (int)g.t;
+      M.tri_cap = (int)g.nt;
+      M.vert_base = (int)g.v;
+      M.vert_cap = (int)g.nv;
+      M.seg_base = (int)g.s;
+      M.adj_base = (int)g.a;
+      M.pts_base = 0;
+      M.status = S_OK;
+      M.active = 1;
+      M.B2 = r.B * r.B;
+      M.B2f = (float)M.B2;
+      M.steiner = 0;
+      M.cand_cap = s->opts.cand_cap;
+      M.first_cand = M.last_cand = -1;
+      M.pending = 0;
+      h.hmi[md] = M;
+      for (int k = 0; k < Ms.n_seg; ++k) {
+        const int2 e = st.S->hseg[Ms.seg_base + k];
+        h.hseg[g.s + k] = make_int2(e.x - Ms.vert_base + (int)g.v, e.y - Ms.vert_base + (int)g.v);
+      }
+      CK(cudaMemcpyAsync(h.P.mi + md, &h.hmi[md], sizeof(MeshInfo), cudaMemcpyHostToDevice, h.stream));
+      LAUNCH(h, k_relocate, h.G, h.P, st.S->P, (int)q, md, (int)g.t, (int)g.v, (int)g.s, (int)g.a);
+      CK(cudaGetLastError());
+      s->live[md] = gdp_server::Live{r.ticket, g, r.t_submit, s->now_ms(), (int64_t)r.xy.size() / 2};
     }
-    const int md = s->free_ids.back();
-    s->free_ids.pop_back();
-    const MeshInfo& Ms = st.S->hmi[0];
-    MeshInfo M = Ms;
-    M.tri_base = (int)st.g.t;
-    M.tri_cap = (int)st.g.nt;
-    M.vert_base = (int)st.g.v;
-    M.vert_cap = (int)st.g.nv;
-    M.seg_base = (int)st.g.s;
-    M.adj_base = (int)st.g.a;
-    M.pts_base = 0;
-    M.status = S_OK;
-    M.active = 1;
-    M.B2 = st.r.B * st.r.B;
-    M.B2f = (float)M.B2;
-    M.steiner = 0;
-    M.cand_cap = s->opts.cand_cap;
-    M.first_cand = M.last_cand = -1;
-    M.pending = 0;
-    h.hmi[md] = M;
-    for (int k = 0; k < Ms.n_seg; ++k) {
-      const int2 q = st.S->hseg[k];
-      h.hseg[st.g.s + k] = make_int2(q.x + (int)st.g.v, q.y + (int)st.g.v);
-    }
-    CK(cudaMemcpyAsync(h.P.mi + md, &h.hmi[md], sizeof(MeshInfo), cudaMemcpyHostToDevice, h.stream));
-    LAUNCH(h, k_relocate, h.G, h.P, st.S->P, md, (int)st.g.t, (int)st.g.v, (int)st.g.s, (int)st.g.a);
-    CK(cudaGetLastError());
-    s->live[md] = gdp_server::Live{st.r.ticket, st.g, st.r.t_submit, s->now_ms(),
-                                   (int64_t)st.r.xy.size() / 2};
-    any = true;
   }
-  if (any || !s->staged.empty()) {
+  if (!s->staged.empty()) {
     // the staging pools are read by k_relocate: free them after it ran
     CK(cudaStreamSynchronize(h.stream));
     s->staged.clear();
@@ -440,8 +492,8 @@ int gdp_server_step(gdp_server* s, int32_t* n_waiting, int32_t* n_live, int32_t*
     });
     if (st != GDP_OK) return st;
   }
-  // overlaps the replay: staging builds on the side stream
-  server_stage(s, refine ? 2 : 8);
+  // overlaps the replay: one staging build on the side stream
+  server_stage(s, 256, 16ll << 20);
   if (refine) {
     if (h.sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
     if (h.hctrl->err) return h.hctrl->err;

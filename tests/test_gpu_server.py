@@ -93,3 +93,22 @@ def test_request_too_large_is_refused():
         srv.submit(p.xy, p.seg, SQ2)
     assert e.value.status == gdp.ERR_NOMEM
     srv.close()
+
+
+def test_invalid_request_fails_alone(oracle):
+    """A request with an invalid input (crossing segments) fails with
+    GDP_ERR_INPUT; requests staged with it are not affected."""
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    good = [W.square_pslg(1500, 30, 700 + i) for i in range(3)]
+    bad_xy = np.array([[0, 0], [1, 0], [1, 1], [0, 1], [0.2, 0.2], [0.8, 0.8], [0.2, 0.8], [0.8, 0.2]], float)
+    bad_seg = np.array([[0, 1], [1, 2], [2, 3], [3, 0], [4, 5], [6, 7]], np.int32)
+    srv = gdp.Server(1 << 20, 1 << 19, 1 << 12, 16)
+    tg = [srv.submit(good[0].xy, good[0].seg, SQ2), srv.submit(bad_xy, bad_seg, SQ2),
+          srv.submit(good[1].xy, good[1].seg, SQ2), srv.submit(good[2].xy, good[2].seg, 1.5)]
+    got = drain(srv)
+    assert got[tg[1]][0]["status"] == gdp.ERR_INPUT
+    for t, p, B in ((tg[0], good[0], SQ2), (tg[2], good[1], SQ2), (tg[3], good[2], 1.5)):
+        assert got[t][0]["status"] == 0
+        same(oracle, got[t][1], alone(gdp, p, B))
+    srv.close()
