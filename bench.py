@@ -409,6 +409,20 @@ def cpu_baseline(p, B, reps=3):
                       f"Steiner points each), {dt:.2f} s"}
 
 
+def replica_totals(ms, steiner, world, device):
+    """Replicas (one independent mesh per rank, no data-path collective): the
+    job's time is the slowest rank's, its work the sum over ranks."""
+    if world <= 1:
+        return float(ms), float(steiner)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(steiner)], dtype=torch.float64, device=device)
+    dist.all_reduce(s)
+    return float(t.item()), float(s.item())
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -502,16 +516,7 @@ def main():
                 grow[k] += stats[k]
             del m
         barrier()
-    tot_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        s = torch.tensor([float(steiner)], device=dev)
-        dist.all_reduce(s)
-        steiner_all = float(s.item())
-    else:
-        steiner_all = float(steiner)
+    tot_ms, steiner_all = replica_totals(sum(times), steiner, world, dev)
     value = steiner_all / (tot_ms / 1000.0)
 
     # end to end through the C ABI with pinned host buffers
