@@ -603,7 +603,8 @@ int PoolHost::launch_cdt_round(const Pool& Q, int stop_cons) {
   LAUNCH_C(*this, k_survive, Q);
   LAUNCH(*this, k_depend, G, Q);
   LAUNCH(*this, k_offsets, G, Q);
-  LAUNCH_C(*this, k_insert<1>, Q);
+  LAUNCH_B(*this, k_insert_w<1>, n_sm * 16, 128, Q);
+  LAUNCH_C(*this, k_insert_t<1>, Q);
   LAUNCH_C(*this, k_link<1>, Q);
   LAUNCH(*this, k_cdt_keep_count, G, Q);
   LAUNCH(*this, k_cdt_keep_write, G, Q);
@@ -1042,7 +1043,8 @@ int PoolHost::launch_iteration(int k) {
   LAUNCH_C(*this, k_survive, P);
   LAUNCH(*this, k_depend, G, P);
   LAUNCH(*this, k_offsets, G, P);
-  LAUNCH_C(*this, k_insert<0>, P);
+  LAUNCH_B(*this, k_insert_w<0>, n_sm * 16, 128, P);
+  LAUNCH_C(*this, k_insert_t<0>, P);
   LAUNCH_C(*this, k_link<0>, P);
   return cudaGetLastError() == cudaSuccess ? GDP_OK : GDP_ERR_CUDA;
 }
@@ -1404,7 +1406,8 @@ int gdp_mesh_split_subsegments(gdp_mesh* g, const double* abxy, int64_t n) {
     LAUNCH_C(h, k_survive, h.P);
     LAUNCH(h, k_depend, h.G, h.P);
     LAUNCH(h, k_offsets, h.G, h.P);
-    LAUNCH_C(h, k_insert<0>, h.P);
+    LAUNCH_B(h, k_insert_w<0>, h.n_sm * 16, 128, h.P);
+    LAUNCH_C(h, k_insert_t<0>, h.P);
     LAUNCH_C(h, k_link<0>, h.P);
     CK(cudaGetLastError());
     if (h.sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;

@@ -1039,8 +1039,9 @@ __device__ __forceinline__ bool replaced(const Pool& P, int ref, int n) {
 // (Sec. 5.2 insertion + housekeeping).  Cavity slots are reused first, extra
 // slots come from the mesh's bump region at stable prefix-sum offsets.
 template <int MODE>
-__global__ void __launch_bounds__(BS) k_insert(Pool P) {
+__global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
   const int n = P.ctrl->n_cand;
+  if (n <= WARP_GROW_MAX) return;   // k_insert_w's case
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int i = gt; i < n; i += gs) {
     const int m = P.c_mesh[i];
@@ -1101,6 +1102,137 @@ __global__ void __launch_bounds__(BS) k_insert(Pool P) {
       P.vtri[v] = s;
       P.vtri[vid] = s;
       ++j;
+    }
+  }
+}
+
+// The same, one warp per candidate up to WARP_GROW_MAX candidates: the
+// lanes take the cavity's boundary records (up to 64; larger spill-tier
+// cavities go through lane 0), find the fan neighbours by shuffles and write
+// the new triangles in parallel.  Identical output to k_insert_t.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_insert_w(Pool P) {
+  const unsigned FULL = 0xffffffffu;
+  const int n = P.ctrl->n_cand;
+  if (n > WARP_GROW_MAX) return;   // k_insert_t's case
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = gw; i < n; i += nw) {
+    const int m = P.c_mesh[i];
+    const MeshInfo& M = P.mi[m];
+    const int f = M.first_cand, l = M.last_cand;
+    int totE, totV;
+    mesh_totals(P, f, l, totE, totV);
+    const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
+    if (lane == 0) {
+      if (i == f) {
+        P.mi[m].ins_ok = ok ? 1 : 0;
+        if (!ok) P.mi[m].status = S_NOMEM;
+      }
+      // the element is re-checked whatever happens
+      if (MODE == 0) P.dirty[P.c_elem[i] >> 2] = 1;
+    }
+    if (!P.c_final[i] || !ok) continue;
+    const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
+    const int vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
+    const int4* bnd = bnd_of(P, i);
+    const int* cav = cav_of(P, i);
+    const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
+    const int2 sub = P.c_sub[i];
+    const bool is_mid = sub.x >= 0;
+    if (lane == 0) {
+      P.c_base[i] = base;
+      P.V[vid] = P.c_pt[i];
+      P.Vf[vid] = P.c_ptf[i];
+      P.vseg[vid] = P.c_vseg[i];
+      if (MODE == 1) P.loc[vid] = -1;
+    }
+    if (nb > 64) {   // a spill-tier cavity: one lane, the sequential order
+      if (lane == 0) {
+        int j = 0;
+        for (int r = 0; r < nb; ++r) {
+          const int4 rec = bnd[r];
+          if (is_split_edge(rec, sub)) continue;
+          const int s = j < nc ? cav[j] : base + (j - nc);
+          const int u = rec.x, v = rec.y;
+          int cb = rec.w < 0 ? 1 : 0;
+          if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
+          if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
+          int n1 = -1, n2 = -1, jj = 0;
+          for (int r2 = 0; r2 < nb; ++r2) {
+            const int4 q = bnd[r2];
+            if (is_split_edge(q, sub)) continue;
+            const int s2 = jj < nc ? cav[jj] : base + (jj - nc);
+            if (q.x == v) n1 = (s2 << 2) | 2;
+            if (q.y == u) n2 = (s2 << 2) | 1;
+            ++jj;
+          }
+          int n0 = rec.z;
+          if (n0 >= 0) {
+            if (replaced(P, n0, n)) n0 = -1;
+            else *comp_ptr(&P.N[n0 >> 2], n0 & 3) = s << 2;
+          }
+          P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
+          P.N[s] = make_int4(n0, n1, n2, 0);
+          P.newref[rec.w & 0x7fffffff] = s << 2;
+          P.dirty[s] = 1;
+          P.vtri[u] = s;
+          P.vtri[v] = s;
+          P.vtri[vid] = s;
+          ++j;
+        }
+      }
+      __syncwarp();
+      continue;
+    }
+    // records lane and lane + 32; j = rank among the records that are not the split edge
+    int4 rec[2];
+    bool keep[2];
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      rec[h] = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
+      keep[h] = r < nb && !is_split_edge(rec[h], sub);
+    }
+    const unsigned k0 = __ballot_sync(FULL, keep[0]), k1 = __ballot_sync(FULL, keep[1]);
+    int slot[2];
+    for (int h = 0; h < 2; ++h) {
+      const int j = h == 0 ? __popc(k0 & lt_mask) : __popc(k0) + __popc(k1 & lt_mask);
+      slot[h] = j < nc ? cav[j] : base + (j - nc);
+    }
+    // fan neighbours: the record starting where mine ends (edge 2), the one ending where mine starts (edge 1)
+    int n1[2] = {-1, -1}, n2[2] = {-1, -1};
+    for (int q = 0; q < nb; ++q) {
+      const int h = q >> 5, src = q & 31;
+      const int qx = __shfl_sync(FULL, h ? rec[1].x : rec[0].x, src);
+      const int qy = __shfl_sync(FULL, h ? rec[1].y : rec[0].y, src);
+      const int qs = __shfl_sync(FULL, h ? slot[1] : slot[0], src);
+      const bool qk = ((h ? k1 : k0) >> src) & 1;
+      if (!qk) continue;
+      for (int g = 0; g < 2; ++g) {
+        if (qx == rec[g].y) n1[g] = (qs << 2) | 2;
+        if (qy == rec[g].x) n2[g] = (qs << 2) | 1;
+      }
+    }
+    for (int h = 0; h < 2; ++h) {
+      if (!keep[h]) continue;
+      const int s = slot[h];
+      const int u = rec[h].x, v = rec[h].y;
+      int cb = rec[h].w < 0 ? 1 : 0;
+      if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
+      if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
+      int n0 = rec[h].z;
+      if (n0 >= 0) {
+        if (replaced(P, n0, n)) n0 = -1;   // linked by k_link
+        else *comp_ptr(&P.N[n0 >> 2], n0 & 3) = s << 2;
+      }
+      P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
+      P.N[s] = make_int4(n0, n1[h], n2[h], 0);
+      P.newref[rec[h].w & 0x7fffffff] = s << 2;
+      P.dirty[s] = 1;
+      P.vtri[u] = s;
+      P.vtri[v] = s;
+      P.vtri[vid] = s;
     }
   }
 }
