@@ -1148,96 +1148,49 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   return status;
 }
 
-// Export ids: input points 0..n_in-1, the three enclosing vertices dropped,
-// Steiner points after.  Subsegments are the subsegment-flagged edges.
+// Export ids: input points 0..n_in-1, the auxiliary vertices dropped,
+// Steiner points after.  Triangles and subsegments are gathered on the
+// device (k_export_count / k_export_write) and copied out once.
 int PoolHost::export_mesh(int m, double* xy, int64_t cap_pts, int32_t* tri, int64_t cap_tri,
                           int32_t* sub, int64_t cap_seg, int64_t* n_pts, int64_t* n_tri,
                           int64_t* n_seg) {
   if (m < 0 || m >= n_mesh) return GDP_ERR_INPUT;
   if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
   const MeshInfo& M = hmi[m];
-  std::vector<int4> T(M.tri_count);
-  std::vector<double2> V(M.vert_count);
-  std::vector<int32_t> vs(M.vert_count);
-  if (M.tri_count)
-    CK(cudaMemcpyAsync(T.data(), P.T + M.tri_base, sizeof(int4) * M.tri_count, cudaMemcpyDeviceToHost, stream));
-  CK(cudaMemcpyAsync(V.data(), P.V + M.vert_base, sizeof(double2) * M.vert_count, cudaMemcpyDeviceToHost, stream));
-  CK(cudaMemcpyAsync(vs.data(), P.vseg + M.vert_base, sizeof(int32_t) * M.vert_count, cudaMemcpyDeviceToHost, stream));
+  LAUNCH(*this, k_export_count, G, P, m);
+  std::vector<int> blk(2 * G);
+  CK(cudaMemcpyAsync(blk.data(), P.blk, sizeof(int) * 2 * G, cudaMemcpyDeviceToHost, stream));
   CK(cudaStreamSynchronize(stream));
-  const int sv = M.n_in;   // local id of the first auxiliary vertex
-  auto ex = [&](int g) { int l = g - M.vert_base; return l < sv ? l : l - N_AUX; };
-  const long long npts = M.vert_count - N_AUX;
   long long ntri = 0, nsub = 0;
-  for (const int4& t : T) {
-    if (t.w < 0 || (t.w & INFO_DEAD)) continue;
-    ++ntri;
-    for (int e = 0; e < 3; ++e) {
-      if (!((t.w >> e) & 1)) continue;
-      const int u = (e == 0) ? t.y : (e == 1 ? t.z : t.x);
-      const int v = (e == 0) ? t.z : (e == 1 ? t.x : t.y);
-      (void)v;
-      nsub += 1;
-      (void)u;
-    }
+  for (int b = 0; b < G; ++b) {
+    ntri += blk[b];
+    nsub += blk[G + b];
   }
-  // every interior subsegment is seen from both sides, hull ones once: count properly
-  std::unordered_map<unsigned long long, int> seen;
-  seen.reserve((size_t)nsub * 2 + 16);
-  std::vector<int32_t> subs;
-  subs.reserve((size_t)nsub * 3);
-  // per input vertex: incident segments (for unsplit segments)
-  std::unordered_map<unsigned long long, int> segid;
-  for (int k = 0; k < M.n_seg; ++k) {
-    const int2 s = hseg[M.seg_base + k];
-    const unsigned long long a = (unsigned)std::min(s.x, s.y), b = (unsigned)std::max(s.x, s.y);
-    segid[(a << 32) | b] = M.seg_base + k;
-  }
-  for (const int4& t : T) {
-    if (t.w < 0 || (t.w & INFO_DEAD)) continue;
-    const int vv[3] = {t.x, t.y, t.z};
-    for (int e = 0; e < 3; ++e) {
-      if (!((t.w >> e) & 1)) continue;
-      const int u = vv[(e + 1) % 3], v = vv[(e + 2) % 3];
-      const unsigned long long a = (unsigned)std::min(u, v), b = (unsigned)std::max(u, v);
-      const unsigned long long key = (a << 32) | b;
-      if (seen.count(key)) continue;
-      seen[key] = 1;
-      int s = vs[u - M.vert_base];
-      if (s < 0) s = vs[v - M.vert_base];
-      if (s < 0) {
-        auto it = segid.find(key);
-        s = it == segid.end() ? -1 : it->second;
-      }
-      subs.push_back(ex(u));
-      subs.push_back(ex(v));
-      subs.push_back(s < 0 ? -1 : s - M.seg_base);
-    }
-  }
-  nsub = (long long)subs.size() / 3;
+  const long long npts = M.vert_count - N_AUX;
   if (n_pts) *n_pts = npts;
   if (n_tri) *n_tri = ntri;
   if (n_seg) *n_seg = nsub;
   if ((xy && cap_pts < npts) || (tri && cap_tri < ntri) || (sub && cap_seg < nsub)) return GDP_ERR_INPUT;
   if (xy) {
-    long long k = 0;
-    for (int l = 0; l < M.vert_count; ++l) {
-      if (l >= sv && l < sv + N_AUX) continue;
-      xy[2 * k] = V[l].x;
-      xy[2 * k + 1] = V[l].y;
-      ++k;
-    }
+    CK(cudaMemcpyAsync(xy, P.V + M.vert_base, sizeof(double2) * M.n_in, cudaMemcpyDeviceToHost, stream));
+    const long long rest = M.vert_count - M.n_in - N_AUX;
+    if (rest > 0)
+      CK(cudaMemcpyAsync(xy + 2 * (size_t)M.n_in, P.V + M.vert_base + M.n_in + N_AUX, sizeof(double2) * rest,
+                         cudaMemcpyDeviceToHost, stream));
   }
-  if (tri) {
-    long long k = 0;
-    for (const int4& t : T) {
-      if (t.w < 0 || (t.w & INFO_DEAD)) continue;
-      tri[3 * k] = ex(t.x);
-      tri[3 * k + 1] = ex(t.y);
-      tri[3 * k + 2] = ex(t.z);
-      ++k;
-    }
+  if (tri || sub) {
+    int *dt = nullptr, *ds = nullptr;
+    int st;
+    if ((st = alloc(&dt, 3 * (size_t)std::max(ntri, 1LL))) != GDP_OK) return st;
+    if ((st = alloc(&ds, 3 * (size_t)std::max(nsub, 1LL))) != GDP_OK) return st;
+    LAUNCH(*this, k_export_write, G, P, m, dt, ds);
+    CK(cudaGetLastError());
+    if (tri && ntri) CK(cudaMemcpyAsync(tri, dt, sizeof(int) * 3 * ntri, cudaMemcpyDeviceToHost, stream));
+    if (sub && nsub) CK(cudaMemcpyAsync(sub, ds, sizeof(int) * 3 * nsub, cudaMemcpyDeviceToHost, stream));
+    release(dt);
+    release(ds);
   }
-  if (sub) std::memcpy(sub, subs.data(), sizeof(int32_t) * subs.size());
+  CK(cudaStreamSynchronize(stream));
   return GDP_OK;
 }
 

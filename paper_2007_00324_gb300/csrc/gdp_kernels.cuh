@@ -1279,6 +1279,93 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
   }
 }
 
+// ---------------------------------------------------------------- export
+// Mesh m in export numbering (input points first, the auxiliary vertices
+// dropped, Steiner points after): its live triangles in slot order and its
+// subsegments, each emitted once -- from the triangle with the smaller slot,
+// or the only one on the hull -- with the input segment it lies on.
+__device__ __forceinline__ int ex_id(const MeshInfo& M, int g) {
+  const int l = g - M.vert_base;
+  return l < M.n_in ? l : l - N_AUX;
+}
+
+__device__ __forceinline__ bool ex_sub(const Pool& P, int t, const int4& T4, int e) {
+  if (!((T4.w >> e) & 1)) return false;
+  const int nb = comp(P.N[t], e);
+  return nb < 0 || (nb >> 2) > t;
+}
+
+__global__ void __launch_bounds__(BS) k_export_count(Pool P, int m) {
+  __shared__ int sm[33];
+  const MeshInfo& M = P.mi[m];
+  const Chunk ch = chunk_of(M.tri_count);
+  int nt = 0, ns = 0;
+  for (int k = ch.b0 + threadIdx.x; k < ch.b1; k += BS) {
+    const int t = M.tri_base + k;
+    const int4 T4 = P.T[t];
+    if (T4.w < 0 || (T4.w & INFO_DEAD)) continue;
+    ++nt;
+    for (int e = 0; e < 3; ++e) ns += ex_sub(P, t, T4, e) ? 1 : 0;
+  }
+  nt = block_sum(nt, sm);
+  ns = block_sum(ns, sm);
+  if (threadIdx.x == 0) {
+    P.blk[blockIdx.x] = nt;
+    P.blk[gridDim.x + blockIdx.x] = ns;
+  }
+}
+
+__global__ void __launch_bounds__(BS) k_export_write(Pool P, int m, int* tri_out, int* sub_out) {
+  __shared__ int sm[33];
+  const MeshInfo& M = P.mi[m];
+  const Chunk ch = chunk_of(M.tri_count);
+  int ot = block_prefix(P.blk, blockIdx.x, sm);
+  int os = block_prefix(P.blk + gridDim.x, blockIdx.x, sm);
+  for (int base = ch.b0; base < ch.b1; base += BS) {
+    const int k = base + threadIdx.x;
+    int4 T4 = make_int4(-1, -1, -1, -1);
+    const int t = M.tri_base + k;
+    bool live = false;
+    int es = 0;
+    if (k < ch.b1) {
+      T4 = P.T[t];
+      live = !(T4.w < 0 || (T4.w & INFO_DEAD));
+      if (live)
+        for (int e = 0; e < 3; ++e) es += ex_sub(P, t, T4, e) ? 1 : 0;
+    }
+    int tt, ts;
+    const int rt = block_excl_scan(live ? 1 : 0, sm, tt);
+    const int rs = block_excl_scan(es, sm, ts);
+    if (live) {
+      int* o = tri_out + 3 * (size_t)(ot + rt);
+      o[0] = ex_id(M, T4.x);
+      o[1] = ex_id(M, T4.y);
+      o[2] = ex_id(M, T4.z);
+      int q = os + rs;
+      for (int e = 0; e < 3; ++e) {
+        if (!ex_sub(P, t, T4, e)) continue;
+        const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
+        int sg = P.vseg[u];
+        if (sg < 0) sg = P.vseg[v];
+        if (sg < 0) {   // both ends are input points: the segment joining them
+          const int lu = u - M.vert_base;
+          for (int a = P.adj_off[M.adj_base + lu]; a < P.adj_off[M.adj_base + lu + 1] && sg < 0; ++a) {
+            const int g = P.adj[a];
+            const int2 s2 = P.seg[g];
+            if ((s2.x == u && s2.y == v) || (s2.x == v && s2.y == u)) sg = g;
+          }
+        }
+        int* w = sub_out + 3 * (size_t)q++;
+        w[0] = ex_id(M, u);
+        w[1] = ex_id(M, v);
+        w[2] = sg < 0 ? -1 : sg - M.seg_base;
+      }
+    }
+    ot += tt;
+    os += ts;
+  }
+}
+
 // ---------------------------------------------------------------- consistency (test hook)
 // counts: [0] links that are not mutual, [1] links whose shared edge does not
 // match, [2] subsegment bits that differ across an edge, [3] triangles not CCW
