@@ -79,10 +79,12 @@ typedef struct {
     int64_t cavity_tris;  /* triangles in those cavities */
     int64_t cavity_edges; /* boundary edges of those cavities */
     int64_t walk_steps;   /* point-location steps of circumcentres */
-    /* with GDP_REFINE_TIME_GROW: device time of every k_grow launch of the
-     * refinement, from CUDA events recorded around it inside the graph    */
+    /* with GDP_REFINE_TIME_GROW: the cavity-growth launches of the first
+     * iteration of every graph replay are bracketed by CUDA events inside
+     * the graph; their device time, their number and their work:          */
     double grow_ms;
     int64_t grow_launches;
+    int64_t timed_grown, timed_cavity_tris, timed_cavity_edges, timed_walk_steps;
 } gdp_stats;
 
 /* gdp_refine_opts.flags */

@@ -159,8 +159,8 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
 // candidate cavities: own slots, then the two spill tiers
 #define LAUNCH_GROW(h, MODE, P)                                      \
   do {                                                               \
-    LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P);              \
-    LAUNCH_C(h, k_grow_t<MODE>, P);                                  \
+    LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P, 0);           \
+    LAUNCH_C(h, k_grow_t<MODE>, P, 0);                               \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_A / 32, 32, P, 0);           \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_B, 1, P, 1);                 \
   } while (0)
@@ -456,7 +456,7 @@ struct PoolHost {
     bs_cand = (b == 32 || b == 128 || b == 256) ? b : 64;
     Gc = n_sm * (1024 / bs_cand);
   }
-  // GDP_REFINE_TIME_GROW: an event pair around k_grow_w<0> per iteration slot of the graph
+  // GDP_REFINE_TIME_GROW: an event pair around the first growth launch of each replay
   bool time_grow = false;
   std::vector<cudaEvent_t> tg;
   int add_grow_times(int iters);
@@ -503,6 +503,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   P.n_slots = (int)tb;
   P.n_verts = (int)vb;
   P.cap_cand = (int)std::min<long long>(std::max<long long>(tb / 4, 65536), 1 << 23);
+  P.warp_max = (int)env_double("GDP_WARP_GROW_MAX", WARP_GROW_MAX);
   int st;
 #define AL(ptr, n, fill) \
   if ((st = alloc(&(ptr), (size_t)(n), fill)) != GDP_OK) return st;
@@ -1033,11 +1034,14 @@ int PoolHost::launch_iteration(int k) {
     LAUNCH(*this, k_cap_count, G, P);
   }
   LAUNCH(*this, k_scan_write, G, P);
+  // the first iteration of each replay is timed (events in the graph stall
+  // the pipeline, so not every one): its growth work is counted apart
   const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-  if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k], stream, rec));
-  LAUNCH_B(*this, k_grow_w<0>, n_sm * 16, 128, P);
-  LAUNCH_C(*this, k_grow_t<0>, P);
-  if (time_grow) CK(cudaEventRecordWithFlags(tg[2 * k + 1], stream, rec));
+  const int timed = (time_grow && k == 0) ? 1 : 0;
+  if (timed) CK(cudaEventRecordWithFlags(tg[0], stream, rec));
+  LAUNCH_B(*this, k_grow_w<0>, n_sm * 16, 128, P, timed);
+  LAUNCH_C(*this, k_grow_t<0>, P, timed);
+  if (timed) CK(cudaEventRecordWithFlags(tg[1], stream, rec));
   LAUNCH_B(*this, k_grow_big<0>, LANES_A / 32, 32, P, 0);
   LAUNCH_B(*this, k_grow_big<0>, LANES_B, 1, P, 1);
   LAUNCH_C(*this, k_survive, P);
@@ -1049,15 +1053,13 @@ int PoolHost::launch_iteration(int k) {
   return cudaGetLastError() == cudaSuccess ? GDP_OK : GDP_ERR_CUDA;
 }
 
-// after a synchronised replay of `iters` iterations: accumulate k_grow times
+// after a synchronised replay: the timed growth launch's device time
 int PoolHost::add_grow_times(int iters) {
-  if (!time_grow) return GDP_OK;
-  for (int k = 0; k < iters; ++k) {
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, tg[2 * k], tg[2 * k + 1]));
-    stats.grow_ms += ms;
-    stats.grow_launches += 1;
-  }
+  if (!time_grow || iters <= 0) return GDP_OK;
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, tg[0], tg[1]));
+  stats.grow_ms += ms;
+  stats.grow_launches += 1;
   return GDP_OK;
 }
 
@@ -1089,8 +1091,7 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   stats.grow_ms = 0;
   stats.grow_launches = 0;
   if (time_grow) {
-    const size_t need = 2 * (size_t)std::max(giters, 1);
-    while (tg.size() < need) {
+    while (tg.size() < 2) {
       cudaEvent_t e;
       CK(cudaEventCreate(&e));
       tg.push_back(e);
@@ -1137,6 +1138,10 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   stats.cavity_tris = (int64_t)hctrl->sum_cav;
   stats.cavity_edges = (int64_t)hctrl->sum_bnd;
   stats.walk_steps = (int64_t)hctrl->sum_walk;
+  stats.timed_grown = (int64_t)hctrl->t_grown;
+  stats.timed_cavity_tris = (int64_t)hctrl->t_cav;
+  stats.timed_cavity_edges = (int64_t)hctrl->t_bnd;
+  stats.timed_walk_steps = (int64_t)hctrl->t_walk;
   long long st = 0, nt = 0;
   for (auto& M : hmi) {
     st += M.steiner;

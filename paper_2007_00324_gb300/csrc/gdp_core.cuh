@@ -83,6 +83,8 @@ struct Ctrl {
   unsigned long long tot_cand, tot_ins, iters, n_ins, n_surv;
   // refinement work counters (algorithmic bytes of the cavity kernels)
   unsigned long long n_grown, sum_cav, sum_bnd, sum_walk;
+  // the same for the launches timed with CUDA events (GDP_REFINE_TIME_GROW)
+  unsigned long long t_grown, t_cav, t_bnd, t_walk;
 };
 
 struct Pool {
@@ -108,6 +110,7 @@ struct Pool {
   int32_t* adj;
   // candidates
   int32_t cap_cand;
+  int32_t warp_max;      // up to this many candidates, one warp grows each cavity
   int32_t* c_elem;
   int32_t* c_loc;
   int32_t* c_vid;

@@ -571,7 +571,7 @@ struct GrowAcc {
   unsigned long long grown = 0, cav = 0, bnd = 0, walk = 0;
 };
 
-__device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a) {
+__device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a, int timed = 0) {
   for (int o = 16; o; o >>= 1) {
     a.grown += __shfl_xor_sync(0xffffffffu, a.grown, o);
     a.cav += __shfl_xor_sync(0xffffffffu, a.cav, o);
@@ -583,6 +583,12 @@ __device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a) {
     atomicAdd(&P.ctrl->sum_cav, a.cav);
     atomicAdd(&P.ctrl->sum_bnd, a.bnd);
     atomicAdd(&P.ctrl->sum_walk, a.walk);
+    if (timed) {
+      atomicAdd(&P.ctrl->t_grown, a.grown);
+      atomicAdd(&P.ctrl->t_cav, a.cav);
+      atomicAdd(&P.ctrl->t_bnd, a.bnd);
+      atomicAdd(&P.ctrl->t_walk, a.walk);
+    }
   }
 }
 
@@ -831,15 +837,16 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
 }
 
 // Cavity growth of the candidates in their own slots of CMAX triangles
-// (larger cavities go to the spill tiers).  Up to WARP_GROW_MAX candidates
+// (larger cavities go to the spill tiers).  Up to P.warp_max candidates
 // -- the usual, latency-bound case -- one warp grows each cavity (wgrow,
 // k_grow_w); beyond that the launch is throughput-bound and one thread per
 // candidate does less total work (grow, k_grow_t).  Both give the same
 // cavities.
-constexpr int WARP_GROW_MAX = 32768;
+constexpr int WARP_GROW_MAX = 32768;   // default of Pool::warp_max
 
+// timed: this launch is bracketed by CUDA events; its work is also counted apart
 template <int MODE>
-__global__ void __maxnreg__(128) k_grow_w(Pool P) {
+__global__ void __maxnreg__(128) k_grow_w(Pool P, int timed) {
   __shared__ int wcs[4][32];
   __shared__ CandSetup ws[4];
   const unsigned FULL = 0xffffffffu;
@@ -847,7 +854,7 @@ __global__ void __maxnreg__(128) k_grow_w(Pool P) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n = P.ctrl->n_cand;
   int* wc = wcs[wib];
-  if (n > WARP_GROW_MAX) return;   // k_grow_t's case
+  if (n > P.warp_max) return;   // k_grow_t's case
   GrowAcc acc;
   for (int i = gw; i < n; i += nw) {
     int ok = 1;
@@ -885,17 +892,17 @@ __global__ void __maxnreg__(128) k_grow_w(Pool P) {
     if (lane == 0) cand_record(P, i, s, nc, nb, acc);
     __syncwarp();
   }
-  if (MODE == 0) acc_flush(P, acc);
+  if (MODE == 0) acc_flush(P, acc, timed);
 }
 
 
 // the same, one thread per candidate, when there are more than
-// WARP_GROW_MAX candidates (a separate kernel keeps each version's register
+// P.warp_max candidates (a separate kernel keeps each version's register
 // allocation to itself)
 template <int MODE>
-__global__ void __launch_bounds__(BS) k_grow_t(Pool P) {
+__global__ void __launch_bounds__(BS) k_grow_t(Pool P, int timed) {
   const int n = P.ctrl->n_cand;
-  if (n <= WARP_GROW_MAX) return;   // k_grow_w's case
+  if (n <= P.warp_max) return;   // k_grow_w's case
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   GrowAcc acc;
   for (int i = gt; i < n; i += gs) {
@@ -903,7 +910,7 @@ __global__ void __launch_bounds__(BS) k_grow_t(Pool P) {
     const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
     if (grow_cand<MODE>(P, i, B, acc) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
   }
-  if (MODE == 0) acc_flush(P, acc);   // every thread of the block reaches this
+  if (MODE == 0) acc_flush(P, acc, timed);   // every thread of the block reaches this
 }
 
 // Cavities that outgrew their slot (tier 0) or their tier-A lane (tier 1):
@@ -1041,7 +1048,7 @@ __device__ __forceinline__ bool replaced(const Pool& P, int ref, int n) {
 template <int MODE>
 __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
   const int n = P.ctrl->n_cand;
-  if (n <= WARP_GROW_MAX) return;   // k_insert_w's case
+  if (n <= P.warp_max) return;   // k_insert_w's case
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int i = gt; i < n; i += gs) {
     const int m = P.c_mesh[i];
@@ -1106,7 +1113,7 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
   }
 }
 
-// The same, one warp per candidate up to WARP_GROW_MAX candidates: the
+// The same, one warp per candidate up to P.warp_max candidates: the
 // lanes take the cavity's boundary records (up to 64; larger spill-tier
 // cavities go through lane 0), find the fan neighbours by shuffles and write
 // the new triangles in parallel.  Identical output to k_insert_t.
@@ -1114,7 +1121,7 @@ template <int MODE>
 __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
   const unsigned FULL = 0xffffffffu;
   const int n = P.ctrl->n_cand;
-  if (n > WARP_GROW_MAX) return;   // k_insert_t's case
+  if (n > P.warp_max) return;   // k_insert_t's case
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;

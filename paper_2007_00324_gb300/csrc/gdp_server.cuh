@@ -214,6 +214,7 @@ static int server_setup(gdp_server* s, long long tb, long long vb, long long sb,
   h.P.n_slots = (int)tb;
   h.P.n_verts = (int)vb;
   h.P.cap_cand = (int)std::min<long long>(std::max<long long>(tb / 4, 65536), 1 << 23);
+  h.P.warp_max = (int)env_double("GDP_WARP_GROW_MAX", WARP_GROW_MAX);
   const long long ab = vb + nm;   // adjacency rows: at most one per vertex plus one per mesh
   int st;
 #define AL(ptr, n, fill) \

@@ -39,7 +39,9 @@ class Stats(C.Structure):
                 ("inserted", C.c_int64), ("cdt_rounds", C.c_int64), ("refine_ms", C.c_double),
                 ("cdt_ms", C.c_double), ("launches", C.c_int64), ("grown", C.c_int64),
                 ("cavity_tris", C.c_int64), ("cavity_edges", C.c_int64), ("walk_steps", C.c_int64),
-                ("grow_ms", C.c_double), ("grow_launches", C.c_int64)]
+                ("grow_ms", C.c_double), ("grow_launches", C.c_int64), ("timed_grown", C.c_int64),
+                ("timed_cavity_tris", C.c_int64), ("timed_cavity_edges", C.c_int64),
+                ("timed_walk_steps", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
