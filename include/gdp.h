@@ -52,7 +52,8 @@ typedef struct gdp_mesh gdp_mesh;
 /* Refinement options.  Zero-initialised fields take the defaults. */
 typedef struct {
     double B;             /* radius-edge bound (> 0.70711; sqrt 2 default when 0) */
-    double max_len;       /* reserved: edge-length bound, <= 0 or INF = off */
+    double max_len;       /* edge-length bound l (Sec. 4.1): a triangle whose longest
+                             edge exceeds l is refined as well; <= 0 or INF = off */
     int32_t max_iter;     /* parallel iterations (Algorithm 1 loop), 0 = 100000 */
     int32_t cand_cap;     /* candidates per iteration and mesh; 0 = no cap (Rule 2) */
     int32_t graph_iters;  /* iterations per CUDA-graph replay; 0 = 8, < 0 = no graph */

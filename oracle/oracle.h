@@ -47,6 +47,8 @@ int  or_lex_less(double ax, double ay, double bx, double by);
 /* ---------------- FP64 geometry with a fixed evaluation order (pred.c) ---- */
 int    or_is_bad(double ax, double ay, double bx, double by, double cx, double cy,
                  double B2);
+int    or_is_long(double ax, double ay, double bx, double by, double cx, double cy,
+                  double L2);
 double or_ratio_key(double ax, double ay, double bx, double by, double cx, double cy);
 void   or_circumcenter(double ax, double ay, double bx, double by, double cx, double cy,
                        double* ox, double* oy);
@@ -63,6 +65,10 @@ or_mesh* or_cdt_create(const double* xy, int64_t n, const int32_t* seg, int64_t 
 void     or_destroy(or_mesh*);
 /* order: 0 = worst ratio first, 1 = FIFO, 2 = largest area first */
 int      or_refine(or_mesh*, double B, int64_t max_steiner, int order);
+/* the same with the edge-length bound l of Sec. 4.1 as well (l <= 0: none):
+ * a triangle whose longest edge exceeds l is refined like a bad one (the
+ * small-angle exemption covers only the radius-edge test) */
+int      or_refine_len(or_mesh*, double B, double l, int64_t max_steiner, int order);
 /* insert free points (strictly inside the domain, not on a subsegment) */
 int      or_insert_points(or_mesh*, const double* xy, int64_t n);
 /* split the subsegments given by endpoint coordinates (ax,ay,bx,by) at midpoints */

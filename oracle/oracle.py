@@ -82,6 +82,10 @@ def lib():
             L.or_destroy.argtypes = [vp]
             L.or_refine.argtypes = [vp, d, i64, C.c_int]
             L.or_refine.restype = C.c_int
+            L.or_refine_len.argtypes = [vp, d, d, i64, C.c_int]
+            L.or_refine_len.restype = C.c_int
+            L.or_is_long.argtypes = [d] * 7
+            L.or_is_long.restype = C.c_int
             L.or_insert_points.argtypes = [vp, vp, i64]
             L.or_insert_points.restype = C.c_int
             L.or_split_subsegments.argtypes = [vp, vp, i64]
@@ -167,6 +171,10 @@ class Mesh:
     def refine(self, B: float, max_steiner: int = 1 << 40, order: int = 0) -> int:
         return lib().or_refine(self._h, B, max_steiner, order)
 
+    def refine_len(self, B: float, l: float, max_steiner: int = 1 << 40, order: int = 0) -> int:
+        """refinement with the edge-length bound l as well (l <= 0: none)"""
+        return lib().or_refine_len(self._h, B, l, max_steiner, order)
+
     def insert_points(self, xy) -> int:
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
         return lib().or_insert_points(self._h, _p(xy), len(xy))
@@ -187,6 +195,10 @@ class Mesh:
         sub = np.zeros((ns, 3), np.int32)
         L.or_export(self._h, _p(xy), _p(tri), _p(sub))
         return xy, tri, sub
+
+
+def is_long(a, b, c, L2):
+    return lib().or_is_long(a[0], a[1], b[0], b[1], c[0], c[1], L2)
 
 
 def check(xy, tri, sub, seg_in, n_in, B=None, brute=False) -> dict:

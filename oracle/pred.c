@@ -230,6 +230,18 @@ int or_is_bad(double ax, double ay, double bx, double by, double cx, double cy, 
     return lhs > rhs;
 }
 
+/* Edge-length criterion (Sec. 4.1: besides the angle bound, an edge length
+ * bound l): the longest edge is longer than l, i.e. max(|ab|^2, |bc|^2,
+ * |ca|^2) > L2 = l^2 with the squared lengths of the quality test above. */
+int or_is_long(double ax, double ay, double bx, double by, double cx, double cy, double L2) {
+    tri_terms t;
+    terms(ax, ay, bx, by, cx, cy, &t);
+    double lmax = t.la;
+    if (t.lb > lmax) lmax = t.lb;
+    if (t.lc > lmax) lmax = t.lc;
+    return lmax > L2;
+}
+
 /* (R / l_min)^2 * 4, used only to order the oracle's queue of bad triangles */
 double or_ratio_key(double ax, double ay, double bx, double by, double cx, double cy) {
     tri_terms t;

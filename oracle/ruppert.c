@@ -185,6 +185,7 @@ typedef struct {
     or_mesh* M;
     seg_adj A;
     double B2;
+    double L2;   /* edge-length bound squared, 0 = none */
     int order;
     int64_t seq;
     heap H;
@@ -198,8 +199,11 @@ static void consider_tri(rstate* S, int64_t t) {
     const int32_t* v = M->tv + 3 * t;
     double ax = M->x[v[0]], ay = M->y[v[0]], bx = M->x[v[1]], by = M->y[v[1]];
     double cx = M->x[v[2]], cy = M->y[v[2]];
-    if (!or_is_bad(ax, ay, bx, by, cx, cy, S->B2)) return;
-    if (exempt(M, &S->A, t)) return;
+    const int lng = S->L2 > 0 && or_is_long(ax, ay, bx, by, cx, cy, S->L2);
+    if (!lng) {
+        if (!or_is_bad(ax, ay, bx, by, cx, cy, S->B2)) return;
+        if (exempt(M, &S->A, t)) return;
+    }
     hent e;
     e.t = t;
     e.v[0] = v[0];
@@ -256,10 +260,15 @@ static int split_sub(rstate* S, int64_t u, int64_t v) {
 }
 
 int or_refine(or_mesh* M, double B, int64_t max_steiner, int order) {
+    return or_refine_len(M, B, 0.0, max_steiner, order);
+}
+
+int or_refine_len(or_mesh* M, double B, double l, int64_t max_steiner, int order) {
     rstate S;
     memset(&S, 0, sizeof(S));
     S.M = M;
     S.B2 = B * B;
+    S.L2 = l > 0 ? l * l : 0.0;
     S.order = order;
     build_adj(M, &S.A);
     int status = OR_OK;

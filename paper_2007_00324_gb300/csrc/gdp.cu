@@ -1076,6 +1076,7 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
     if (!(b > 0.7072)) return GDP_ERR_INPUT;
     M.B2 = b * b;
     M.B2f = (float)M.B2;
+    M.L2 = (d.max_len > 0 && std::isfinite(d.max_len)) ? d.max_len * d.max_len : 0.0;
     M.active = M.status == S_OK ? 1 : 0;
     M.steiner = 0;
     M.cand_cap = d.cand_cap;

@@ -59,6 +59,7 @@ struct MeshInfo {
   int32_t pts_base;      // offset of this mesh's points in the construction list
   int32_t tmp;           // scratch for per-mesh reductions
   double B2;
+  double L2;             // edge-length bound squared (Sec. 4.1), 0 = none
   double2 lo, hi;        // bounding box of the input points
   double2 org;           // origin of the float coordinate copies (box centre)
   float B2f;             // B^2 rounded to float (FP32 pre-checks)

@@ -243,6 +243,10 @@ __device__ int eval_tri(const Pool& P, int t) {
     }
     if (best >= 0) return 1 + best;
   }
+  if (M.L2 > 0) {   // edge-length bound: a longest edge above l is refined, exempt or not
+    const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
+    if (fmax(tt.la, fmax(tt.lb, tt.lc)) > M.L2) return 4;
+  }
   const int q = bad_f32(P.Vf[T4.x], P.Vf[T4.y], P.Vf[T4.z], M.B2f);
   const bool bad = q > 0 || (q == 0 && is_bad(tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]), M.B2));
   if (bad && !exempt(P, M, T4)) return 4;

@@ -365,6 +365,7 @@ static int server_admit(gdp_server* s) {
       M.active = 1;
       M.B2 = r.B * r.B;
       M.B2f = (float)M.B2;
+      M.L2 = (s->opts.max_len > 0 && std::isfinite(s->opts.max_len)) ? s->opts.max_len * s->opts.max_len : 0.0;
       M.steiner = 0;
       M.cand_cap = s->opts.cand_cap;
       M.first_cand = M.last_cand = -1;

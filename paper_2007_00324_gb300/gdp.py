@@ -122,8 +122,8 @@ def _p(a):
 REFINE_TIME_GROW = 1   # gdp_refine_opts.flags: time every k_grow launch with CUDA events
 
 
-def _opts(B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, flags=0, cand_block=0):
-    return RefineOpts(B=B, max_len=0.0, max_iter=max_iter, cand_cap=cand_cap,
+def _opts(B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, flags=0, cand_block=0, max_len=0.0):
+    return RefineOpts(B=B, max_len=max_len, max_iter=max_iter, cand_cap=cand_cap,
                       graph_iters=graph_iters, flags=flags, cand_block=cand_block)
 
 
@@ -168,9 +168,9 @@ class Mesh:
             pass
 
     def refine(self, B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0,
-               cand_block=0):
+               cand_block=0, max_len=0.0):
         s = Stats()
-        o = _opts(B, max_iter, cand_cap, graph_iters, flags, cand_block)
+        o = _opts(B, max_iter, cand_cap, graph_iters, flags, cand_block, max_len)
         st = load().gdp_mesh_refine(self._h, C.byref(o), C.byref(s))
         if check and st != OK:
             raise GdpError(st, "gdp_mesh_refine")
@@ -286,10 +286,11 @@ class Batch:
         except Exception:
             pass
 
-    def refine(self, B, max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0, cand_block=0):
+    def refine(self, B, max_iter=0, cand_cap=0, graph_iters=0, check=True, flags=0, cand_block=0,
+               max_len=0.0):
         Bs = np.ascontiguousarray(np.broadcast_to(np.asarray(B, np.float64), (self.n,)))
         s = Stats()
-        o = _opts(float(Bs[0]), max_iter, cand_cap, graph_iters, flags, cand_block)
+        o = _opts(float(Bs[0]), max_iter, cand_cap, graph_iters, flags, cand_block, max_len)
         st = load().gdp_batch_refine(self._h, _p(Bs), C.byref(o), C.byref(s))
         if check and st != OK:
             raise GdpError(st, "gdp_batch_refine")
@@ -366,8 +367,8 @@ class Server:
     pool (capacities in triangle slots, vertices, segments and meshes)."""
 
     def __init__(self, tri_slots, vert_slots, seg_slots, max_meshes, cand_cap=0, cand_block=0,
-                 graph_iters=0, stream=None):
-        o = _opts(math.sqrt(2.0), 0, cand_cap, graph_iters, 0, cand_block)
+                 graph_iters=0, stream=None, max_len=0.0):
+        o = _opts(math.sqrt(2.0), 0, cand_cap, graph_iters, 0, cand_block, max_len)
         self._h = C.c_void_p()
         st = load().gdp_server_create(int(tri_slots), int(vert_slots), int(seg_slots), int(max_meshes),
                                       C.byref(o), _stream_handle(stream), C.byref(self._h))

@@ -247,6 +247,40 @@ def paper_shaped(n_uniform=500_000, n_gauss=300_000, n_circle=200_000, n_seg=10_
                 name="paper_shaped", meta={"seed": seed, "fans": fans})
 
 
+def contours(n_hills=20, levels=25, per_curve=200, seed=SEED_BASE + 5) -> PSLG:
+    """Contour-map-like input (the paper's inputs are contour maps, Sec. 7.1):
+    the unit square plus n_hills families of nested closed polylines (levels
+    each, per_curve vertices per curve).  A family is r(theta) = r_k * f(theta)
+    around its centre with a common shape f > 0 and r_k = R k / (levels + 1),
+    so its curves never cross; families are placed apart.  No other points."""
+    rng = _rng(seed)
+    centres, radii = [], []
+    tries = 0
+    while len(centres) < n_hills and tries < 10000:
+        tries += 1
+        R = 0.03 + 0.07 * rng.random()
+        c = 0.02 + R * 1.3 + (1 - 2 * (0.02 + R * 1.3)) * rng.random(2)
+        if all(np.hypot(*(c - c2)) > 1.3 * (R + R2) + 0.01 for c2, R2 in zip(centres, radii)):
+            centres.append(c)
+            radii.append(R)
+    corners = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    pts = [corners]
+    segs = [(0, 1), (1, 2), (2, 3), (3, 0)]
+    n = 4
+    th = 2 * math.pi * np.arange(per_curve) / per_curve
+    for c, R in zip(centres, radii):
+        a, k, ph = 0.1 + 0.15 * rng.random(), int(rng.integers(2, 6)), 2 * math.pi * rng.random()
+        f = 1.0 + a * np.sin(k * th + ph)
+        for lv in range(1, levels + 1):
+            r = R * lv / (levels + 1) * f
+            pts.append(np.stack([c[0] + r * np.cos(th), c[1] + r * np.sin(th)], 1))
+            segs += [(n + j, n + (j + 1) % per_curve) for j in range(per_curve)]
+            n += per_curve
+    return PSLG(xy=np.ascontiguousarray(np.concatenate(pts), np.float64),
+                seg=np.ascontiguousarray(np.array(segs, np.int32)),
+                name="contours", meta={"seed": seed, "hills": len(centres)})
+
+
 def batched_sizes(count=4096, lo=200, hi=50_000, seed=SEED_BASE + 3):
     """point counts, log-uniform in [lo, hi]"""
     rng = _rng(seed)
