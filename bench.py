@@ -86,13 +86,23 @@ def parse():
     ap.add_argument("--impl", default="gdp", choices=["gdp", "reference"])
     ap.add_argument("--B", type=float, default=SQ2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mid", choices=["mid", "batched", "served"],
-                    help="mid: the headline line; batched / served: the batching and "
-                         "serving configurations (one JSON line each)")
+    ap.add_argument("--workload", default="mid", choices=["mid", "paper_shaped", "contours", "batched", "served"],
+                    help="mid: the headline line; paper_shaped / contours (with --max-len): the same "
+                         "step on those inputs; batched / served: the batching and serving "
+                         "configurations (one JSON line each)")
     ap.add_argument("--count", type=int, default=4096, help="batched: number of PSLGs")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
+    ap.add_argument("--cand-cap", type=int, default=0, help="per-mesh candidate cap (Rule 2), 0 = none")
+    ap.add_argument("--cand-block", type=int, default=0, help="threads per block of the per-candidate kernels")
+    ap.add_argument("--graph-iters", type=int, default=0, help="iterations per graph replay, -1 = no graph")
+    ap.add_argument("--max-len", type=float, default=0.0, help="edge-length bound l, 0 = none")
     return ap.parse_args()
+
+
+def refine_kwargs(args):
+    return {"cand_cap": args.cand_cap, "cand_block": args.cand_block, "graph_iters": args.graph_iters,
+            "max_len": args.max_len}
 
 
 # ---------------------------------------------------------------- batched / served
@@ -395,7 +405,7 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def cpu_baseline(p, B, reps=3):
+def cpu_baseline(p, B, reps=3, max_len=0.0, name="mid"):
     """the oracle as it stands: CDT + sequential Ruppert on the host, one thread"""
     from oracle import oracle
     oracle.build()
@@ -403,11 +413,11 @@ def cpu_baseline(p, B, reps=3):
     steiner = 0
     for _ in range(reps):
         m = oracle.Mesh(p.xy, p.seg)
-        assert m.refine(B) == 0
+        assert m.refine_len(B, max_len) == 0
         steiner += m.n_steiner
     dt = time.perf_counter() - t0
     return {"value": steiner / dt, "unit": "Steiner pts/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full runs of the mid workload (CDT + refine, {steiner // reps} "
+            "sample": f"{reps} full runs of the {name} workload (CDT + refine, {steiner // reps} "
                       f"Steiner points each), {dt:.2f} s"}
 
 
@@ -477,7 +487,19 @@ def main():
     dev = torch.device("cuda", local)
     from paper_2007_00324_gb300 import gdp, workloads
     gdp.load()
-    p = workloads.mid()
+    p = {"mid": workloads.mid, "paper_shaped": workloads.paper_shaped, "contours": workloads.contours}[
+        args.workload]()
+    config = dict(CONFIG) if args.workload == "mid" else {
+        "workload": {"paper_shaped": "paper-shaped: 1,000,164 points (uniform, Gaussian clusters, circles), "
+                                     "10,164 segments incl. 20 small-angle fans",
+                     "contours": "contours: unit square + 20 families x 25 nested closed polylines x 200 "
+                                 "vertices (100,004 points and segments)"}[args.workload],
+        "points": p.n, "segments": p.m, "B": args.B, "l2": CONFIG["l2"]}
+    if args.max_len > 0:
+        config["max_len"] = args.max_len
+    for k in ("cand_cap", "cand_block", "graph_iters"):
+        if getattr(args, k):
+            config[k] = getattr(args, k)
     stream = torch.cuda.current_stream(dev)
     xy_d = torch.from_numpy(p.xy).to(dev)
     seg_d = torch.from_numpy(p.seg).to(dev)
@@ -485,7 +507,7 @@ def main():
 
     def step():
         m = gdp.Mesh(xy_d, seg_d, stream=stream, device=True)
-        s = m.refine(args.B, flags=gdp.REFINE_TIME_GROW)
+        s = m.refine(args.B, flags=gdp.REFINE_TIME_GROW, **refine_kwargs(args))
         return m, s
 
     for _ in range(max(args.warmup, 3)):
@@ -530,7 +552,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m = gdp.Mesh(xy_h.numpy(), seg_h.numpy(), stream=stream)
-        s2 = m.refine(args.B)
+        s2 = m.refine(args.B, **refine_kwargs(args))
         xy_o, tri_o, sub_o = m.export()
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
@@ -574,11 +596,11 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    line = {"metric": "Steiner points inserted per second (CDT + refine, mid workload)",
+    line = {"metric": f"Steiner points inserted per second (CDT + refine, {args.workload} workload)",
             "value": value, "unit": "Steiner pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas x{world}"),
+            "data": "synthetic", "config": dict(config, parallelism=f"replicas x{world}"),
             "refine_ms": stats["refine_ms"], "cdt_ms": stats["cdt_ms"],
             "steiner_per_step": stats["n_steiner"], "iterations": stats["iterations"],
             "cdt_rounds": stats["cdt_rounds"],
@@ -586,7 +608,8 @@ def main():
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk.summary(),
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, args.B)
+        line["cpu_baseline"] = cpu_baseline(p, args.B, 3 if args.workload != "paper_shaped" else 1,
+                                            args.max_len, args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
