@@ -161,8 +161,8 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
   do {                                                               \
     LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P, 0);           \
     LAUNCH_C(h, k_grow_t<MODE>, P, 0);                               \
-    LAUNCH_B(h, k_grow_big<MODE>, LANES_A / 32, 32, P, 0);           \
-    LAUNCH_B(h, k_grow_big<MODE>, LANES_B, 1, P, 1);                 \
+    LAUNCH_B(h, k_grow_big<MODE>, LANES_A / 4, 128, P, 0);           \
+    LAUNCH_B(h, k_grow_big<MODE>, LANES_B / 4, 128, P, 1);                 \
   } while (0)
 
 double env_double(const char* name, double def) {
@@ -1042,8 +1042,8 @@ int PoolHost::launch_iteration(int k) {
   LAUNCH_B(*this, k_grow_w<0>, n_sm * 16, 128, P, timed);
   LAUNCH_C(*this, k_grow_t<0>, P, timed);
   if (timed) CK(cudaEventRecordWithFlags(tg[1], stream, rec));
-  LAUNCH_B(*this, k_grow_big<0>, LANES_A / 32, 32, P, 0);
-  LAUNCH_B(*this, k_grow_big<0>, LANES_B, 1, P, 1);
+  LAUNCH_B(*this, k_grow_big<0>, LANES_A / 4, 128, P, 0);
+  LAUNCH_B(*this, k_grow_big<0>, LANES_B / 4, 128, P, 1);
   LAUNCH_C(*this, k_survive, P);
   LAUNCH(*this, k_depend, G, P);
   LAUNCH(*this, k_offsets, G, P);

@@ -917,29 +917,175 @@ __global__ void __launch_bounds__(BS) k_grow_t(Pool P, int timed) {
   if (MODE == 0) acc_flush(P, acc, timed);   // every thread of the block reaches this
 }
 
+// Cavity growth in a spill lane by one warp: the level-synchronous growth of
+// wgrow with the lane's hash set for membership (any capacity).  Insertions
+// into the set use atomicCAS, so lanes adding different triangles in the
+// same step never overwrite each other; the list and record order, and so
+// the result, are those of the sequential growth (grow).
+__device__ __forceinline__ bool hash_has(const CavBuf& B, int t) {
+  int h = (int)(hash32((uint32_t)t) & (uint32_t)B.hmask);
+  for (int s = 0; s <= B.hmask; ++s) {
+    const int x = B.hash[h];
+    if (x == t) return true;
+    if (x < 0) return false;
+    h = (h + 1) & B.hmask;
+  }
+  return true;   // unreachable: the set is never more than half full
+}
+
+__device__ __forceinline__ void hash_put(const CavBuf& B, int t) {
+  int h = (int)(hash32((uint32_t)t) & (uint32_t)B.hmask);
+  for (int s = 0; s <= B.hmask; ++s) {
+    const int prev = atomicCAS(&B.hash[h], -1, t);
+    if (prev == -1 || prev == t) return;
+    h = (h + 1) & B.hmask;
+  }
+}
+
+__device__ int wgrow_h(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1, bool conv, int& nc,
+                       int& nb, int& ct, int& ce) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int j = lane; j <= B.hmask; j += 32) B.hash[j] = -1;
+  __syncwarp();
+  int k = 1, b = 0;
+  if (lane == 0) {
+    B.cav[0] = t0;
+    hash_put(B, t0);
+    if (t1 >= 0 && t1 != t0) {
+      B.cav[1] = t1;
+      hash_put(B, t1);
+    }
+  }
+  if (t1 >= 0 && t1 != t0) k = 2;
+  __syncwarp();
+  int lb = 0;
+  while (lb < k) {
+    const int le = k;
+    for (int base = 3 * lb; base < 3 * le; base += 32) {
+      const int slot = base + lane;
+      const bool act = slot < 3 * le;
+      int e = 0, ref = -1, cons = 0, u = -1, v = -1, tn = -1, t = -1;
+      if (act) {
+        const int q = slot / 3;
+        e = slot - 3 * q;
+        t = B.cav[q];
+        const int4 T4 = P.T[t];
+        const int4 N4 = P.N[t];
+        ref = comp(N4, e);
+        cons = (T4.w >> e) & 1;
+        u = comp(T4, mod3(e + 1));
+        v = comp(T4, mod3(e + 2));
+        tn = ref >= 0 ? ref >> 2 : -1;
+      }
+      bool member = act && tn >= 0 && hash_has(B, tn);
+      const bool test = act && !member && tn >= 0 && !cons;
+      const unsigned same = __match_any_sync(FULL, test ? tn : -2 - lane);
+      const int leader = __ffs(same) - 1;
+      bool in = false;
+      if (test && lane == leader) {
+        const int4 Tn = P.T[tn];
+        in = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
+      }
+      in = __shfl_sync(FULL, in, leader);
+      const unsigned adders = __ballot_sync(FULL, test && lane == leader && in);
+      const unsigned same_all = __match_any_sync(FULL, (act && tn >= 0) ? tn : -2 - lane);
+      if (act && tn >= 0 && (same_all & adders & lt_mask)) member = true;
+      int ev = 0;
+      if (act && !member) {
+        if (test) ev = (lane == leader && in) ? 1 : (in ? 0 : 2);
+        else if (cons && conv && dot_sign(pt(P, u), pt(P, v), p) < 0) ev = 3;
+        else ev = 2;
+      }
+      const unsigned am = __ballot_sync(FULL, ev == 1);
+      const unsigned rm = __ballot_sync(FULL, ev == 2);
+      const unsigned cm = __ballot_sync(FULL, ev == 3);
+      const int ar = __popc(am & lt_mask), rr = __popc(rm & lt_mask);
+      const unsigned ovf = __ballot_sync(FULL, (ev == 1 && k + ar >= B.cap) || (ev == 2 && b + rr >= B.cap + 2));
+      const int first_conv = cm ? __ffs(cm) - 1 : 32;
+      const int first_ovf = ovf ? __ffs(ovf) - 1 : 32;
+      if (first_conv < first_ovf) {
+        ct = __shfl_sync(FULL, t, first_conv);
+        ce = __shfl_sync(FULL, e, first_conv);
+        return G_CONV;
+      }
+      if (first_ovf < 32) return G_OVF;
+      if (ev == 1) {
+        B.cav[k + ar] = tn;
+        hash_put(B, tn);
+      } else if (ev == 2) {
+        B.bnd[b + rr] = make_int4(u, v, ref, (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
+      }
+      k += __popc(am);
+      b += __popc(rm);
+      __syncwarp();
+    }
+    lb = le;
+  }
+  nc = k;
+  nb = b;
+  return G_OK;
+}
+
 // Cavities that outgrew their slot (tier 0) or their tier-A lane (tier 1):
-// one thread per lane; the lane is freed for the next round as it is read.
+// one warp per lane; the lane is freed for the next round as it is read.
 template <int MODE>
-__global__ void k_grow_big(Pool P, int TIER) {
+__global__ void __maxnreg__(128) k_grow_big(Pool P, int TIER) {
+  __shared__ CandSetup ws[4];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int lanes = TIER ? LANES_B : LANES_A;
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= lanes) return;
-  int* lane = P.lane + (TIER ? LANES_A : 0) + l;
-  const int i = *lane;
-  if (i == LANE_FREE) return;
-  *lane = LANE_FREE;
-  const int cap = TIER ? CAP_B : CAP_A;
-  const size_t off = TIER ? (size_t)LANES_A * (CAP_A + 2) + (size_t)l * (CAP_B + 2)
-                          : (size_t)l * (CAP_A + 2);
-  const size_t hoff = TIER ? (size_t)LANES_A * 2 * CAP_A + (size_t)l * 2 * CAP_B
-                           : (size_t)l * 2 * CAP_A;
-  P.c_big[i] = (int)off;
-  const CavBuf B{P.big_cav + off, P.big_bnd + off, P.big_hash + hoff, cap, 2 * cap - 1};
-  GrowAcc acc;   // the work counters cover k_grow only
-  if (grow_cand<MODE>(P, i, B, acc) == G_OVF) {
-    P.c_big[i] = -1;
-    if (TIER == 0) atomicMin(&P.lane[LANES_A + (i & (LANES_B - 1))], i);
-    else set_err(P.ctrl, S_CAPACITY);
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int l = gw; l < lanes; l += nw) {
+    int* lp = P.lane + (TIER ? LANES_A : 0) + l;
+    const int i = *lp;
+    __syncwarp();
+    if (i == LANE_FREE) continue;
+    if (lane == 0) *lp = LANE_FREE;
+    const int cap = TIER ? CAP_B : CAP_A;
+    const size_t off = TIER ? (size_t)LANES_A * (CAP_A + 2) + (size_t)l * (CAP_B + 2)
+                            : (size_t)l * (CAP_A + 2);
+    const size_t hoff = TIER ? (size_t)LANES_A * 2 * CAP_A + (size_t)l * 2 * CAP_B
+                             : (size_t)l * 2 * CAP_A;
+    const CavBuf B{P.big_cav + off, P.big_bnd + off, P.big_hash + hoff, cap, 2 * cap - 1};
+    GrowAcc acc;   // the work counters cover k_grow_w / k_grow_t only
+    int ok = 1;
+    if (lane == 0) {
+      P.c_big[i] = (int)off;
+      ok = cand_setup<MODE>(P, i, ws[wib], acc) ? 1 : 0;
+    }
+    __syncwarp();
+    if (!__shfl_sync(FULL, ok, 0)) continue;
+    CandSetup s = ws[wib];
+    int nc = 0, nb = 0, ct = -1, ce = -1;
+    int g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, s.conv, nc, nb, ct, ce);
+    if (g == G_CONV) {
+      if (lane == 0) cand_conv(P, i, ws[wib], ct, ce);
+      __syncwarp();
+      s = ws[wib];
+      g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, false, nc, nb, ct, ce);
+    }
+    if (g == G_OVF) {
+      if (lane == 0) {
+        P.c_big[i] = -1;
+        if (TIER == 0) atomicMin(&P.lane[LANES_A + (i & (LANES_B - 1))], i);
+        else set_err(P.ctrl, S_CAPACITY);
+      }
+      __syncwarp();
+      continue;
+    }
+    __syncwarp();
+    const P2 pp{s.p, s.pf};
+    bool bad = false;
+    for (int r = lane; r < nb; r += 32) {
+      const int4 rec = B.bnd[r];
+      if (!is_split_edge(rec, s.sub) && orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) bad = true;
+    }
+    if (__any_sync(FULL, bad)) continue;
+    for (int j = lane; j < nc; j += 32) atomicMax(&P.mark[B.cav[j]], s.key);
+    if (lane == 0) cand_record(P, i, s, nc, nb, acc);
+    __syncwarp();
   }
 }
 
