@@ -1,8 +1,8 @@
 #!/usr/bin/env python
 """Benchmark of the gDP2d hot path on GB300: Steiner points inserted per second.
 
-One step = the whole hot path on one synthetic PSLG: the GPU CDT (Algorithm 1
-line 1) and the refinement loop (lines 2-9) of the mid workload
+One step = the whole hot path on one synthetic PSLG: the GPU CDT (the first step of
+Algorithm 1) and the refinement loop (the rest of Algorithm 1) of the mid workload
 (unit square + 100,000 uniform points + 1,000 random segments, B = sqrt 2).
 
   value   Steiner points / (CDT + refine) device time, inputs resident in HBM
@@ -46,6 +46,10 @@ CONFIG = {"workload": "mid: unit square + 100,000 uniform FP64 points + 1,000 ra
 #   per boundary edge 56 = neighbour test 40 + boundary record 16
 GROW_BYTES = {"candidate": 134, "walk_step": 56, "cavity_tri": 84, "boundary_edge": 56}
 GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
+# the kernels of one refinement iteration (launched once per iteration, so an ncu
+# launch list counts them in every step and their shares compare directly)
+REFINE_KERNELS = ("k_scan_count", "k_scan_write", "k_grow_w<0>", "k_grow_t<0>", "k_grow_big<0>", "k_survive",
+                  "k_depend", "k_insert_w<0>", "k_insert_t<0>", "k_link<0>")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cavity_growth_mid_traffic.md")
 
 
@@ -585,6 +589,8 @@ def main():
             "kernel": "cavity growth: k_grow_w<0> + k_grow_t<0>", "algorithmic_bytes_per_launch": by / n_l,
             "kernel_ms_per_launch": grow["grow_ms"] / n_l, "launches": grow["grow_launches"],
             "share_of_kernel_time": sum(kt.get(k, (0.0, 0))[0] for k in ("k_grow_w<0>", "k_grow_t<0>")) / tot_k,
+            "share_of_refine_kernel_time": sum(kt.get(k, (0.0, 0))[0] for k in ("k_grow_w<0>", "k_grow_t<0>")) /
+            max(sum(kt.get(k, (0.0, 0))[0] for k in REFINE_KERNELS), 1e-9),
             "largest_kernel": top[0],
             "peak_source": "measured (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "timed_launches": "the first iteration of every 8-iteration graph replay",

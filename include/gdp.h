@@ -3,8 +3,8 @@
  *
  * The library turns a planar straight-line graph (PSLG: points P and
  * non-crossing segments E, Sec. 4 of the paper) into its constrained Delaunay
- * triangulation (CDT, Algorithm 1 line 1) and refines it (Algorithm 1 lines
- * 2-9): Steiner points are inserted in parallel until no subsegment is
+ * triangulation (CDT, the first step of Algorithm 1) and refines it (the loop of
+ * Algorithm 1): Steiner points are inserted in parallel until no subsegment is
  * encroached (a vertex strictly inside its diametral circle, Sec. 4.2) and no
  * triangle has radius-edge ratio above B (the 3D bad-element measure of
  * Sec. 5.1, used here in 2D; B = sqrt 2 is a 20.7 degree angle bound).
@@ -91,7 +91,7 @@ typedef struct {
 /* gdp_refine_opts.flags */
 #define GDP_REFINE_TIME_GROW 1
 
-/* Build the CDT of a PSLG on the GPU (Algorithm 1 line 1).
+/* Build the CDT of a PSLG on the GPU (the first step of Algorithm 1).
  *   xy:  2*n_pts doubles, host;   seg: 2*n_seg int32 indices, host (may be NULL if 0)
  * The domain is the region enclosed by segments: triangles reachable from
  * outside without crossing a segment are removed, so the convex hull must be
@@ -104,7 +104,7 @@ int gdp_mesh_create(const double* xy, int64_t n_pts, const int32_t* seg, int64_t
 int gdp_mesh_create_device(const double* xy_device, int64_t n_pts, const int32_t* seg_device,
                            int64_t n_seg, void* cuda_stream, gdp_mesh** out);
 
-/* Refine (Algorithm 1 lines 2-9) until nothing is encroached and no
+/* Refine (the loop of Algorithm 1) until nothing is encroached and no
  * triangle is bad, bad triangles at small input angles excepted (Sec. 4.1).
  * opts may be NULL (defaults); stats may be NULL.  Blocks until done. */
 int gdp_mesh_refine(gdp_mesh* mesh, const gdp_refine_opts* opts, gdp_stats* stats);
@@ -129,8 +129,8 @@ int gdp_mesh_insert_points(gdp_mesh* mesh, const double* xy, int64_t n);
  * ax, ay, bx, by) at their midpoints, in parallel rounds. */
 int gdp_mesh_split_subsegments(gdp_mesh* mesh, const double* abxy, int64_t n);
 
-/* One bad-element scan (Algorithm 1 line 3) plus splitting points and
- * priorities (lines 5-6, before point location) of the current mesh.
+/* One bad-element scan (Algorithm 1) plus splitting points and
+ * priorities (before point location) of the current mesh.
  * Outputs per element, cap entries each (host buffers, NULL to skip):
  *   kind[i]:  0 = bad triangle, 1 = encroached subsegment
  *   verts[3i..3i+2]: the triangle's vertices (CCW), or the subsegment's two
@@ -208,9 +208,9 @@ int gdp_autotune(const double* xy, const int64_t* pt_off, const int32_t* seg,
  * resident device pool with room for tri_slots triangles, vert_slots vertices,
  * seg_slots input segments and max_meshes meshes (admission is by this
  * device memory).  Each gdp_server_step
- *   1. launches opts->graph_iters (0: 8) refinement iterations (lines 2-9)
+ *   1. launches opts->graph_iters (0: 8) refinement iterations
  *      over every resident mesh at once (one CUDA-graph replay);
- *   2. while they run, builds the initial CDT (line 1) of the oldest waiting
+ *   2. while they run, builds the initial CDT of the oldest waiting
  *      requests in staging pools on a second stream, as long as a region of
  *      the resident pool is free for them (first come, first served);
  *   3. retires the meshes that finished (no candidate in the last iteration,

@@ -530,7 +530,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   AL(P.c_vseg, C, 0); AL(P.c_sub, C, 0); AL(P.c_pt, C, 0); AL(P.c_ptf, C, 0); AL(P.c_key, C, 0);
   AL(P.c_ncav, C, 0); AL(P.c_nbnd, C, 0); AL(P.c_cav, C * CMAX, 0); AL(P.c_bnd, C * BMAX, 0);
   AL(P.c_big, C, 0xff); AL(P.big_cav, BIG_ENTRIES, 0); AL(P.big_bnd, BIG_ENTRIES, 0);
-  AL(P.big_hash, BIG_HASH, 0xff); AL(P.lane, LANES_A + LANES_B, 0x7f);
+  AL(P.big_hash, BIG_HASH, 0xff); AL(P.big_val, BIG_HASH, 0xff); AL(P.lane, LANES_A + LANES_B, 0x7f);
   AL(P.c_state, C, 0); AL(P.c_final, C, 0); AL(P.c_extra, C, 0); AL(P.c_offT, C, 0);
   AL(P.c_offV, C, 0); AL(P.c_base, C, 0);
   AL(P.blk, 2 * G, 0);
@@ -590,8 +590,8 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   return GDP_OK;
 }
 
-// One parallel insertion round of the pending points in Q.pts (Algorithm 1
-// line 1 builds the CDT from them; the fixed-batch test hook inserts extra
+// One parallel insertion round of the pending points in Q.pts (the initial
+// CDT of Algorithm 1 is built from them; the fixed-batch test hook inserts extra
 // points the same way): locate, one point per triangle, cavities, marks,
 // dependence, re-triangulation, and the points left go to Q.pts2.
 int PoolHost::launch_cdt_round(const Pool& Q, int stop_cons) {

@@ -1,4 +1,4 @@
-// The initial CDT on the GPU (Algorithm 1 line 1).
+// The initial CDT on the GPU (the first step of Algorithm 1).
 //
 // 1. Point insertion in parallel rounds into one enclosing triangle per mesh.
 //    Every pending point walks to the triangle containing it; each triangle

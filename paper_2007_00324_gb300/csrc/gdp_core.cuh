@@ -9,13 +9,14 @@
 //   dirty[t] u8                       triangle changed since its last quality check
 //   V[v]   double2                    vertex coordinates (FP64)
 //   vseg[v] int32                     input segment a Steiner vertex lies on, else -1
-// Per-candidate scratch (one candidate = one splitting point, Algorithm 1 line 5):
+// Per-candidate scratch (one candidate = one splitting point of Algorithm 1):
 //   c_cav[i*CMAX + j]   cavity triangles;  c_bnd[i*BMAX + j]  cavity boundary edges
 //   as int4 (u, v, outside ref, inside ref | subsegment << 31).
 //   A cavity that outgrows its slot is grown again in a lane of a spill tier
 //   (big_cav / big_bnd at offset c_big[i]): LANES_A lanes of CAP_A triangles,
 //   then LANES_B lanes of CAP_B = CMAX_BIG; each lane has a hash set of twice
-//   its capacity in big_hash.
+//   its capacity in big_hash (cavity membership while growing; the fan map
+//   vertex -> boundary records, with big_val, while inserting).
 #pragma once
 #include <cstdint>
 
@@ -134,6 +135,7 @@ struct Pool {
   int32_t* big_cav;      // BIG_ENTRIES
   int4* big_bnd;         // BIG_ENTRIES
   int32_t* big_hash;     // BIG_HASH
+  int2* big_val;         // BIG_HASH: values of the fan map of a spill-tier cavity
   int32_t* lane;         // LANES_A + LANES_B owners (smallest candidate index)
   uint8_t* c_state;
   uint8_t* c_final;

@@ -1,14 +1,14 @@
 // Kernels of the parallel refinement loop (Algorithm 1) and of the GPU CDT.
 //
-// One refinement iteration (Algorithm 1, lines 3-8) is eight launches, all
+// One refinement iteration of Algorithm 1 is eight launches, all
 // over the whole pool (every mesh of a batch at once, Rule 4):
-//   k_scan_count / k_scan_write   line 3: changed triangles are checked for
+//   k_scan_count / k_scan_write   the scan: changed triangles are checked for
 //                                 encroached subsegments and bad quality and the
 //                                 hits are compacted, in slot order, into the
 //                                 candidate list (block counts + block scans;
 //                                 the compaction is stable so the run is
 //                                 deterministic)
-//   k_grow                        lines 5-7: splitting point and priority,
+//   k_grow                        splitting point and priority,
 //                                 point location by walking, cavity growth by
 //                                 incircle blocked at subsegments, then one
 //                                 64-bit atomicMax mark per cavity triangle
@@ -17,7 +17,7 @@
 //                                 boundary edges (Sec. 5.2): the lower priority
 //                                 point of a dependent pair is dropped
 //   k_offsets                     stable prefix sums for new slots / vertex ids
-//   k_insert / k_link             line 8: cavity re-triangulation as a fan,
+//   k_insert / k_link             insertion: cavity re-triangulation as a fan,
 //                                 neighbour fix-up, then links between adjacent
 //                                 cavities
 // The same cavity kernels insert the input points of the initial CDT; the
@@ -222,7 +222,7 @@ __device__ double2 split_point(const Pool& P, const MeshInfo& M, int u, int v) {
   return make_double2(O.x + dx * r, O.y + dy * r);
 }
 
-// ---------------------------------------------------------------- scan (line 3)
+// ---------------------------------------------------------------- scan
 // 0: nothing; 1..3: encroached subsegment on edge 0..2 (longest); 4: bad triangle
 __device__ int eval_tri(const Pool& P, int t) {
   const int4 T4 = P.T[t];
@@ -288,25 +288,38 @@ __device__ __forceinline__ int4* bnd_of(const Pool& P, int i) {
   return o < 0 ? P.c_bnd + (size_t)i * BMAX : P.big_bnd + o;
 }
 
-__global__ void __launch_bounds__(BS) k_clear_marks(Pool P) {
+// Clears the marks of the previous iteration's cavities: one thread per
+// candidate, the whole warp for a spill-tier cavity.  Called by all threads.
+__device__ __forceinline__ void clear_prev_marks(const Pool& P) {
+  const unsigned FULL = 0xffffffffu;
   const int prev = P.ctrl->prev_cand;
+  const int lane = threadIdx.x & 31;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int i = gt; i < prev; i += gs) {
-    const int n = P.c_ncav[i];
-    const int* cav = cav_of(P, i);
-    for (int j = 0; j < n; ++j) P.mark[cav[j]] = 0ull;
+  for (int i0 = gt - lane; i0 < prev; i0 += gs) {
+    const int i = i0 + lane;
+    const int n = i < prev ? P.c_ncav[i] : 0;
+    const bool big = n > CMAX;
+    if (!big) {
+      const int* cav = cav_of(P, i);
+      for (int j = 0; j < n; ++j) P.mark[cav[j]] = 0ull;
+    }
+    unsigned bm = __ballot_sync(FULL, big);
+    while (bm) {
+      const int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      const int ib = __shfl_sync(FULL, i, src), nb = __shfl_sync(FULL, n, src);
+      const int* cav = cav_of(P, ib);
+      for (int j = lane; j < nb; j += 32) P.mark[cav[j]] = 0ull;
+    }
   }
 }
 
+__global__ void __launch_bounds__(BS) k_clear_marks(Pool P) { clear_prev_marks(P); }
+
 __global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
   __shared__ int sm[33];
-  const int prev = P.ctrl->prev_cand;
+  clear_prev_marks(P);
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int i = gt; i < prev; i += gs) {
-    const int n = P.c_ncav[i];
-    const int* cav = cav_of(P, i);
-    for (int j = 0; j < n; ++j) P.mark[cav[j]] = 0ull;
-  }
   for (int m = gt; m < P.n_mesh; m += gs) {
     P.mi[m].first_cand = -1;
     P.mi[m].last_cand = -1;
@@ -419,7 +432,7 @@ __global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
   }
 }
 
-// ---------------------------------------------------------------- locate + grow (lines 5-7)
+// ---------------------------------------------------------------- locate + grow
 // Visibility walk from t towards p.  Returns the triangle containing p
 // (closed), -1 when the next step would cross a subsegment (stop_cons) or the
 // hull -- (bt, be) is that edge -- or -2 at the step limit.  In a CDT every
@@ -597,7 +610,7 @@ __device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a, int timed =
 }
 
 // Splitting point, priority key and start triangles of candidate i
-// (Algorithm 1 lines 5-6).  MODE 0: refinement candidates (element =
+// (Algorithm 1).  MODE 0: refinement candidates (element =
 // triangle << 2 | edge, 3 = the triangle); MODE 1: given points (element =
 // vertex id, c_loc = located triangle).  False when the walk failed.
 struct CandSetup {
@@ -690,7 +703,7 @@ __device__ void cand_conv(const Pool& P, int i, CandSetup& s, int ct, int ce) {
   s.conv = false;
 }
 
-// the grown candidate's record (lines 6-7 of the candidate's state)
+// the grown candidate's record: point, priority, cavity sizes
 __device__ void cand_record(const Pool& P, int i, const CandSetup& s, int nc, int nb, GrowAcc& acc) {
   P.c_pt[i] = s.p;
   P.c_ptf[i] = s.pf;
@@ -1091,20 +1104,49 @@ __global__ void __maxnreg__(128) k_grow_big(Pool P, int TIER) {
 
 // a point survives iff it still owns the mark of every cavity triangle
 __global__ void __launch_bounds__(BS) k_survive(Pool P) {
+  const unsigned FULL = 0xffffffffu;
   const int n = P.ctrl->n_cand;
+  const int lane = threadIdx.x & 31;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int i = gt; i < n; i += gs) {
-    const int m = P.c_mesh[i];
-    if (i == 0 || P.c_mesh[i - 1] != m) P.mi[m].first_cand = i;
-    if (i == n - 1 || P.c_mesh[i + 1] != m) P.mi[m].last_cand = i;
-    if (P.c_state[i] != C_GROWN) continue;
-    const unsigned long long key = P.c_key[i];
-    const int* cav = cav_of(P, i);
-    const int nc = P.c_ncav[i];
-    bool own = true;
-    for (int j = 0; j < nc && own; ++j) own = P.mark[cav[j]] == key;
-    P.c_state[i] = own ? C_SURV : C_LOST;
-    if (own) atomicAdd(&P.ctrl->n_surv, 1ull);
+  for (int i0 = gt - lane; i0 < n; i0 += gs) {   // whole warps: spill-tier cavities below
+    const int i = i0 + lane;
+    bool big = false;
+    if (i < n) {
+      const int m = P.c_mesh[i];
+      if (i == 0 || P.c_mesh[i - 1] != m) P.mi[m].first_cand = i;
+      if (i == n - 1 || P.c_mesh[i + 1] != m) P.mi[m].last_cand = i;
+      if (P.c_state[i] == C_GROWN) {
+        const int nc = P.c_ncav[i];
+        big = nc > CMAX;
+        if (!big) {
+          const unsigned long long key = P.c_key[i];
+          const int* cav = cav_of(P, i);
+          bool own = true;
+          for (int j = 0; j < nc && own; ++j) own = P.mark[cav[j]] == key;
+          P.c_state[i] = own ? C_SURV : C_LOST;
+          if (own) atomicAdd(&P.ctrl->n_surv, 1ull);
+        }
+      }
+    }
+    unsigned bm = __ballot_sync(FULL, big);
+    while (bm) {
+      const int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      const int ib = __shfl_sync(FULL, i, src);
+      const unsigned long long key = P.c_key[ib];
+      const int* cav = cav_of(P, ib);
+      const int nc = P.c_ncav[ib];
+      bool own = true;
+      for (int j0 = 0; j0 < nc; j0 += 32) {
+        const int j = j0 + lane;
+        own = __all_sync(FULL, j >= nc || P.mark[cav[j]] == key);
+        if (!own) break;
+      }
+      if (lane == 0) {
+        P.c_state[ib] = own ? C_SURV : C_LOST;
+        if (own) atomicAdd(&P.ctrl->n_surv, 1ull);
+      }
+    }
   }
 }
 
@@ -1192,60 +1234,108 @@ __device__ __forceinline__ bool replaced(const Pool& P, int ref, int n) {
   return j < n && P.c_final[j];
 }
 
-// Re-triangulate every surviving cavity as the fan from its point
-// (Sec. 5.2 insertion + housekeeping).  Cavity slots are reused first, extra
-// slots come from the mesh's bump region at stable prefix-sum offsets.
-template <int MODE>
-__global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
-  const int n = P.ctrl->n_cand;
-  if (n <= P.warp_max) return;   // k_insert_w's case
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int i = gt; i < n; i += gs) {
-    const int m = P.c_mesh[i];
-    const MeshInfo& M = P.mi[m];
-    const int f = M.first_cand, l = M.last_cand;
-    int totE, totV;
-    mesh_totals(P, f, l, totE, totV);
-    const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
-    if (i == f) {
-      P.mi[m].ins_ok = ok ? 1 : 0;
-      if (!ok) P.mi[m].status = S_NOMEM;
+// ---------------------------------------------------------------- spill-tier cavities, one warp each
+// Cavities of the spill tiers have hundreds to tens of thousands of triangles.
+// The thread-per-candidate kernels hand them to their whole warp (ballot, then
+// one such candidate at a time), so no lane walks one alone.
+
+// the fan map of the spill-tier region at offset off: keys (vertex ids) in
+// big_hash, values in big_val, capacity twice the region's
+struct BigMap {
+  int* key;
+  int2* val;
+  int cap;
+};
+__device__ __forceinline__ BigMap big_map(const Pool& P, int off) {
+  const int endA = LANES_A * (CAP_A + 2);
+  if (off < endA) {
+    const size_t h = (size_t)(off / (CAP_A + 2)) * 2 * CAP_A;
+    return {P.big_hash + h, P.big_val + h, 2 * CAP_A};
+  }
+  const size_t h = (size_t)LANES_A * 2 * CAP_A + (size_t)((off - endA) / (CAP_B + 2)) * 2 * CAP_B;
+  return {P.big_hash + h, P.big_val + h, 2 * CAP_B};
+}
+
+// slot of vertex v, inserted if absent (atomicCAS, linear probing); -1 only
+// if the map were full, which it never is (at most half full)
+__device__ __forceinline__ int map_slot(const BigMap& M, int mask, int v) {
+  int h = (int)(hash32((uint32_t)v) & (uint32_t)mask);
+  for (int s = 0; s <= mask; ++s) {
+    const int prev = atomicCAS(&M.key[h], -1, v);
+    if (prev == -1 || prev == v) return h;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int map_find(const BigMap& M, int mask, int v) {
+  int h = (int)(hash32((uint32_t)v) & (uint32_t)mask);
+  for (int s = 0; s <= mask; ++s) {
+    const int x = __ldcg(&M.key[h]);
+    if (x == v) return h;
+    if (x < 0) return -1;
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// The fan of spill-tier cavity i, written by the calling warp (all lanes).
+// The map gives per vertex the largest rank of a kept boundary record that
+// starts (x) and that ends (y) there, so every record finds its two fan
+// neighbours in O(1) -- the same ones as the quadratic search of the small
+// cavities, which keeps the last match.
+__device__ void fan_big(const Pool& P, int i, int m, int base, int vid, int n) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int off = P.c_big[i];
+  const BigMap M = big_map(P, off);
+  const int4* bnd = P.big_bnd + off;
+  const int* cav = P.big_cav + off;
+  const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
+  const int2 sub = P.c_sub[i];
+  const bool is_mid = sub.x >= 0;
+  int hs = 64;
+  while (hs < 2 * (nb + 1) && hs < M.cap) hs <<= 1;
+  const int mask = hs - 1;
+  for (int j = lane; j < hs; j += 32) {
+    M.key[j] = -1;
+    M.val[j] = make_int2(-1, -1);
+  }
+  __syncwarp();
+  int done = 0;   // kept records before this chunk
+  for (int r0 = 0; r0 < nb; r0 += 32) {
+    const int r = r0 + lane;
+    const int4 rec = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
+    const bool keep = r < nb && !is_split_edge(rec, sub);
+    const unsigned km = __ballot_sync(FULL, keep);
+    if (keep) {
+      const int j = done + __popc(km & lt_mask);
+      const int hu = map_slot(M, mask, rec.x), hv = map_slot(M, mask, rec.y);
+      if (hu >= 0) atomicMax(&M.val[hu].x, j);
+      if (hv >= 0) atomicMax(&M.val[hv].y, j);
     }
-    // the element is re-checked whatever happens: it may be untouched when its
-    // splitting point moved to a subsegment, or when the point was not inserted
-    if (MODE == 0) P.dirty[P.c_elem[i] >> 2] = 1;
-    if (!P.c_final[i] || !ok) continue;
-    const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
-    const int vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
-    P.c_base[i] = base;
-    const double2 p = P.c_pt[i];
-    P.V[vid] = p;
-    P.Vf[vid] = P.c_ptf[i];
-    P.vseg[vid] = P.c_vseg[i];
-    if (MODE == 1) P.loc[vid] = -1;
-    const int4* bnd = bnd_of(P, i);
-    const int* cav = cav_of(P, i);
-    const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
-    const int2 sub = P.c_sub[i];
-    const bool is_mid = sub.x >= 0;
-    int j = 0;
-    for (int r = 0; r < nb; ++r) {
-      const int4 rec = bnd[r];
-      if (is_split_edge(rec, sub)) continue;
+    done += __popc(km);
+  }
+  __syncwarp();
+  done = 0;
+  for (int r0 = 0; r0 < nb; r0 += 32) {
+    const int r = r0 + lane;
+    const int4 rec = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
+    const bool keep = r < nb && !is_split_edge(rec, sub);
+    const unsigned km = __ballot_sync(FULL, keep);
+    if (keep) {
+      const int j = done + __popc(km & lt_mask);
       const int s = j < nc ? cav[j] : base + (j - nc);
       const int u = rec.x, v = rec.y;
       int cb = rec.w < 0 ? 1 : 0;
       if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
       if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
-      int n1 = -1, n2 = -1, jj = 0;
-      for (int r2 = 0; r2 < nb; ++r2) {
-        const int4 q = bnd[r2];
-        if (is_split_edge(q, sub)) continue;
-        const int s2 = jj < nc ? cav[jj] : base + (jj - nc);
-        if (q.x == v) n1 = (s2 << 2) | 2;
-        if (q.y == u) n2 = (s2 << 2) | 1;
-        ++jj;
-      }
+      const int hv = map_find(M, mask, v), hu = map_find(M, mask, u);
+      const int a = hv >= 0 ? __ldcg(&M.val[hv].x) : -1;
+      const int b = hu >= 0 ? __ldcg(&M.val[hu].y) : -1;
+      const int n1 = a >= 0 ? ((a < nc ? cav[a] : base + (a - nc)) << 2) | 2 : -1;
+      const int n2 = b >= 0 ? ((b < nc ? cav[b] : base + (b - nc)) << 2) | 1 : -1;
       int n0 = rec.z;
       if (n0 >= 0) {
         if (replaced(P, n0, n)) n0 = -1;   // linked by k_link
@@ -1258,14 +1348,102 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
       P.vtri[u] = s;
       P.vtri[v] = s;
       P.vtri[vid] = s;
-      ++j;
+    }
+    done += __popc(km);
+  }
+}
+
+// Re-triangulate every surviving cavity as the fan from its point
+// (Sec. 5.2 insertion + housekeeping).  Cavity slots are reused first, extra
+// slots come from the mesh's bump region at stable prefix-sum offsets.
+template <int MODE>
+__global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
+  const unsigned FULL = 0xffffffffu;
+  const int n = P.ctrl->n_cand;
+  if (n <= P.warp_max) return;   // k_insert_w's case
+  const int lane = threadIdx.x & 31;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int i0 = gt - lane; i0 < n; i0 += gs) {   // whole warps: spill-tier fans below
+    const int i = i0 + lane;
+    bool big = false;
+    int m = 0, base = 0, vid = 0;
+    if (i < n) {
+      m = P.c_mesh[i];
+      const MeshInfo& M = P.mi[m];
+      const int f = M.first_cand, l = M.last_cand;
+      int totE, totV;
+      mesh_totals(P, f, l, totE, totV);
+      const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
+      if (i == f) {
+        P.mi[m].ins_ok = ok ? 1 : 0;
+        if (!ok) P.mi[m].status = S_NOMEM;
+      }
+      // the element is re-checked whatever happens: it may be untouched when its
+      // splitting point moved to a subsegment, or when the point was not inserted
+      if (MODE == 0) P.dirty[P.c_elem[i] >> 2] = 1;
+      if (P.c_final[i] && ok) {
+        base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
+        vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
+        P.c_base[i] = base;
+        P.V[vid] = P.c_pt[i];
+        P.Vf[vid] = P.c_ptf[i];
+        P.vseg[vid] = P.c_vseg[i];
+        if (MODE == 1) P.loc[vid] = -1;
+        big = P.c_big[i] >= 0;
+        if (!big) {
+          const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+          const int* cav = P.c_cav + (size_t)i * CMAX;
+          const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
+          const int2 sub = P.c_sub[i];
+          const bool is_mid = sub.x >= 0;
+          int j = 0;
+          for (int r = 0; r < nb; ++r) {
+            const int4 rec = bnd[r];
+            if (is_split_edge(rec, sub)) continue;
+            const int s = j < nc ? cav[j] : base + (j - nc);
+            const int u = rec.x, v = rec.y;
+            int cb = rec.w < 0 ? 1 : 0;
+            if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
+            if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
+            int n1 = -1, n2 = -1, jj = 0;
+            for (int r2 = 0; r2 < nb; ++r2) {
+              const int4 q = bnd[r2];
+              if (is_split_edge(q, sub)) continue;
+              const int s2 = jj < nc ? cav[jj] : base + (jj - nc);
+              if (q.x == v) n1 = (s2 << 2) | 2;
+              if (q.y == u) n2 = (s2 << 2) | 1;
+              ++jj;
+            }
+            int n0 = rec.z;
+            if (n0 >= 0) {
+              if (replaced(P, n0, n)) n0 = -1;   // linked by k_link
+              else *comp_ptr(&P.N[n0 >> 2], n0 & 3) = s << 2;
+            }
+            P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
+            P.N[s] = make_int4(n0, n1, n2, 0);
+            P.newref[rec.w & 0x7fffffff] = s << 2;
+            P.dirty[s] = 1;
+            P.vtri[u] = s;
+            P.vtri[v] = s;
+            P.vtri[vid] = s;
+            ++j;
+          }
+        }
+      }
+    }
+    unsigned bm = __ballot_sync(FULL, big);
+    while (bm) {
+      const int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      fan_big(P, __shfl_sync(FULL, i, src), __shfl_sync(FULL, m, src), __shfl_sync(FULL, base, src),
+              __shfl_sync(FULL, vid, src), n);
     }
   }
 }
 
 // The same, one warp per candidate up to P.warp_max candidates: the
 // lanes take the cavity's boundary records (up to 64; larger spill-tier
-// cavities go through lane 0), find the fan neighbours by shuffles and write
+// cavities go through fan_big), find the fan neighbours by shuffles and write
 // the new triangles in parallel.  Identical output to k_insert_t.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
@@ -1305,42 +1483,8 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
       P.vseg[vid] = P.c_vseg[i];
       if (MODE == 1) P.loc[vid] = -1;
     }
-    if (nb > 64) {   // a spill-tier cavity: one lane, the sequential order
-      if (lane == 0) {
-        int j = 0;
-        for (int r = 0; r < nb; ++r) {
-          const int4 rec = bnd[r];
-          if (is_split_edge(rec, sub)) continue;
-          const int s = j < nc ? cav[j] : base + (j - nc);
-          const int u = rec.x, v = rec.y;
-          int cb = rec.w < 0 ? 1 : 0;
-          if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
-          if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
-          int n1 = -1, n2 = -1, jj = 0;
-          for (int r2 = 0; r2 < nb; ++r2) {
-            const int4 q = bnd[r2];
-            if (is_split_edge(q, sub)) continue;
-            const int s2 = jj < nc ? cav[jj] : base + (jj - nc);
-            if (q.x == v) n1 = (s2 << 2) | 2;
-            if (q.y == u) n2 = (s2 << 2) | 1;
-            ++jj;
-          }
-          int n0 = rec.z;
-          if (n0 >= 0) {
-            if (replaced(P, n0, n)) n0 = -1;
-            else *comp_ptr(&P.N[n0 >> 2], n0 & 3) = s << 2;
-          }
-          P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
-          P.N[s] = make_int4(n0, n1, n2, 0);
-          P.newref[rec.w & 0x7fffffff] = s << 2;
-          P.dirty[s] = 1;
-          P.vtri[u] = s;
-          P.vtri[v] = s;
-          P.vtri[vid] = s;
-          ++j;
-        }
-      }
-      __syncwarp();
+    if (nb > 64) {   // a spill-tier cavity: the map-based fan
+      fan_big(P, i, m, base, vid, n);
       continue;
     }
     // records lane and lane + 32; j = rank among the records that are not the split edge
@@ -1397,36 +1541,70 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
 // links between adjacent cavities, then per-mesh counters
 template <int MODE>
 __global__ void __launch_bounds__(BS) k_link(Pool P) {
+  const unsigned FULL = 0xffffffffu;
   const int n = P.ctrl->n_cand;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   int ins = 0;
-  for (int i = gt; i < n; i += gs) {
-    const int m = P.c_mesh[i];
-    const MeshInfo& M = P.mi[m];
-    const bool ok = M.ins_ok;
-    if (P.c_final[i] && ok) {
-      ++ins;
-      const int4* bnd = bnd_of(P, i);
-      const int* cav = cav_of(P, i);
-      const int nc = P.c_ncav[i], nb = P.c_nbnd[i], base = P.c_base[i];
-      const int2 sub = P.c_sub[i];
-      int j = 0;
-      for (int r = 0; r < nb; ++r) {
-        const int4 rec = bnd[r];
-        if (is_split_edge(rec, sub)) continue;
-        if (rec.z >= 0 && replaced(P, rec.z, n)) {
+  for (int i0 = gt - lane; i0 < n; i0 += gs) {   // whole warps: spill-tier cavities below
+    const int i = i0 + lane;
+    bool big = false;
+    if (i < n) {
+      const int m = P.c_mesh[i];
+      const MeshInfo& M = P.mi[m];
+      const bool ok = M.ins_ok;
+      if (P.c_final[i] && ok) {
+        ++ins;
+        big = P.c_big[i] >= 0;
+        if (!big) {
+          const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+          const int* cav = P.c_cav + (size_t)i * CMAX;
+          const int nc = P.c_ncav[i], nb = P.c_nbnd[i], base = P.c_base[i];
+          const int2 sub = P.c_sub[i];
+          int j = 0;
+          for (int r = 0; r < nb; ++r) {
+            const int4 rec = bnd[r];
+            if (is_split_edge(rec, sub)) continue;
+            if (rec.z >= 0 && replaced(P, rec.z, n)) {
+              const int s = j < nc ? cav[j] : base + (j - nc);
+              P.N[s].x = P.newref[rec.z];
+            }
+            ++j;
+          }
+        }
+      }
+      if (i == M.last_cand && ok) {
+        int totE, totV;
+        mesh_totals(P, M.first_cand, i, totE, totV);
+        P.mi[m].tri_count = M.tri_count + totE;
+        P.mi[m].vert_count = M.vert_count + totV;
+        if (MODE == 0) P.mi[m].steiner = M.steiner + totV;
+      }
+    }
+    unsigned bm = __ballot_sync(FULL, big);
+    while (bm) {
+      const int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      const int ib = __shfl_sync(FULL, i, src);
+      const int off = P.c_big[ib];
+      const int4* bnd = P.big_bnd + off;
+      const int* cav = P.big_cav + off;
+      const int nc = P.c_ncav[ib], nb = P.c_nbnd[ib], base = P.c_base[ib];
+      const int2 sub = P.c_sub[ib];
+      int done = 0;   // kept records before this chunk
+      for (int r0 = 0; r0 < nb; r0 += 32) {
+        const int r = r0 + lane;
+        const int4 rec = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
+        const bool keep = r < nb && !is_split_edge(rec, sub);
+        const unsigned km = __ballot_sync(FULL, keep);
+        if (keep && rec.z >= 0 && replaced(P, rec.z, n)) {
+          const int j = done + __popc(km & lt_mask);
           const int s = j < nc ? cav[j] : base + (j - nc);
           P.N[s].x = P.newref[rec.z];
         }
-        ++j;
+        done += __popc(km);
       }
-    }
-    if (i == M.last_cand && ok) {
-      int totE, totV;
-      mesh_totals(P, M.first_cand, i, totE, totV);
-      P.mi[m].tri_count = M.tri_count + totE;
-      P.mi[m].vert_count = M.vert_count + totV;
-      if (MODE == 0) P.mi[m].steiner = M.steiner + totV;
     }
   }
   for (int o = 16; o; o >>= 1) ins += __shfl_xor_sync(0xffffffffu, ins, o);

@@ -244,7 +244,7 @@ static int server_setup(gdp_server* s, long long tb, long long vb, long long sb,
   AL(H.P.c_key, C, 0); AL(H.P.c_ncav, C, 0); AL(H.P.c_nbnd, C, 0);
   AL(H.P.c_cav, C * CMAX, 0); AL(H.P.c_bnd, C * BMAX, 0);
   AL(H.P.c_big, C, 0xff); AL(H.P.big_cav, BIG_ENTRIES, 0); AL(H.P.big_bnd, BIG_ENTRIES, 0);
-  AL(H.P.big_hash, BIG_HASH, 0xff); AL(H.P.lane, LANES_A + LANES_B, 0x7f);
+  AL(H.P.big_hash, BIG_HASH, 0xff); AL(H.P.big_val, BIG_HASH, 0xff); AL(H.P.lane, LANES_A + LANES_B, 0x7f);
   AL(H.P.c_state, C, 0); AL(H.P.c_final, C, 0); AL(H.P.c_extra, C, 0); AL(H.P.c_offT, C, 0);
   AL(H.P.c_offV, C, 0); AL(H.P.c_base, C, 0);
   AL(H.P.blk, 2 * H.G, 0);

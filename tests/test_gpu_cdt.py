@@ -1,4 +1,4 @@
-"""GPU initial CDT (Algorithm 1 line 1) against the oracle: the CDT is unique
+"""GPU initial CDT (first step of Algorithm 1) against the oracle: the CDT is unique
 under simulation of simplicity, so the triangle sets must be identical."""
 import numpy as np
 import pytest

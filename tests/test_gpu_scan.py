@@ -1,4 +1,4 @@
-"""Scan and splitting points (Algorithm 1 lines 3 and 5): the bad-triangle
+"""Scan and splitting points (the scan and the splitting points of Algorithm 1): the bad-triangle
 test, the circumcentre / midpoint and the priority measure bits are
 bit-identical to the oracle's fixed-order FP64 formulas."""
 import math

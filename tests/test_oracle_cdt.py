@@ -1,4 +1,4 @@
-"""Pins for the oracle's CDT (Sec. 4 definition; Algorithm 1, line 1)."""
+"""Pins for the oracle's CDT (Sec. 4 definition; the first step of Algorithm 1)."""
 import math
 import random
 
