@@ -48,7 +48,7 @@ GROW_BYTES = {"candidate": 134, "walk_step": 56, "cavity_tri": 84, "boundary_edg
 GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
 # the kernels of one refinement iteration (launched once per iteration, so an ncu
 # launch list counts them in every step and their shares compare directly)
-REFINE_KERNELS = ("k_scan_count", "k_scan_write", "k_grow_w<0>", "k_grow_t<0>", "k_grow_big<0>", "k_survive",
+REFINE_KERNELS = ("k_scan_eval", "k_scan_count", "k_scan_write", "k_grow_w<0>", "k_grow_t<0>", "k_grow_big<0>", "k_survive",
                   "k_depend", "k_insert_w<0>", "k_insert_t<0>", "k_link<0>")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cavity_growth_mid_traffic.md")
 

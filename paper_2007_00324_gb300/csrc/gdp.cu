@@ -625,6 +625,7 @@ int PoolHost::launch_flip_passes() {
     LAUNCH(*this, k_flip_link, G, Q);
     LAUNCH_B(*this, k_fl_next, 1, 1, Q);
   }
+  LAUNCH_B(*this, k_flip_tail, 1, FLIP_TAIL_THREADS, flip_pool(true));
   CK(cudaGetLastError());
   return GDP_OK;
 }
@@ -728,7 +729,8 @@ int PoolHost::build_split_graph(cudaGraphExec_t* out) {
         fail(GDP_ERR_CUDA);
         break;
       }
-      // the flip loop's body: two passes (the list ends in flA again) and the condition
+      // the flip loop's body: two passes (the list ends in flA again), the
+      // single-block tail for a short list, and the condition
       stream = cs2;
       if (cudaStreamBeginCaptureToGraph(cs2, fbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
           cudaSuccess) {
@@ -743,6 +745,7 @@ int PoolHost::build_split_graph(cudaGraphExec_t* out) {
         LAUNCH(*this, k_flip_link, G, F);
         LAUNCH_B(*this, k_fl_next, 1, 1, F);
       }
+      LAUNCH_B(*this, k_flip_tail, 1, FLIP_TAIL_THREADS, flip_pool(true));
       LAUNCH_B(*this, k_flip_cond, 1, 1, P, hf);
       if (cudaStreamEndCapture(cs2, &fbody) != cudaSuccess) fail(GDP_ERR_CUDA);
       stream = cs;
@@ -803,8 +806,8 @@ int PoolHost::insert_rounds(int stop_cons, int* rounds_out, bool split) {
       CK(cudaGraphLaunch(split_graph, stream));
       if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
       if (hctrl->err) return hctrl->err;
-      // kernels run: 27 per round pair, 9 per flip loop iteration
-      launches += 27LL * (hctrl->guard_r + 1) + 9LL * hctrl->guard_f;
+      // kernels run: 27 per round pair, 10 per flip loop iteration
+      launches += 27LL * (hctrl->guard_r + 1) + 10LL * hctrl->guard_f;
       last = hctrl->n_pts;
     }
     while (!use_graph && hctrl->n_pts > 0) {
@@ -1028,6 +1031,7 @@ int PoolHost::build_cdt() {
 
 // one refinement iteration; k = its position in the graph (event pair)
 int PoolHost::launch_iteration(int k) {
+  LAUNCH(*this, k_scan_eval, G, P);
   LAUNCH(*this, k_scan_count, G, P);
   if (capped) {
     LAUNCH(*this, k_cap_select, G, P);

@@ -279,8 +279,8 @@ __global__ void k_cdt_next(Pool P) {
 // rewritten (tstamp == pass) and writes back the others.
 
 // push t for the next flip pass once (pass = the pass that will read it)
-__device__ __forceinline__ void fl_push(const Pool& P, int t, int pass) {
-  if (atomicMax(&P.lstamp[t], pass) < pass) P.fl_nxt[atomicAdd(&P.ctrl->n_fl_next, 1)] = t;
+__device__ __forceinline__ void fl_push(const Pool& P, int* list, int t, int pass) {
+  if (atomicMax(&P.lstamp[t], pass) < pass) list[atomicAdd(&P.ctrl->n_fl_next, 1)] = t;
 }
 
 // per-mesh candidate ranges and slot counts (two new triangles per split),
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(BS) k_split(Pool P) {
       P.N[s[e]] = make_int4(comp(N4, e), (s[mod3(e + 1)] << 2) | 2, (s[mod3(e + 2)] << 2) | 1, 0);
       P.newref[(t << 2) | e] = s[e] << 2;
       P.tstamp[s[e]] = step;
-      fl_push(P, s[e], step + 1);
+      fl_push(P, P.fl_nxt, s[e], step + 1);
     }
     P.loc[v] = -1;
   }
@@ -389,80 +389,70 @@ __device__ __forceinline__ unsigned long long flip_key(const Pool& P, int step, 
 
 // each listed triangle proposes its first edge whose opposite vertex lies in
 // its circumcircle; the proposal marks both triangles (atomicMax)
-__global__ void __launch_bounds__(BS) k_flip_propose(Pool P) {
-  const int n = P.ctrl->n_fl;
-  const int step = P.ctrl->step;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int k = gt; k < n; k += gs) {
-    const int t = P.fl_cur[k];
-    const int4 T4 = P.T[t];
-    const int4 N4 = P.N[t];
-    int prop = -1, t2 = -1;
-    const P2 a = pt(P, T4.x), b = pt(P, T4.y), c = pt(P, T4.z);
-    for (int e = 0; e < 3 && prop < 0; ++e) {
-      const int r = comp(N4, e);
-      if (r < 0) continue;
-      const int d = comp(P.T[r >> 2], r & 3);
-      if (incircle(a, b, c, pt(P, d)) > 0) {
-        prop = (t << 2) | e;
-        t2 = r >> 2;
-      }
+__device__ __forceinline__ void flip_propose_one(const Pool& P, const int* cur, int k, int step) {
+  const int t = cur[k];
+  const int4 T4 = P.T[t];
+  const int4 N4 = P.N[t];
+  int prop = -1, t2 = -1;
+  const P2 a = pt(P, T4.x), b = pt(P, T4.y), c = pt(P, T4.z);
+  for (int e = 0; e < 3 && prop < 0; ++e) {
+    const int r = comp(N4, e);
+    if (r < 0) continue;
+    const int d = comp(P.T[r >> 2], r & 3);
+    if (incircle(a, b, c, pt(P, d)) > 0) {
+      prop = (t << 2) | e;
+      t2 = r >> 2;
     }
-    P.fprop[k] = prop;
-    if (prop >= 0) {
-      const unsigned long long key = flip_key(P, step, t, prop);
-      atomicMax(&P.mark[t], key);
-      atomicMax(&P.mark[t2], key);
-    }
+  }
+  P.fprop[k] = prop;
+  if (prop >= 0) {
+    const unsigned long long key = flip_key(P, step, t, prop);
+    atomicMax(&P.mark[t], key);
+    atomicMax(&P.mark[t2], key);
   }
 }
 
 // proposals that own both marks flip; the others try again next pass
-__global__ void __launch_bounds__(BS) k_flip_do(Pool P) {
-  const int n = P.ctrl->n_fl;
-  const int step = P.ctrl->step;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int k = gt; k < n; k += gs) {
-    const int prop = P.fprop[k];
-    if (prop < 0) continue;
-    const int t = prop >> 2, e = prop & 3;
-    const unsigned long long key = flip_key(P, step, t, prop);
-    // t and t2 are read only once this proposal owns them: a triangle whose
-    // mark another proposal holds may be rewritten by it meanwhile
-    if (P.mark[t] != key) {
-      fl_push(P, t, step + 1);
-      continue;
-    }
-    const int4 T4 = P.T[t];
-    const int4 N4 = P.N[t];
-    const int r = comp(N4, e);
-    const int t2 = r >> 2, e2 = r & 3;
-    if (P.mark[t2] != key) {
-      fl_push(P, t, step + 1);
-      continue;
-    }
-    const int4 U4 = P.T[t2];
-    const int4 M4 = P.N[t2];
-    const int a = comp(T4, e), b = comp(T4, mod3(e + 1)), c = comp(T4, mod3(e + 2));
-    const int d = comp(U4, e2);
-    const int nab = comp(N4, mod3(e + 2)), nca = comp(N4, mod3(e + 1));
-    const int nbd = comp(M4, mod3(e2 + 1)), ndc = comp(M4, mod3(e2 + 2));
-    const int info = T4.w & ~15;
-    // (a, b, c) + (d, c, b) -> (a, b, d) + (a, d, c)
-    P.T[t] = make_int4(a, b, d, info);
-    P.N[t] = make_int4(nbd, (t2 << 2) | 2, nab, 0);
-    P.T[t2] = make_int4(a, d, c, info);
-    P.N[t2] = make_int4(ndc, nca, (t << 2) | 1, 0);
-    P.newref[(t << 2) | mod3(e + 2)] = (t << 2) | 2;      // ab
-    P.newref[(t << 2) | mod3(e + 1)] = (t2 << 2) | 1;     // ca
-    P.newref[(t2 << 2) | mod3(e2 + 1)] = t << 2;          // bd
-    P.newref[(t2 << 2) | mod3(e2 + 2)] = t2 << 2;         // dc
-    P.tstamp[t] = step;
-    P.tstamp[t2] = step;
-    P.fprop[k] = -2 - prop;
-    fl_push(P, t, step + 1);
-    fl_push(P, t2, step + 1);
+__device__ __forceinline__ void flip_do_one(const Pool& P, int* nxt, int k, int step) {
+  const int prop = P.fprop[k];
+  if (prop < 0) return;
+  const int t = prop >> 2, e = prop & 3;
+  const unsigned long long key = flip_key(P, step, t, prop);
+  // t and t2 are read only once this proposal owns them: a triangle whose
+  // mark another proposal holds may be rewritten by it meanwhile
+  if (__ldcg(&P.mark[t]) != key) {
+    fl_push(P, nxt, t, step + 1);
+    return;
   }
+  const int4 T4 = P.T[t];
+  const int4 N4 = P.N[t];
+  const int r = comp(N4, e);
+  const int t2 = r >> 2, e2 = r & 3;
+  if (__ldcg(&P.mark[t2]) != key) {
+    fl_push(P, nxt, t, step + 1);
+    return;
+  }
+  const int4 U4 = P.T[t2];
+  const int4 M4 = P.N[t2];
+  const int a = comp(T4, e), b = comp(T4, mod3(e + 1)), c = comp(T4, mod3(e + 2));
+  const int d = comp(U4, e2);
+  const int nab = comp(N4, mod3(e + 2)), nca = comp(N4, mod3(e + 1));
+  const int nbd = comp(M4, mod3(e2 + 1)), ndc = comp(M4, mod3(e2 + 2));
+  const int info = T4.w & ~15;
+  // (a, b, c) + (d, c, b) -> (a, b, d) + (a, d, c)
+  P.T[t] = make_int4(a, b, d, info);
+  P.N[t] = make_int4(nbd, (t2 << 2) | 2, nab, 0);
+  P.T[t2] = make_int4(a, d, c, info);
+  P.N[t2] = make_int4(ndc, nca, (t << 2) | 1, 0);
+  P.newref[(t << 2) | mod3(e + 2)] = (t << 2) | 2;      // ab
+  P.newref[(t << 2) | mod3(e + 1)] = (t2 << 2) | 1;     // ca
+  P.newref[(t2 << 2) | mod3(e2 + 1)] = t << 2;          // bd
+  P.newref[(t2 << 2) | mod3(e2 + 2)] = t2 << 2;         // dc
+  P.tstamp[t] = step;
+  P.tstamp[t2] = step;
+  P.fprop[k] = -2 - prop;
+  fl_push(P, nxt, t, step + 1);
+  fl_push(P, nxt, t2, step + 1);
 }
 
 __device__ __forceinline__ void flip_fix(const Pool& P, int x, int idx, int step) {
@@ -472,20 +462,77 @@ __device__ __forceinline__ void flip_fix(const Pool& P, int x, int idx, int step
   else *comp_ptr(&P.N[r >> 2], r & 3) = (x << 2) | idx;
 }
 
-// outer neighbours of the flipped pairs
+// outer neighbours of a flipped pair
+__device__ __forceinline__ void flip_link_one(const Pool& P, int k, int step) {
+  const int f = P.fprop[k];
+  if (f > -2) return;
+  const int t = (-2 - f) >> 2;
+  const int t2 = P.N[t].y >> 2;
+  flip_fix(P, t, 0, step);
+  flip_fix(P, t, 2, step);
+  flip_fix(P, t2, 0, step);
+  flip_fix(P, t2, 1, step);
+}
+
+__global__ void __launch_bounds__(BS) k_flip_propose(Pool P) {
+  const int n = P.ctrl->n_fl;
+  const int step = P.ctrl->step;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int k = gt; k < n; k += gs) flip_propose_one(P, P.fl_cur, k, step);
+}
+
+__global__ void __launch_bounds__(BS) k_flip_do(Pool P) {
+  const int n = P.ctrl->n_fl;
+  const int step = P.ctrl->step;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int k = gt; k < n; k += gs) flip_do_one(P, P.fl_nxt, k, step);
+}
+
 __global__ void __launch_bounds__(BS) k_flip_link(Pool P) {
   const int n = P.ctrl->n_fl;
   const int step = P.ctrl->step;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int k = gt; k < n; k += gs) {
-    const int f = P.fprop[k];
-    if (f > -2) continue;
-    const int t = (-2 - f) >> 2;
-    const int t2 = P.N[t].y >> 2;
-    flip_fix(P, t, 0, step);
-    flip_fix(P, t, 2, step);
-    flip_fix(P, t2, 0, step);
-    flip_fix(P, t2, 1, step);
+  for (int k = gt; k < n; k += gs) flip_link_one(P, k, step);
+}
+
+// The last flip passes of a round in one block: while the list is short, a
+// pass costs three block barriers instead of four kernel launches.  Passes
+// go in pairs (P.fl_cur -> P.fl_nxt -> P.fl_cur), so the list ends where the
+// launched passes expect it; a list that grows past FLIP_TAIL meanwhile is
+// still finished here, and after FLIP_TAIL_PAIRS pairs the launched passes
+// and the loop's condition (bounded) take over.  Same keys, marks and steps
+// as the launched passes, so the same flips.
+constexpr int FLIP_TAIL = 4096;
+constexpr int FLIP_TAIL_THREADS = 512;
+constexpr int FLIP_TAIL_PAIRS = 64;
+__global__ void __launch_bounds__(FLIP_TAIL_THREADS) k_flip_tail(Pool P) {
+  __shared__ int s_n, s_step;
+  Ctrl* C = P.ctrl;
+  if (threadIdx.x == 0) {
+    s_n = C->n_fl;
+    s_step = C->step;
+  }
+  __syncthreads();
+  if (s_n == 0 || s_n > FLIP_TAIL) return;
+  for (int pass = 0; pass < 2 * FLIP_TAIL_PAIRS; ++pass) {
+    const int n = s_n, step = s_step;
+    if (n == 0 && (pass & 1) == 0) break;
+    const int* cur = (pass & 1) ? P.fl_nxt : P.fl_cur;
+    int* nxt = (pass & 1) ? P.fl_cur : P.fl_nxt;
+    for (int k = threadIdx.x; k < n; k += FLIP_TAIL_THREADS) flip_propose_one(P, cur, k, step);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += FLIP_TAIL_THREADS) flip_do_one(P, nxt, k, step);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += FLIP_TAIL_THREADS) flip_link_one(P, k, step);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int nn = atomicExch(&C->n_fl_next, 0);
+      C->n_fl = nn;
+      C->step = step + 1;
+      s_n = nn;
+      s_step = step + 1;
+    }
+    __syncthreads();
   }
 }
 

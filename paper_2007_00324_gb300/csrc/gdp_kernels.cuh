@@ -1,8 +1,8 @@
 // Kernels of the parallel refinement loop (Algorithm 1) and of the GPU CDT.
 //
-// One refinement iteration of Algorithm 1 is eight launches, all
-// over the whole pool (every mesh of a batch at once, Rule 4):
-//   k_scan_count / k_scan_write   the scan: changed triangles are checked for
+// One refinement iteration of Algorithm 1 is a fixed sequence of launches,
+// all over the whole pool (every mesh of a batch at once, Rule 4):
+//   k_scan_eval / _count / _write the scan: changed triangles are checked for
 //                                 encroached subsegments and bad quality and the
 //                                 hits are compacted, in slot order, into the
 //                                 candidate list (block counts + block scans;
@@ -316,8 +316,10 @@ __device__ __forceinline__ void clear_prev_marks(const Pool& P) {
 
 __global__ void __launch_bounds__(BS) k_clear_marks(Pool P) { clear_prev_marks(P); }
 
-__global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
-  __shared__ int sm[33];
+// Evaluation of the changed triangles, interleaved over the whole grid (new
+// triangles sit together at the end of a mesh's slots, so contiguous chunks
+// would leave their evaluation to a few blocks); every slot's flag is written.
+__global__ void __launch_bounds__(BS) k_scan_eval(Pool P) {
   clear_prev_marks(P);
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int m = gt; m < P.n_mesh; m += gs) {
@@ -325,29 +327,32 @@ __global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
     P.mi[m].last_cand = -1;
     P.mi[m].pending = 0;
   }
-  const Chunk ch = chunk_of(scan_slots(P));
-  int cnt = 0;
-  for (int base = ch.b0; base < ch.b1; base += BS) {
-    const int t = base + threadIdx.x;
-    if (t < ch.b1) {
-      int code = 0;
-      if (P.dirty[t]) {
-        P.dirty[t] = 0;
-        code = eval_tri(P, t);
-        if (code) {
-          const int4 T4 = P.T[t];
-          const int m = T4.w >> 4;
-          if (P.mi[m].cand_cap > 0) {
-            const int b = cap_bucket(P, T4, code);
-            P.cbucket[t] = (uint16_t)b;
-            atomicAdd(&P.cap_hist[(size_t)m * CAP_BUCKETS + b], 1);
-          }
+  const int ns = scan_slots(P);
+  for (int t = gt; t < ns; t += gs) {
+    int code = 0;
+    if (P.dirty[t]) {
+      P.dirty[t] = 0;
+      code = eval_tri(P, t);
+      if (code) {
+        const int4 T4 = P.T[t];
+        const int m = T4.w >> 4;
+        if (P.mi[m].cand_cap > 0) {
+          const int b = cap_bucket(P, T4, code);
+          P.cbucket[t] = (uint16_t)b;
+          atomicAdd(&P.cap_hist[(size_t)m * CAP_BUCKETS + b], 1);
         }
       }
-      P.flag[t] = (uint8_t)code;
-      cnt += code != 0;
     }
+    P.flag[t] = (uint8_t)code;
   }
+}
+
+// flagged slots per block chunk (the stable compaction's block counts)
+__global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
+  __shared__ int sm[33];
+  const Chunk ch = chunk_of(scan_slots(P));
+  int cnt = 0;
+  for (int t = ch.b0 + threadIdx.x; t < ch.b1; t += BS) cnt += P.flag[t] != 0;
   cnt = block_sum(cnt, sm);
   if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
 }
