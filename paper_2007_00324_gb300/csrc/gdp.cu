@@ -887,7 +887,7 @@ int PoolHost::build_cdt() {
     if (st0 != GDP_OK) return st0;
   }
   LAUNCH(*this, k_cdt_bbox, mesh_grid, P, part);
-  LAUNCH(*this, k_cdt_init, n_mesh, P, part, (int)mesh_grid.x);
+  LAUNCH(*this, k_cdt_init, n_mesh, P, part, (int)mesh_grid.x, env_double("GDP_FRAME_MARGIN", 16.0));
   LAUNCH(*this, k_cdt_vf, mesh_grid, P);
   release(part);
   CK(cudaGetLastError());

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(BS) k_cdt_bbox(Pool P, double* part) {
   }
 }
 
-__global__ void k_cdt_init(Pool P, const double* part, int bx) {
+__global__ void k_cdt_init(Pool P, const double* part, int bx, double frame) {
   const int m = blockIdx.x;
   MeshInfo& M = P.mi[m];
   if (threadIdx.x == 0) {
@@ -87,7 +87,7 @@ __global__ void k_cdt_init(Pool P, const double* part, int bx) {
     // frame 16 D out (inside the enclosing triangle): far enough that few
     // Delaunay edges from interior points to the frame cross the input's
     // hull, so boundary segments are mostly edges already
-    const double d = 16.0 * D;
+    const double d = frame * D;
     P.V[s0 + 3] = make_double2(x0 - d, y0 - d);
     P.V[s0 + 4] = make_double2(x1 + d, y0 - d);
     P.V[s0 + 5] = make_double2(x1 + d, y1 + d);

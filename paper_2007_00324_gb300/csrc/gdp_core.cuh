@@ -6,7 +6,8 @@
 //   N[t]   int4  (n0, n1, n2, -)      neighbour across edge e as (tri << 2 | edge), -1 none
 //   mark[t] u64                       cavity priority mark (Sec. 5.2 atomic marks)
 //   newref[4t+e] int32                the new triangle that replaced edge e of t (this iteration)
-//   dirty[t] u8                       triangle changed since its last quality check
+//   dirty[t] u8                       1: triangle changed since its last quality check;
+//                                     2 + code: unchanged, code carried over
 //   V[v]   double2                    vertex coordinates (FP64)
 //   vseg[v] int32                     input segment a Steiner vertex lies on, else -1
 // Per-candidate scratch (one candidate = one splitting point of Algorithm 1):
@@ -87,6 +88,7 @@ struct Ctrl {
   unsigned long long n_grown, sum_cav, sum_bnd, sum_walk;
   // the same for the launches timed with CUDA events (GDP_REFINE_TIME_GROW)
   unsigned long long t_grown, t_cav, t_bnd, t_walk;
+  int32_t grow_next;     // k_grow_t: next candidate to hand out
 };
 
 struct Pool {

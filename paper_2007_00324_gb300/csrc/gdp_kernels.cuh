@@ -319,6 +319,26 @@ __global__ void __launch_bounds__(BS) k_clear_marks(Pool P) { clear_prev_marks(P
 // Evaluation of the changed triangles, interleaved over the whole grid (new
 // triangles sit together at the end of a mesh's slots, so contiguous chunks
 // would leave their evaluation to a few blocks); every slot's flag is written.
+// code of slot t whose dirty byte is d (nonzero); the cap histogram entry
+__device__ __forceinline__ int scan_one(const Pool& P, int t, int d) {
+  int code;
+  if (d == 1) {
+    code = eval_tri(P, t);
+  } else if ((code = d - 2) != 0 && !P.mi[P.T[t].w >> 4].active) {
+    code = 0;   // a code carried over (recheck_elem) of a mesh that stopped
+  }
+  if (code) {
+    const int4 T4 = P.T[t];
+    const int m = T4.w >> 4;
+    if (P.mi[m].cand_cap > 0) {
+      const int b = cap_bucket(P, T4, code);
+      P.cbucket[t] = (uint16_t)b;
+      atomicAdd(&P.cap_hist[(size_t)m * CAP_BUCKETS + b], 1);
+    }
+  }
+  return code;
+}
+
 __global__ void __launch_bounds__(BS) k_scan_eval(Pool P) {
   clear_prev_marks(P);
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
@@ -327,32 +347,54 @@ __global__ void __launch_bounds__(BS) k_scan_eval(Pool P) {
     P.mi[m].last_cand = -1;
     P.mi[m].pending = 0;
   }
+  // one slot per thread and step: the changed triangles sit together (the
+  // new ones at the end of each mesh's slots), and spreading them over all
+  // threads beats fewer, wider loads
   const int ns = scan_slots(P);
   for (int t = gt; t < ns; t += gs) {
+    const int d = P.dirty[t];
     int code = 0;
-    if (P.dirty[t]) {
+    if (d) {
       P.dirty[t] = 0;
-      code = eval_tri(P, t);
-      if (code) {
-        const int4 T4 = P.T[t];
-        const int m = T4.w >> 4;
-        if (P.mi[m].cand_cap > 0) {
-          const int b = cap_bucket(P, T4, code);
-          P.cbucket[t] = (uint16_t)b;
-          atomicAdd(&P.cap_hist[(size_t)m * CAP_BUCKETS + b], 1);
-        }
-      }
+      code = scan_one(P, t, d);
     }
     P.flag[t] = (uint8_t)code;
   }
 }
 
+// The compaction's chunk of this block: whole groups of eight slots (flags
+// are read eight at a time), the last chunk ending at ns.
+__device__ __forceinline__ Chunk scan_chunk(int ns) {
+  const int ngr = (ns + 7) >> 3;
+  const int c = (ngr + gridDim.x - 1) / gridDim.x;
+  const int g0 = min(ngr, (int)blockIdx.x * c);
+  return {min(ns, 8 * g0), min(ns, 8 * (g0 + c))};
+}
+
+// flags of the eight slots from t0 (a multiple of 8), zero from ns on
+__device__ __forceinline__ uint2 flags8(const Pool& P, int t0, int ns) {
+  if (t0 + 8 <= ns) return reinterpret_cast<const uint2*>(P.flag)[t0 >> 3];
+  unsigned lo = 0u, hi = 0u;
+  for (int k = 0; t0 + k < ns; ++k) {
+    const unsigned f = P.flag[t0 + k];
+    if (k < 4) lo |= f << (8 * k);
+    else hi |= f << (8 * (k - 4));
+  }
+  return make_uint2(lo, hi);
+}
+
+__device__ __forceinline__ int nz_bytes(unsigned w) { return __popc(__vcmpne4(w, 0u)) >> 3; }
+
 // flagged slots per block chunk (the stable compaction's block counts)
 __global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
   __shared__ int sm[33];
-  const Chunk ch = chunk_of(scan_slots(P));
+  const int ns = scan_slots(P);
+  const Chunk ch = scan_chunk(ns);
   int cnt = 0;
-  for (int t = ch.b0 + threadIdx.x; t < ch.b1; t += BS) cnt += P.flag[t] != 0;
+  for (int t0 = ch.b0 + 8 * threadIdx.x; t0 < ch.b1; t0 += 8 * BS) {
+    const uint2 f = flags8(P, t0, ns);
+    cnt += nz_bytes(f.x) + nz_bytes(f.y);
+  }
   cnt = block_sum(cnt, sm);
   if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
 }
@@ -385,7 +427,7 @@ __global__ void __launch_bounds__(BS) k_cap_select(Pool P) {
 // iteration (flag cleared, slot dirty again); block counts for k_scan_write
 __global__ void __launch_bounds__(BS) k_cap_count(Pool P) {
   __shared__ int sm[33];
-  const Chunk ch = chunk_of(scan_slots(P));
+  const Chunk ch = scan_chunk(scan_slots(P));
   int cnt = 0;
   for (int t = ch.b0 + threadIdx.x; t < ch.b1; t += BS) {
     if (!P.flag[t]) continue;
@@ -404,21 +446,29 @@ __global__ void __launch_bounds__(BS) k_cap_count(Pool P) {
 
 __global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
   __shared__ int sm[33];
-  const Chunk ch = chunk_of(scan_slots(P));
+  const int ns = scan_slots(P);
+  const Chunk ch = scan_chunk(ns);
   int off = block_prefix(P.blk, blockIdx.x, sm);
   const int cap = P.cap_cand;
-  for (int base = ch.b0; base < ch.b1; base += BS) {
-    const int t = base + threadIdx.x;
-    const int code = t < ch.b1 ? P.flag[t] : 0;
+  for (int base = ch.b0; base < ch.b1; base += 8 * BS) {
+    const int t0 = base + 8 * threadIdx.x;
+    const uint2 f = t0 < ch.b1 ? flags8(P, t0, ns) : make_uint2(0u, 0u);
+    const int c = nz_bytes(f.x) + nz_bytes(f.y);
     int tot;
-    const int r = block_excl_scan(code != 0, sm, tot);
-    if (code) {
-      const int rank = off + r;
-      if (rank < cap) {
-        P.c_elem[rank] = (t << 2) | (code == 4 ? 3 : code - 1);
-      } else {
-        P.dirty[t] = 1;   // over the per-iteration capacity: retried next iteration
-        P.mi[P.T[t].w >> 4].pending = 1;
+    const int r = block_excl_scan(c, sm, tot);
+    if (c) {
+      int rank = off + r;
+      for (int k = 0; k < 8; ++k) {
+        const int code = (int)(((k < 4 ? f.x : f.y) >> (8 * (k & 3))) & 0xffu);
+        if (!code) continue;
+        const int t = t0 + k;
+        if (rank < cap) {
+          P.c_elem[rank] = (t << 2) | (code == 4 ? 3 : code - 1);
+        } else {
+          P.dirty[t] = 1;   // over the per-iteration capacity: retried next iteration
+          P.mi[P.T[t].w >> 4].pending = 1;
+        }
+        ++rank;
       }
     }
     off += tot;
@@ -876,6 +926,7 @@ __global__ void __maxnreg__(128) k_grow_w(Pool P, int timed) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n = P.ctrl->n_cand;
   int* wc = wcs[wib];
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->grow_next = 0;   // k_grow_t's counter
   if (n > P.warp_max) return;   // k_grow_t's case
   GrowAcc acc;
   for (int i = gw; i < n; i += nw) {
@@ -920,14 +971,25 @@ __global__ void __maxnreg__(128) k_grow_w(Pool P, int timed) {
 
 // the same, one thread per candidate, when there are more than
 // P.warp_max candidates (a separate kernel keeps each version's register
-// allocation to itself)
+// allocation to itself).  Warps take runs of 32 candidates from a counter
+// (reset by k_grow_w, launched just before), so that the uneven per-candidate
+// work (walks, cavity sizes) does not leave SMs idle at the end.
+#ifndef GDP_GROW_T_REGS
+#define GDP_GROW_T_REGS 128
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(BS) k_grow_t(Pool P, int timed) {
+__global__ void __maxnreg__(GDP_GROW_T_REGS) k_grow_t(Pool P, int timed) {
   const int n = P.ctrl->n_cand;
   if (n <= P.warp_max) return;   // k_grow_w's case
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
   GrowAcc acc;
-  for (int i = gt; i < n; i += gs) {
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&P.ctrl->grow_next, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n) break;
+    const int i = base + lane;
+    if (i >= n) continue;
     P.c_big[i] = -1;
     const CavBuf B{P.c_cav + (size_t)i * CMAX, P.c_bnd + (size_t)i * BMAX, nullptr, CMAX, 0};
     if (grow_cand<MODE>(P, i, B, acc) == G_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
@@ -1239,6 +1301,19 @@ __device__ __forceinline__ bool replaced(const Pool& P, int ref, int n) {
   return j < n && P.c_final[j];
 }
 
+// The element of candidate i is looked at again next iteration whatever
+// happens (its splitting point may have moved to a subsegment, or lost).  If
+// an inserted cavity took its slot, the new triangle there is evaluated as
+// every new one is (dirty = 1).  Otherwise the triangle is unchanged, and its
+// code -- a function of its vertices and of fixed per-mesh data only -- is
+// carried over without evaluating it again (dirty = 2 + this iteration's
+// flag).  Meshes out of memory insert nothing: their elements are evaluated.
+__device__ __forceinline__ void recheck_elem(const Pool& P, int i, int n, bool ok) {
+  const int t = P.c_elem[i] >> 2;
+  if (!ok) P.dirty[t] = 1;
+  else if (!replaced(P, t << 2, n)) P.dirty[t] = (uint8_t)(2 + P.flag[t]);
+}
+
 // ---------------------------------------------------------------- spill-tier cavities, one warp each
 // Cavities of the spill tiers have hundreds to tens of thousands of triangles.
 // The thread-per-candidate kernels hand them to their whole warp (ballot, then
@@ -1383,9 +1458,7 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
         P.mi[m].ins_ok = ok ? 1 : 0;
         if (!ok) P.mi[m].status = S_NOMEM;
       }
-      // the element is re-checked whatever happens: it may be untouched when its
-      // splitting point moved to a subsegment, or when the point was not inserted
-      if (MODE == 0) P.dirty[P.c_elem[i] >> 2] = 1;
+      if (MODE == 0) recheck_elem(P, i, n, ok);
       if (P.c_final[i] && ok) {
         base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
         vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
@@ -1470,8 +1543,7 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
         P.mi[m].ins_ok = ok ? 1 : 0;
         if (!ok) P.mi[m].status = S_NOMEM;
       }
-      // the element is re-checked whatever happens
-      if (MODE == 0) P.dirty[P.c_elem[i] >> 2] = 1;
+      if (MODE == 0) recheck_elem(P, i, n, ok);
     }
     if (!P.c_final[i] || !ok) continue;
     const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
