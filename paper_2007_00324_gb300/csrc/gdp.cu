@@ -1032,12 +1032,12 @@ int PoolHost::build_cdt() {
 // one refinement iteration; k = its position in the graph (event pair)
 int PoolHost::launch_iteration(int k) {
   LAUNCH(*this, k_scan_eval, G, P);
-  LAUNCH(*this, k_scan_count, G, P);
+  LAUNCH(*this, k_scan_count, G, P, capped ? 1 : 0);
   if (capped) {
     LAUNCH(*this, k_cap_select, G, P);
     LAUNCH(*this, k_cap_count, G, P);
   }
-  LAUNCH(*this, k_scan_write, G, P);
+  LAUNCH(*this, k_scan_write, G, P, capped ? 1 : 0);
   // the first iteration of each replay is timed (events in the graph stall
   // the pipeline, so not every one): its growth work is counted apart
   const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -1087,8 +1087,10 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   }
   if (push_mi() != GDP_OK) return GDP_ERR_CUDA;
   std::memset(hctrl, 0, sizeof(Ctrl));
+  hctrl->need_eval = 1;   // every triangle is evaluated with this call's bounds
   CK(cudaMemcpyAsync(P.ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
   CK(cudaEventRecord(ev0, stream));
+  LAUNCH(*this, k_mark_all, G, P);
   int status = GDP_OK;
   time_grow = (d.flags & GDP_REFINE_TIME_GROW) != 0;
   capped = d.cand_cap > 0;

@@ -1084,6 +1084,7 @@ __global__ void __launch_bounds__(BS) k_compact_finish(Pool P, const int4* T2, c
       P.N[t] = make_int4(-1, -1, -1, -1);
       P.dirty[t] = 0;
     }
+    P.flag[t] = 0;
     P.mark[t] = 0ull;
   }
 }

@@ -6,8 +6,9 @@
 //   N[t]   int4  (n0, n1, n2, -)      neighbour across edge e as (tri << 2 | edge), -1 none
 //   mark[t] u64                       cavity priority mark (Sec. 5.2 atomic marks)
 //   newref[4t+e] int32                the new triangle that replaced edge e of t (this iteration)
-//   dirty[t] u8                       1: triangle changed since its last quality check;
-//                                     2 + code: unchanged, code carried over
+//   dirty[t] u8                       triangle not yet evaluated (construction, relocation)
+//   flag[t] u8                        its code: 0 good, 1-3 encroached edge + 1, 4 bad;
+//                                     persists until the slot is rewritten
 //   V[v]   double2                    vertex coordinates (FP64)
 //   vseg[v] int32                     input segment a Steiner vertex lies on, else -1
 // Per-candidate scratch (one candidate = one splitting point of Algorithm 1):
@@ -89,6 +90,7 @@ struct Ctrl {
   // the same for the launches timed with CUDA events (GDP_REFINE_TIME_GROW)
   unsigned long long t_grown, t_cav, t_bnd, t_walk;
   int32_t grow_next;     // k_grow_t: next candidate to hand out
+  int32_t need_eval;     // some triangles are marked dirty (construction, relocation)
 };
 
 struct Pool {

@@ -319,26 +319,11 @@ __global__ void __launch_bounds__(BS) k_clear_marks(Pool P) { clear_prev_marks(P
 // Evaluation of the changed triangles, interleaved over the whole grid (new
 // triangles sit together at the end of a mesh's slots, so contiguous chunks
 // would leave their evaluation to a few blocks); every slot's flag is written.
-// code of slot t whose dirty byte is d (nonzero); the cap histogram entry
-__device__ __forceinline__ int scan_one(const Pool& P, int t, int d) {
-  int code;
-  if (d == 1) {
-    code = eval_tri(P, t);
-  } else if ((code = d - 2) != 0 && !P.mi[P.T[t].w >> 4].active) {
-    code = 0;   // a code carried over (recheck_elem) of a mesh that stopped
-  }
-  if (code) {
-    const int4 T4 = P.T[t];
-    const int m = T4.w >> 4;
-    if (P.mi[m].cand_cap > 0) {
-      const int b = cap_bucket(P, T4, code);
-      P.cbucket[t] = (uint16_t)b;
-      atomicAdd(&P.cap_hist[(size_t)m * CAP_BUCKETS + b], 1);
-    }
-  }
-  return code;
-}
-
+// Flags persist from one iteration to the next: a triangle's code depends on
+// its vertices and on fixed per-mesh data only, and the insertion kernels
+// evaluate every triangle they create.  This pass evaluates the triangles
+// marked dirty by the construction or a relocation (Ctrl::need_eval, cleared
+// by k_scan_count) and otherwise only clears the last iteration's marks.
 __global__ void __launch_bounds__(BS) k_scan_eval(Pool P) {
   clear_prev_marks(P);
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
@@ -347,19 +332,20 @@ __global__ void __launch_bounds__(BS) k_scan_eval(Pool P) {
     P.mi[m].last_cand = -1;
     P.mi[m].pending = 0;
   }
-  // one slot per thread and step: the changed triangles sit together (the
-  // new ones at the end of each mesh's slots), and spreading them over all
-  // threads beats fewer, wider loads
+  if (!P.ctrl->need_eval) return;
   const int ns = scan_slots(P);
   for (int t = gt; t < ns; t += gs) {
-    const int d = P.dirty[t];
-    int code = 0;
-    if (d) {
-      P.dirty[t] = 0;
-      code = scan_one(P, t, d);
-    }
-    P.flag[t] = (uint8_t)code;
+    if (!P.dirty[t]) continue;
+    P.dirty[t] = 0;
+    P.flag[t] = (uint8_t)eval_tri(P, t);
   }
+}
+
+// start of a refinement: every slot is evaluated with this call's bounds
+__global__ void __launch_bounds__(BS) k_mark_all(Pool P) {
+  const int ns = scan_slots(P);
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int t = gt; t < ns; t += gs) P.dirty[t] = 1;
 }
 
 // The compaction's chunk of this block: whole groups of eight slots (flags
@@ -386,14 +372,29 @@ __device__ __forceinline__ uint2 flags8(const Pool& P, int t0, int ns) {
 __device__ __forceinline__ int nz_bytes(unsigned w) { return __popc(__vcmpne4(w, 0u)) >> 3; }
 
 // flagged slots per block chunk (the stable compaction's block counts)
-__global__ void __launch_bounds__(BS) k_scan_count(Pool P) {
+// (capped: also the priority buckets and per-mesh histograms of the flagged
+// slots of meshes with a cap)
+__global__ void __launch_bounds__(BS) k_scan_count(Pool P, int capped) {
   __shared__ int sm[33];
+  if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->need_eval = 0;   // k_scan_eval has run
   const int ns = scan_slots(P);
   const Chunk ch = scan_chunk(ns);
   int cnt = 0;
   for (int t0 = ch.b0 + 8 * threadIdx.x; t0 < ch.b1; t0 += 8 * BS) {
     const uint2 f = flags8(P, t0, ns);
     cnt += nz_bytes(f.x) + nz_bytes(f.y);
+    if (!capped || (f.x | f.y) == 0u) continue;
+    for (int k = 0; k < 8; ++k) {
+      const int code = (int)(((k < 4 ? f.x : f.y) >> (8 * (k & 3))) & 0xffu);
+      if (!code) continue;
+      const int t = t0 + k;
+      const int4 T4 = P.T[t];
+      const int m = T4.w >> 4;
+      if (P.mi[m].cand_cap <= 0) continue;
+      const int b = cap_bucket(P, T4, code);
+      P.cbucket[t] = (uint16_t)b;
+      atomicAdd(&P.cap_hist[(size_t)m * CAP_BUCKETS + b], 1);
+    }
   }
   cnt = block_sum(cnt, sm);
   if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(BS) k_cap_select(Pool P) {
 }
 
 // capped meshes: flagged elements below the threshold wait for a later
-// iteration (flag cleared, slot dirty again); block counts for k_scan_write
+// iteration (k_scan_write skips them too); block counts for k_scan_write
 __global__ void __launch_bounds__(BS) k_cap_count(Pool P) {
   __shared__ int sm[33];
   const Chunk ch = scan_chunk(scan_slots(P));
@@ -433,9 +434,7 @@ __global__ void __launch_bounds__(BS) k_cap_count(Pool P) {
     if (!P.flag[t]) continue;
     const int m = P.T[t].w >> 4;
     if (P.mi[m].cand_cap > 0 && P.cbucket[t] < P.cap_thr[m]) {
-      P.flag[t] = 0;
-      P.dirty[t] = 1;
-      P.mi[m].pending = 1;
+      P.mi[m].pending = 1;   // stays flagged for a later iteration
       continue;
     }
     ++cnt;
@@ -444,7 +443,12 @@ __global__ void __launch_bounds__(BS) k_cap_count(Pool P) {
   if (threadIdx.x == 0) P.blk[blockIdx.x] = cnt;
 }
 
-__global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
+__device__ __forceinline__ bool cap_skipped(const Pool& P, int t) {
+  const int m = P.T[t].w >> 4;
+  return P.mi[m].cand_cap > 0 && P.cbucket[t] < P.cap_thr[m];
+}
+
+__global__ void __launch_bounds__(BS) k_scan_write(Pool P, int capped) {
   __shared__ int sm[33];
   const int ns = scan_slots(P);
   const Chunk ch = scan_chunk(ns);
@@ -452,7 +456,16 @@ __global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
   const int cap = P.cap_cand;
   for (int base = ch.b0; base < ch.b1; base += 8 * BS) {
     const int t0 = base + 8 * threadIdx.x;
-    const uint2 f = t0 < ch.b1 ? flags8(P, t0, ns) : make_uint2(0u, 0u);
+    uint2 f = t0 < ch.b1 ? flags8(P, t0, ns) : make_uint2(0u, 0u);
+    if (capped && (f.x | f.y) != 0u) {   // drop the slots the cap defers
+      for (int k = 0; k < 8; ++k) {
+        const int sh = 8 * (k & 3);
+        if (((k < 4 ? f.x : f.y) >> sh) & 0xffu && cap_skipped(P, t0 + k)) {
+          if (k < 4) f.x &= ~(0xffu << sh);
+          else f.y &= ~(0xffu << sh);
+        }
+      }
+    }
     const int c = nz_bytes(f.x) + nz_bytes(f.y);
     int tot;
     const int r = block_excl_scan(c, sm, tot);
@@ -465,8 +478,7 @@ __global__ void __launch_bounds__(BS) k_scan_write(Pool P) {
         if (rank < cap) {
           P.c_elem[rank] = (t << 2) | (code == 4 ? 3 : code - 1);
         } else {
-          P.dirty[t] = 1;   // over the per-iteration capacity: retried next iteration
-          P.mi[P.T[t].w >> 4].pending = 1;
+          P.mi[P.T[t].w >> 4].pending = 1;   // over the per-iteration capacity: stays flagged
         }
         ++rank;
       }
@@ -1301,17 +1313,13 @@ __device__ __forceinline__ bool replaced(const Pool& P, int ref, int n) {
   return j < n && P.c_final[j];
 }
 
-// The element of candidate i is looked at again next iteration whatever
-// happens (its splitting point may have moved to a subsegment, or lost).  If
-// an inserted cavity took its slot, the new triangle there is evaluated as
-// every new one is (dirty = 1).  Otherwise the triangle is unchanged, and its
-// code -- a function of its vertices and of fixed per-mesh data only -- is
-// carried over without evaluating it again (dirty = 2 + this iteration's
-// flag).  Meshes out of memory insert nothing: their elements are evaluated.
-__device__ __forceinline__ void recheck_elem(const Pool& P, int i, int n, bool ok) {
-  const int t = P.c_elem[i] >> 2;
-  if (!ok) P.dirty[t] = 1;
-  else if (!replaced(P, t << 2, n)) P.dirty[t] = (uint8_t)(2 + P.flag[t]);
+// A triangle made by an insertion: refinement evaluates it at once (the
+// flag persists until its slot is rewritten); construction marks it dirty
+// (the construction's end marks every triangle dirty anyway).
+template <int MODE>
+__device__ __forceinline__ void new_tri_code(const Pool& P, int s) {
+  if (MODE == 0) P.flag[s] = (uint8_t)eval_tri(P, s);
+  else P.dirty[s] = 1;
 }
 
 // ---------------------------------------------------------------- spill-tier cavities, one warp each
@@ -1364,8 +1372,10 @@ __device__ __forceinline__ int map_find(const BigMap& M, int mask, int v) {
 // starts (x) and that ends (y) there, so every record finds its two fan
 // neighbours in O(1) -- the same ones as the quadratic search of the small
 // cavities, which keeps the last match.
+template <int MODE>
 __device__ void fan_big(const Pool& P, int i, int m, int base, int vid, int n) {
   const unsigned FULL = 0xffffffffu;
+  __syncwarp();   // the new vertex, written by one lane, is read by all
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int off = P.c_big[i];
@@ -1424,7 +1434,7 @@ __device__ void fan_big(const Pool& P, int i, int m, int base, int vid, int n) {
       P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
       P.N[s] = make_int4(n0, n1, n2, 0);
       P.newref[rec.w & 0x7fffffff] = s << 2;
-      P.dirty[s] = 1;
+      new_tri_code<MODE>(P, s);
       P.vtri[u] = s;
       P.vtri[v] = s;
       P.vtri[vid] = s;
@@ -1458,7 +1468,6 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
         P.mi[m].ins_ok = ok ? 1 : 0;
         if (!ok) P.mi[m].status = S_NOMEM;
       }
-      if (MODE == 0) recheck_elem(P, i, n, ok);
       if (P.c_final[i] && ok) {
         base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
         vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
@@ -1500,7 +1509,7 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
             P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
             P.N[s] = make_int4(n0, n1, n2, 0);
             P.newref[rec.w & 0x7fffffff] = s << 2;
-            P.dirty[s] = 1;
+            new_tri_code<MODE>(P, s);
             P.vtri[u] = s;
             P.vtri[v] = s;
             P.vtri[vid] = s;
@@ -1513,7 +1522,7 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
     while (bm) {
       const int src = __ffs(bm) - 1;
       bm &= bm - 1;
-      fan_big(P, __shfl_sync(FULL, i, src), __shfl_sync(FULL, m, src), __shfl_sync(FULL, base, src),
+      fan_big<MODE>(P, __shfl_sync(FULL, i, src), __shfl_sync(FULL, m, src), __shfl_sync(FULL, base, src),
               __shfl_sync(FULL, vid, src), n);
     }
   }
@@ -1538,12 +1547,9 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
     int totE, totV;
     mesh_totals(P, f, l, totE, totV);
     const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
-    if (lane == 0) {
-      if (i == f) {
-        P.mi[m].ins_ok = ok ? 1 : 0;
-        if (!ok) P.mi[m].status = S_NOMEM;
-      }
-      if (MODE == 0) recheck_elem(P, i, n, ok);
+    if (lane == 0 && i == f) {
+      P.mi[m].ins_ok = ok ? 1 : 0;
+      if (!ok) P.mi[m].status = S_NOMEM;
     }
     if (!P.c_final[i] || !ok) continue;
     const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
@@ -1560,8 +1566,9 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
       P.vseg[vid] = P.c_vseg[i];
       if (MODE == 1) P.loc[vid] = -1;
     }
+    __syncwarp();   // the new vertex is read by every lane (new_tri_code)
     if (nb > 64) {   // a spill-tier cavity: the map-based fan
-      fan_big(P, i, m, base, vid, n);
+      fan_big<MODE>(P, i, m, base, vid, n);
       continue;
     }
     // records lane and lane + 32; j = rank among the records that are not the split edge
@@ -1607,7 +1614,7 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
       P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
       P.N[s] = make_int4(n0, n1[h], n2[h], 0);
       P.newref[rec[h].w & 0x7fffffff] = s << 2;
-      P.dirty[s] = 1;
+      new_tri_code<MODE>(P, s);
       P.vtri[u] = s;
       P.vtri[v] = s;
       P.vtri[vid] = s;

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(BS) k_relocate(Pool D, Pool S, int ms, int md,
   const MeshInfo& Ms = S.mi[ms];
   const int st = Ms.tri_base, sv0 = Ms.vert_base, ss = Ms.seg_base, sa = Ms.adj_base;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  if (gt == 0) D.ctrl->need_eval = 1;
   for (int t = gt; t < Ms.tri_count; t += gs) {
     const int4 T4 = S.T[st + t];
     const int4 N4 = S.N[st + t];
