@@ -1090,6 +1090,9 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   hctrl->need_eval = 1;   // every triangle is evaluated with this call's bounds
   CK(cudaMemcpyAsync(P.ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
   CK(cudaEventRecord(ev0, stream));
+  // a call that stopped with candidates (iteration limit, error) leaves their
+  // marks behind: the next call starts from clean marks
+  CK(cudaMemsetAsync(P.mark, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
   LAUNCH(*this, k_mark_all, G, P);
   int status = GDP_OK;
   time_grow = (d.flags & GDP_REFINE_TIME_GROW) != 0;

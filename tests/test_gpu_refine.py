@@ -96,3 +96,31 @@ def test_iteration_limit_keeps_valid_cdt(oracle):
     assert st == gdp.ERR_ITER_LIMIT
     xy, tri, sub = g.export()
     assert_valid(oracle.check(xy, tri, sub, p.seg, p.n, brute=True), refined=False, brute=True)
+
+
+def test_second_call_uses_its_own_bound(oracle):
+    # codes persist between iterations, so a refine call must evaluate every
+    # triangle again with its own bound: a looser first call, then B = sqrt 2
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.tiny()
+    g = gdp.Mesh(p.xy, p.seg)
+    s1 = g.refine(2.0)
+    s2 = g.refine(SQ2)
+    assert s2["n_steiner"] > 0, (s1, s2)
+    xy, tri, sub = g.export()
+    assert_valid(oracle.check(xy, tri, sub, p.seg, p.n, B=SQ2, brute=True), brute=True)
+
+
+def test_stopped_call_then_finished(oracle):
+    # a call stopped by the iteration limit leaves flagged triangles behind;
+    # the next call finishes the refinement to the same bound
+    gdp = need_gpu()
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.tiny()
+    g = gdp.Mesh(p.xy, p.seg)
+    st, _ = g.refine(SQ2, max_iter=2, check=False)
+    assert st == gdp.ERR_ITER_LIMIT
+    g.refine(SQ2)
+    xy, tri, sub = g.export()
+    assert_valid(oracle.check(xy, tri, sub, p.seg, p.n, B=SQ2, brute=True), brute=True)
