@@ -50,6 +50,12 @@ static int small_pair_xy(const double* xy, const int32_t* seg, int64_t s1, int64
 int or_check(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
              const int32_t* sub, int64_t ns, const int32_t* seg_in, int64_t m,
              int64_t n_in, double B2, int brute, or_report* rep) {
+    return or_check_mode(xy, nv, tri, nt, sub, ns, seg_in, m, n_in, B2, brute, 0, rep);
+}
+
+int or_check_mode(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                  const int32_t* sub, int64_t ns, const int32_t* seg_in, int64_t m,
+                  int64_t n_in, double B2, int brute, int lens, or_report* rep) {
     memset(rep, 0, sizeof(*rep));
     rep->n_tri = nt;
     rep->n_vert = nv;
@@ -130,8 +136,10 @@ int or_check(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
                     rep->not_locally_cd++;
             }
             if (is_sub &&
-                or_dot_sign(xy[2 * u], xy[2 * u + 1], xy[2 * w], xy[2 * w + 1], xy[2 * apex],
-                            xy[2 * apex + 1]) < 0)
+                (lens ? or_lens_sign(xy[2 * u], xy[2 * u + 1], xy[2 * w], xy[2 * w + 1], xy[2 * apex],
+                                     xy[2 * apex + 1])
+                      : or_dot_sign(xy[2 * u], xy[2 * u + 1], xy[2 * w], xy[2 * w + 1], xy[2 * apex],
+                                    xy[2 * apex + 1])) < 0)
                 rep->encroached++;
         }
     }

@@ -8,7 +8,8 @@
  * What it computes, and where the paper defines it:
  *   - PSLG, triangulation, subsegment, CDT ........ Sec. 4 (definitions)
  *   - bad triangle (radius-edge ratio form) ....... Sec. 4.1 / Sec. 5.1
- *   - encroachment (diametral circle, Ruppert) .... Sec. 4.2
+ *   - encroachment (diametral circle, Ruppert;
+ *     diametral lens, Chew) ...................... Sec. 4.2
  *   - splitting points (midpoint / circumcentre) .. Sec. 4.2, Algorithm 1
  *   - priorities (midpoint first, larger first) ... Sec. 4.3
  *   - exact predicates + simulation of simplicity . Sec. 7 (set-up)
@@ -42,6 +43,9 @@ int  or_incircle(double ax, double ay, double bx, double by, double cx, double c
 int  or_incircle_sos(double ax, double ay, double bx, double by, double cx, double cy,
                      double dx, double dy);
 int  or_dot_sign(double ax, double ay, double bx, double by, double px, double py);
+/* -1: p strictly inside the diametral lens of ab (the segment subtends more
+ * than 120 degrees at p; Chew's rule, Sec. 4.2), 0: p is a or b, +1: outside */
+int  or_lens_sign(double ax, double ay, double bx, double by, double px, double py);
 int  or_lex_less(double ax, double ay, double bx, double by);
 
 /* ---------------- FP64 geometry with a fixed evaluation order (pred.c) ---- */
@@ -69,6 +73,9 @@ int      or_refine(or_mesh*, double B, int64_t max_steiner, int order);
  * a triangle whose longest edge exceeds l is refined like a bad one (the
  * small-angle exemption covers only the radius-edge test) */
 int      or_refine_len(or_mesh*, double B, double l, int64_t max_steiner, int order);
+/* the same with the encroachment region chosen: lens = 0 the diametral circle
+ * (Ruppert's rule), lens != 0 the diametral lens (Chew's rule), Sec. 4.2 */
+int      or_refine_mode(or_mesh*, double B, double l, int lens, int64_t max_steiner, int order);
 /* insert free points (strictly inside the domain, not on a subsegment) */
 int      or_insert_points(or_mesh*, const double* xy, int64_t n);
 /* split the subsegments given by endpoint coordinates (ax,ay,bx,by) at midpoints */
@@ -107,6 +114,10 @@ typedef struct {
 int or_check(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
              const int32_t* sub, int64_t ns, const int32_t* seg_in, int64_t m,
              int64_t n_in, double B2, int brute, or_report* rep);
+/* the same with encroachment tested against the diametral lens when lens != 0 */
+int or_check_mode(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                  const int32_t* sub, int64_t ns, const int32_t* seg_in, int64_t m,
+                  int64_t n_in, double B2, int brute, int lens, or_report* rep);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,8 @@ def lib():
                 getattr(L, n).restype = C.c_int
             L.or_dot_sign.argtypes = [d] * 6
             L.or_dot_sign.restype = C.c_int
+            L.or_lens_sign.argtypes = [d] * 6
+            L.or_lens_sign.restype = C.c_int
             L.or_is_bad.argtypes = [d] * 7
             L.or_is_bad.restype = C.c_int
             L.or_circumcenter.argtypes = [d] * 6 + [C.POINTER(d), C.POINTER(d)]
@@ -84,6 +86,8 @@ def lib():
             L.or_refine.restype = C.c_int
             L.or_refine_len.argtypes = [vp, d, d, i64, C.c_int]
             L.or_refine_len.restype = C.c_int
+            L.or_refine_mode.argtypes = [vp, d, d, C.c_int, i64, C.c_int]
+            L.or_refine_mode.restype = C.c_int
             L.or_is_long.argtypes = [d] * 7
             L.or_is_long.restype = C.c_int
             L.or_insert_points.argtypes = [vp, vp, i64]
@@ -97,6 +101,9 @@ def lib():
             L.or_check.argtypes = [vp, i64, vp, i64, vp, i64, vp, i64, i64, d, C.c_int,
                                    C.POINTER(Report)]
             L.or_check.restype = C.c_int
+            L.or_check_mode.argtypes = [vp, i64, vp, i64, vp, i64, vp, i64, i64, d, C.c_int, C.c_int,
+                                        C.POINTER(Report)]
+            L.or_check_mode.restype = C.c_int
             L.or_eval_tris.argtypes = [vp, vp, i64, d, vp, vp, vp]
             L.or_eval_subs.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp]
             _lib = L
@@ -126,6 +133,12 @@ def incircle_sos(a, b, c, d):
 
 def dot_sign(a, b, p):
     return lib().or_dot_sign(*a, *b, *p)
+
+
+def lens_sign(a, b, p):
+    """-1: p strictly inside the diametral lens of ab (Chew's rule, Sec. 4.2),
+    0: p is a or b, +1: outside"""
+    return lib().or_lens_sign(*a, *b, *p)
 
 
 def is_bad(a, b, c, B2):
@@ -175,6 +188,12 @@ class Mesh:
         """refinement with the edge-length bound l as well (l <= 0: none)"""
         return lib().or_refine_len(self._h, B, l, max_steiner, order)
 
+    def refine_mode(self, B: float, l: float = 0.0, lens: bool = False, max_steiner: int = 1 << 40,
+                    order: int = 0) -> int:
+        """refinement with the encroachment region chosen: the diametral circle
+        (Ruppert's rule) or, with lens, the diametral lens (Chew's rule)"""
+        return lib().or_refine_mode(self._h, B, l, 1 if lens else 0, max_steiner, order)
+
     def insert_points(self, xy) -> int:
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
         return lib().or_insert_points(self._h, _p(xy), len(xy))
@@ -201,16 +220,17 @@ def is_long(a, b, c, L2):
     return lib().or_is_long(a[0], a[1], b[0], b[1], c[0], c[1], L2)
 
 
-def check(xy, tri, sub, seg_in, n_in, B=None, brute=False) -> dict:
-    """Invariant report for any mesh (see oracle/check.c)."""
+def check(xy, tri, sub, seg_in, n_in, B=None, brute=False, lens=False) -> dict:
+    """Invariant report for any mesh (see oracle/check.c); lens: encroachment
+    against the diametral lens (Chew's rule) instead of the diametral circle."""
     xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
     tri = np.ascontiguousarray(tri, np.int32).reshape(-1, 3)
     sub = np.ascontiguousarray(sub, np.int32).reshape(-1, 3)
     seg_in = np.ascontiguousarray(seg_in, np.int32).reshape(-1, 2)
     rep = Report()
-    lib().or_check(_p(xy), len(xy), _p(tri), len(tri), _p(sub), len(sub), _p(seg_in),
-                   len(seg_in), int(n_in), (B * B) if B else 0.0, 1 if brute else 0,
-                   C.byref(rep))
+    lib().or_check_mode(_p(xy), len(xy), _p(tri), len(tri), _p(sub), len(sub), _p(seg_in),
+                        len(seg_in), int(n_in), (B * B) if B else 0.0, 1 if brute else 0,
+                        1 if lens else 0, C.byref(rep))
     return rep.as_dict()
 
 

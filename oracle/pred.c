@@ -13,6 +13,9 @@
  *                      the circle through CCW a,b,c)
  *   dot(a,b;p)       = (a-p).(b-p)   (< 0: p strictly inside the diametral circle
  *                      of ab, i.e. p encroaches ab -- Sec. 4.2, Ruppert's rule)
+ *   lens(a,b;p)      = p strictly inside the diametral lens of ab (Chew's rule,
+ *                      Sec. 4.2): 3 ((a-p).(b-p))^2 > ((a-p) x (b-p))^2 with a
+ *                      negative dot product
  * A floating-point value with a forward error bound answers when it can;
  * otherwise the monomial expansion of the determinant is summed exactly.
  */
@@ -181,6 +184,59 @@ int or_dot_sign(double ax, double ay, double bx, double by, double px, double py
     mono2(m + 6, -1, py, by);
     mono2(m + 7, 1, py, py);
     return or_exact_sign(m, 8);
+}
+
+/* lens(a,b;p): p strictly inside the diametral lens of ab, the encroachment
+ * region of Chew's rule (Sec. 4.2).  The lens is the set of points from which
+ * the segment subtends an angle above 120 degrees: the intersection of the two
+ * disks through a and b whose centres lie on each other's circles, its apexes
+ * seeing the segment's ends at 30 degrees.  With u = a-p, w = b-p, D = u.w and
+ * C = u x w, Lagrange's identity |u|^2 |w|^2 = D^2 + C^2 turns
+ * cos(angle) < -1/2 into: D < 0 and 3 D^2 - C^2 > 0.
+ * Returns -1 inside, 0 on the boundary (a, b themselves), +1 outside. */
+static int lens_monos(or_mono* m, double ax, double ay, double bx, double by, double px, double py) {
+    /* D and C as signed degree-2 monomials in the raw coordinates */
+    const double dd[8][2] = {{ax, bx}, {ax, px}, {px, bx}, {px, px},
+                             {ay, by}, {ay, py}, {py, by}, {py, py}};
+    const int ds[8] = {1, -1, -1, 1, 1, -1, -1, 1};
+    const double cc[8][2] = {{ax, by}, {ax, py}, {px, by}, {px, py},
+                             {ay, bx}, {ay, px}, {py, bx}, {py, px}};
+    const int cs[8] = {1, -1, -1, 1, -1, 1, 1, -1};
+    int n = 0;
+    for (int r = 0; r < 3; ++r)            /* 3 D^2 */
+        for (int i = 0; i < 8; ++i)
+            for (int j = 0; j < 8; ++j)
+                mono4(m + n++, ds[i] * ds[j], dd[i][0], dd[i][1], dd[j][0], dd[j][1]);
+    for (int i = 0; i < 8; ++i)            /* - C^2 */
+        for (int j = 0; j < 8; ++j)
+            mono4(m + n++, -cs[i] * cs[j], cc[i][0], cc[i][1], cc[j][0], cc[j][1]);
+    return n;
+}
+
+int or_lens_sign(double ax, double ay, double bx, double by, double px, double py) {
+    const int d = or_dot_sign(ax, ay, bx, by, px, py);
+    if (d > 0) return 1;
+    if (d == 0) return ((px == ax && py == ay) || (px == bx && py == by)) ? 0 : 1;
+    if (g_filter) {
+        /* D and C with forward error bounds, then 3 D^2 - C^2 over the intervals */
+        const double ux = ax - px, uy = ay - py, wx = bx - px, wy = by - py;
+        const double D = ux * wx + uy * wy, Cr = ux * wy - uy * wx;
+        const double eD = 4.0 * U_RND * (fabs(ux * wx) + fabs(uy * wy)) + 4.0 * U_RND * (fabs(ux) + fabs(uy)) * (fabs(wx) + fabs(wy));
+        const double eC = 4.0 * U_RND * (fabs(ux * wy) + fabs(uy * wx)) + 4.0 * U_RND * (fabs(ux) + fabs(uy)) * (fabs(wx) + fabs(wy));
+        const double aD = fabs(D), aC = fabs(Cr);
+        if (aD > TINY && aD > eD) {
+            const double dlo = aD - eD, dhi = aD + eD;
+            const double clo = aC > eC ? aC - eC : 0.0, chi = aC + eC;
+            const double lo = 3.0 * dlo * dlo * (1 - 8 * U_RND) - chi * chi * (1 + 8 * U_RND);
+            const double hi = 3.0 * dhi * dhi * (1 + 8 * U_RND) - clo * clo * (1 - 8 * U_RND);
+            if (lo > 0) return -1;
+            if (hi < 0) return 1;
+        }
+    }
+    or_mono m[256];
+    const int n = lens_monos(m, ax, ay, bx, by, px, py);
+    const int s = or_exact_sign(m, n);
+    return s > 0 ? -1 : (s < 0 ? 1 : 0);
 }
 
 /* ---------------- fixed-order FP64 geometry ----------------

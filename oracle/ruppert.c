@@ -4,8 +4,9 @@
  *
  * Loop (Sec. 4.2 rules, applied one point at a time):
  *   1. while a subsegment is encroached -- a vertex strictly inside its
- *      diametral circle -- split it (midpoint, or a concentric-shell point
- *      next to a small input angle);
+ *      diametral circle (Ruppert's rule) or its diametral lens (Chew's rule,
+ *      or_refine_mode with lens != 0) -- split it (midpoint, or a
+ *      concentric-shell point next to a small input angle);
  *   2. otherwise take the worst bad triangle and compute its circumcentre c:
  *      - if the walk from the triangle to c crosses a subsegment, split that
  *        subsegment instead (Sec. 4.3, point location);
@@ -186,6 +187,7 @@ typedef struct {
     seg_adj A;
     double B2;
     double L2;   /* edge-length bound squared, 0 = none */
+    int lens;    /* encroachment region: 0 diametral circle (Ruppert), 1 diametral lens (Chew) */
     int order;
     int64_t seq;
     heap H;
@@ -229,9 +231,17 @@ static void after_insert(rstate* S, int64_t nn) {
     }
 }
 
+/* p strictly inside the encroachment region of ab: the diametral circle
+ * (Ruppert's rule, C2) or the diametral lens (Chew's rule, C22), Sec. 4.2 */
+static int inside_region(const rstate* S, double ax, double ay, double bx, double by, double px,
+                         double py) {
+    return S->lens ? or_lens_sign(ax, ay, bx, by, px, py) < 0 : or_dot_sign(ax, ay, bx, by, px, py) < 0;
+}
+
 /* C2: encroached iff the apex of an adjacent triangle is strictly inside the
- * diametral circle */
-static int encroached(const or_mesh* M, int64_t u, int64_t v) {
+ * encroachment region */
+static int encroached(const rstate* S, int64_t u, int64_t v) {
+    const or_mesh* M = S->M;
     int64_t ts[2] = {or_map_get(&M->edges, or_dkey(u, v)), or_map_get(&M->edges, or_dkey(v, u))};
     for (int k = 0; k < 2; ++k) {
         int64_t t = ts[k];
@@ -240,7 +250,7 @@ static int encroached(const or_mesh* M, int64_t u, int64_t v) {
         for (int j = 0; j < 3; ++j) {
             int64_t w = tv[j];
             if (w == u || w == v) continue;
-            if (or_dot_sign(M->x[u], M->y[u], M->x[v], M->y[v], M->x[w], M->y[w]) < 0) return 1;
+            if (inside_region(S, M->x[u], M->y[u], M->x[v], M->y[v], M->x[w], M->y[w])) return 1;
         }
     }
     return 0;
@@ -264,11 +274,16 @@ int or_refine(or_mesh* M, double B, int64_t max_steiner, int order) {
 }
 
 int or_refine_len(or_mesh* M, double B, double l, int64_t max_steiner, int order) {
+    return or_refine_mode(M, B, l, 0, max_steiner, order);
+}
+
+int or_refine_mode(or_mesh* M, double B, double l, int lens, int64_t max_steiner, int order) {
     rstate S;
     memset(&S, 0, sizeof(S));
     S.M = M;
     S.B2 = B * B;
     S.L2 = l > 0 ? l * l : 0.0;
+    S.lens = lens ? 1 : 0;
     S.order = order;
     build_adj(M, &S.A);
     int status = OR_OK;
@@ -284,7 +299,7 @@ int or_refine_len(or_mesh* M, double B, double l, int64_t max_steiner, int order
         while (S.Q.n > 0) {
             sent s = qpop(&S.Q);
             if (!or_is_sub(M, s.u, s.v)) continue;
-            if (!s.forced && !encroached(M, s.u, s.v)) continue;
+            if (!s.forced && !encroached(&S, s.u, s.v)) continue;
             if (M->n_steiner >= max_steiner) { status = OR_LIMIT; goto done; }
             status = split_sub(&S, s.u, s.v);
             if (status != OR_OK) goto done;
@@ -317,7 +332,7 @@ int or_refine_len(or_mesh* M, double B, double l, int64_t max_steiner, int order
         for (int64_t i = 0; i < nb; ++i) {
             int64_t a = cbnd[2 * i], b = cbnd[2 * i + 1];
             if (!or_is_sub(M, a, b)) continue;
-            if (or_dot_sign(M->x[a], M->y[a], M->x[b], M->y[b], cx, cy) < 0) {
+            if (inside_region(&S, M->x[a], M->y[a], M->x[b], M->y[b], cx, cy)) {
                 qpush(&S.Q, a, b, 1);
                 enc = 1;
             }
