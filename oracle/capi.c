@@ -22,8 +22,17 @@ void or_eval_tris(const double* xy, const int32_t* tri, int64_t nt, double B2, i
 
 /* per subsegment (u,v): encroached by an adjacent triangle's apex (C2),
  * midpoint (C4) and measure bits (C7) */
+void or_eval_subs_mode(const double* xy, const int32_t* tri, int64_t nt, const int32_t* sub,
+                       int64_t ns, int lens, int32_t* enc, double* mid, uint32_t* meas);
+
 void or_eval_subs(const double* xy, const int32_t* tri, int64_t nt, const int32_t* sub,
                   int64_t ns, int32_t* enc, double* mid, uint32_t* meas) {
+    or_eval_subs_mode(xy, tri, nt, sub, ns, 0, enc, mid, meas);
+}
+
+/* the same with encroachment by the diametral lens when lens != 0 (Chew) */
+void or_eval_subs_mode(const double* xy, const int32_t* tri, int64_t nt, const int32_t* sub,
+                       int64_t ns, int lens, int32_t* enc, double* mid, uint32_t* meas) {
     or_map dir;
     or_map_init(&dir, 6 * nt + 16);
     for (int64_t t = 0; t < nt; ++t)
@@ -36,8 +45,10 @@ void or_eval_subs(const double* xy, const int32_t* tri, int64_t nt, const int32_
         int64_t ap[2] = {or_map_get(&dir, or_dkey(u, v)), or_map_get(&dir, or_dkey(v, u))};
         for (int k = 0; k < 2; ++k)
             if (ap[k] >= 0 &&
-                or_dot_sign(xy[2 * u], xy[2 * u + 1], xy[2 * v], xy[2 * v + 1], xy[2 * ap[k]],
-                            xy[2 * ap[k] + 1]) < 0)
+                (lens ? or_lens_sign(xy[2 * u], xy[2 * u + 1], xy[2 * v], xy[2 * v + 1], xy[2 * ap[k]],
+                                     xy[2 * ap[k] + 1])
+                      : or_dot_sign(xy[2 * u], xy[2 * u + 1], xy[2 * v], xy[2 * v + 1], xy[2 * ap[k]],
+                                    xy[2 * ap[k] + 1])) < 0)
                 e = 1;
         enc[i] = e;
         or_midpoint(xy[2 * u], xy[2 * u + 1], xy[2 * v], xy[2 * v + 1], &mid[2 * i], &mid[2 * i + 1]);

@@ -106,6 +106,7 @@ def lib():
             L.or_check_mode.restype = C.c_int
             L.or_eval_tris.argtypes = [vp, vp, i64, d, vp, vp, vp]
             L.or_eval_subs.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp]
+            L.or_eval_subs_mode.argtypes = [vp, vp, i64, vp, i64, C.c_int, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -245,7 +246,9 @@ def eval_tris(xy, tri, B2):
     return bad, cc, meas
 
 
-def eval_subs(xy, tri, sub):
+def eval_subs(xy, tri, sub, lens=False):
+    """per subsegment: encroached by an adjacent apex (diametral circle, or the
+    diametral lens with lens), its midpoint and priority measure"""
     xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
     tri = np.ascontiguousarray(tri, np.int32).reshape(-1, 3)
     sub = np.ascontiguousarray(sub, np.int32).reshape(-1, 3)
@@ -253,7 +256,8 @@ def eval_subs(xy, tri, sub):
     enc = np.zeros(n, np.int32)
     mid = np.zeros((n, 2), np.float64)
     meas = np.zeros(n, np.uint32)
-    lib().or_eval_subs(_p(xy), _p(tri), len(tri), _p(sub), n, _p(enc), _p(mid), _p(meas))
+    lib().or_eval_subs_mode(_p(xy), _p(tri), len(tri), _p(sub), n, 1 if lens else 0, _p(enc), _p(mid),
+                            _p(meas))
     return enc, mid, meas
 
 

@@ -127,6 +127,9 @@ def test_rules_differ_on_one_mesh(h, circle, lens):
     rl = O.check(gxy, tri, sub, BOUNDARY, len(xy), lens=True)
     assert rc["encroached"] == circle
     assert rl["encroached"] == lens
+    # the scan helper (per subsegment) agrees with the checker's count
+    assert int(O.eval_subs(gxy, tri, sub)[0].sum()) == circle
+    assert int(O.eval_subs(gxy, tri, sub, lens=True)[0].sum()) == lens
 
 
 @pytest.mark.parametrize("lens", [False, True])
