@@ -126,13 +126,18 @@ int gdp_mesh_export(gdp_mesh* mesh, double* xy, int64_t cap_pts, int32_t* tri, i
 int gdp_mesh_insert_points(gdp_mesh* mesh, const double* xy, int64_t n);
 
 /* Split the subsegments given by endpoint coordinates (4 doubles each:
- * ax, ay, bx, by) at their midpoints, in parallel rounds. */
+ * ax, ay, bx, by) at their split points -- the midpoint, or the
+ * concentric-shell point when exactly one end is an input vertex where two
+ * segments meet below 60 degrees (Sec. 4.1 small input angles) -- with the
+ * parallel cavity kernels, in as many rounds as conflicts require. */
 int gdp_mesh_split_subsegments(gdp_mesh* mesh, const double* abxy, int64_t n);
 
 /* One bad-element scan (Algorithm 1) plus splitting points and
  * priorities (before point location) of the current mesh.
  * Outputs per element, cap entries each (host buffers, NULL to skip):
- *   kind[i]:  0 = bad triangle, 1 = encroached subsegment
+ *   kind[i]:  0 = bad triangle, 1 = encroached subsegment, 2 = bad triangle
+ *             accepted by the small-angle exemption (Sec. 4.1: its shortest
+ *             edge joins two segments that meet below 60 degrees)
  *   verts[3i..3i+2]: the triangle's vertices (CCW), or the subsegment's two
  *             endpoints and -1
  *   pt[2i..2i+1]: circumcentre (C5 formula) or split point
@@ -262,18 +267,25 @@ void gdp_server_destroy(gdp_server* s);
  *   tri_device: 4 int32 per triangle, 16-byte aligned: v0, v1, v2 (CCW) and a
  *               flags word whose bit e says that edge e = (v[e+1], v[e+2]) is a
  *               subsegment
- *   outputs (device, cap entries each, as in gdp_mesh_scan): kind_device,
- *               verts_device (3 per entry), pt_device (2 doubles per entry,
- *               circumcentre or midpoint), meas_device
+ *   outputs (device, cap entries each, laid out as in gdp_mesh_scan):
+ *               kind_device, verts_device (3 per entry), pt_device (2 doubles
+ *               per entry, 16-byte aligned: the circumcentre, or for an
+ *               encroached subsegment always its midpoint -- the call has no
+ *               segment data, so no concentric-shell points and no small-angle
+ *               exemption), meas_device
  *   *count (host): number of entries found, even beyond cap.  Entries come in
  *               triangle order: a bad triangle first, then its encroached edges.
  * Scratch: one file-scope device array of about 4.2 MB (per-triangle counts for
  * up to GDP_NOALLOC_MAX_TRIANGLES triangles plus block sums) that every GPU
  * which loads the library keeps until the process exits.  n_tri above
  * GDP_NOALLOC_MAX_TRIANGLES gives GDP_ERR_CAPACITY; a vertex id outside
- * [0, n_vert) or a misaligned buffer gives GDP_ERR_INPUT.
+ * [0, n_vert) or a misaligned buffer gives GDP_ERR_INPUT (before anything is
+ * launched, for the alignment).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress), which may load the library's device code and so
+ * allocate: make that first call as a warm-up, outside the context that must
+ * not allocate and before any stream capture.  The address is kept for the
+ * life of the process; resetting the device between calls is not supported.
  * All calls share the array, so calls that overlap on the GPU (for example
  * on two streams) race on it: issue them one after another.  The call blocks
  * until the count has been read back. */

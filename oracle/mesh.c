@@ -405,9 +405,9 @@ int or_insert_segment(or_mesh* M, int64_t a, int64_t b, int32_t sid) {
 static void mark_apexes(or_mesh* M) {
     M->apex = (uint8_t*)calloc((size_t)M->n_in + 1, 1);
     /* per input vertex, every pair of incident segments is compared; the
-     * angle at the shared vertex is below 60 degrees iff cos > 1/2, i.e.
-     * 2 (u.w) > |u||w| with u, w the directions -- decided in FP64, this
-     * only selects where the small-angle rules apply. */
+     * angle at the shared vertex is below 60 degrees iff cos > 1/2
+     * (or_small_angle) -- decided in FP64, this only selects where the
+     * small-angle rules apply. */
     int64_t* deg = (int64_t*)calloc((size_t)M->n_in + 1, sizeof(int64_t));
     for (int64_t s = 0; s < M->nseg; ++s) {
         deg[M->seg[2 * s]]++;
@@ -422,11 +422,7 @@ static void mark_apexes(or_mesh* M) {
                 if (M->seg[2 * r] == o) q = M->seg[2 * r + 1];
                 else if (M->seg[2 * r + 1] == o) q = M->seg[2 * r];
                 if (q < 0) continue;
-                double ux = M->x[p] - M->x[o], uy = M->y[p] - M->y[o];
-                double wx = M->x[q] - M->x[o], wy = M->y[q] - M->y[o];
-                double dot = ux * wx + uy * wy;
-                double nn = sqrt(ux * ux + uy * uy) * sqrt(wx * wx + wy * wy);
-                if (2.0 * dot > nn) M->apex[o] = 1;
+                if (or_small_angle(M->x[o], M->y[o], M->x[p], M->y[p], M->x[q], M->y[q])) M->apex[o] = 1;
             }
         }
     }

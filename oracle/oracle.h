@@ -76,9 +76,28 @@ int      or_refine_len(or_mesh*, double B, double l, int64_t max_steiner, int or
 /* the same with the encroachment region chosen: lens = 0 the diametral circle
  * (Ruppert's rule), lens != 0 the diametral lens (Chew's rule), Sec. 4.2 */
 int      or_refine_mode(or_mesh*, double B, double l, int lens, int64_t max_steiner, int order);
+/* C6: split point of subsegment ab -- the midpoint, or, when exactly one
+ * endpoint is an apex (an input vertex where segments meet below 60 degrees),
+ * the point at the power-of-two distance from it nearest to half the length
+ * in ratio (concentric shells) */
+void     or_split_point(double ax, double ay, double bx, double by, int apex_a, int apex_b,
+                        double* px, double* py);
+/* 1 iff the angle at o between the directions to p and q is below 60 degrees */
+int      or_small_angle(double ox, double oy, double px, double py, double qx, double qy);
+/* C10 on vertices a, b, c of a mesh (ids as in or_export, not necessarily a
+ * triangle of it): 1 if the shortest edge -- each of them on a tie -- joins
+ * vertices on two segments meeting at a small input angle; -1 bad id */
+int      or_exempt_query(const or_mesh*, int64_t a, int64_t b, int64_t c);
+/* per triangle of a mesh given as arrays (sub: (u, v, input segment) triples,
+ * seg_in over the first n_in vertices): 1 if bad (C1) and exempt (C10) */
+void     or_eval_exempt(const double* xy, int64_t nv, const int32_t* tri, int64_t nt,
+                        const int32_t* sub, int64_t ns, const int32_t* seg_in, int64_t m,
+                        int64_t n_in, double B2, int32_t* out);
 /* insert free points (strictly inside the domain, not on a subsegment) */
 int      or_insert_points(or_mesh*, const double* xy, int64_t n);
-/* split the subsegments given by endpoint coordinates (ax,ay,bx,by) at midpoints */
+/* split the subsegments given by endpoint coordinates (ax,ay,bx,by) at their
+ * split points (or_split_point: midpoint, or a concentric-shell point next to
+ * a small input angle) */
 int      or_split_subsegments(or_mesh*, const double* abxy, int64_t n);
 /* bad list of the current mesh: per live triangle / subsegment (see C API) */
 int64_t  or_n_vertices(const or_mesh*);

@@ -107,6 +107,12 @@ def lib():
             L.or_eval_tris.argtypes = [vp, vp, i64, d, vp, vp, vp]
             L.or_eval_subs.argtypes = [vp, vp, i64, vp, i64, vp, vp, vp]
             L.or_eval_subs_mode.argtypes = [vp, vp, i64, vp, i64, C.c_int, vp, vp, vp]
+            L.or_split_point.argtypes = [d, d, d, d, C.c_int, C.c_int, C.POINTER(d), C.POINTER(d)]
+            L.or_small_angle.argtypes = [d] * 6
+            L.or_small_angle.restype = C.c_int
+            L.or_exempt_query.argtypes = [vp, i64, i64, i64]
+            L.or_exempt_query.restype = C.c_int
+            L.or_eval_exempt.argtypes = [vp, i64, vp, i64, vp, i64, vp, i64, i64, d, vp]
             _lib = L
     return _lib
 
@@ -162,6 +168,32 @@ def measure_bits(v):
     return lib().or_measure_bits(v)
 
 
+def split_point(a, b, apex_a=False, apex_b=False):
+    """C6: the midpoint of ab, or the concentric-shell point when exactly one
+    endpoint is an apex (an input vertex with a small input angle)"""
+    x, y = C.c_double(), C.c_double()
+    lib().or_split_point(*a, *b, 1 if apex_a else 0, 1 if apex_b else 0, C.byref(x), C.byref(y))
+    return x.value, y.value
+
+
+def small_angle(o, p, q):
+    """the angle at o between the directions to p and q is below 60 degrees"""
+    return bool(lib().or_small_angle(*o, *p, *q))
+
+
+def eval_exempt(xy, tri, sub, seg_in, n_in, B2):
+    """per triangle: 1 if it is bad (C1) and accepted by the small-angle
+    exemption (C10)"""
+    xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+    tri = np.ascontiguousarray(tri, np.int32).reshape(-1, 3)
+    sub = np.ascontiguousarray(sub, np.int32).reshape(-1, 3)
+    seg_in = np.ascontiguousarray(seg_in, np.int32).reshape(-1, 2)
+    out = np.zeros(len(tri), np.int32)
+    lib().or_eval_exempt(_p(xy), len(xy), _p(tri), len(tri), _p(sub), len(sub), _p(seg_in), len(seg_in),
+                         int(n_in), B2, _p(out))
+    return out
+
+
 # ---------------- meshes ----------------
 class Mesh:
     """Oracle CDT of a PSLG; refine() runs sequential Ruppert refinement."""
@@ -198,6 +230,10 @@ class Mesh:
     def insert_points(self, xy) -> int:
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
         return lib().or_insert_points(self._h, _p(xy), len(xy))
+
+    def exempt(self, a: int, b: int, c: int) -> int:
+        """C10 on three vertices (export ids): 1 exempt, 0 not, -1 bad id"""
+        return lib().or_exempt_query(self._h, a, b, c)
 
     def split_subsegments(self, abxy) -> int:
         abxy = np.ascontiguousarray(abxy, dtype=np.float64).reshape(-1, 4)

@@ -47,77 +47,153 @@ static void build_adj(const or_mesh* M, seg_adj* A) {
     free(fill);
 }
 
-/* two distinct input segments meeting at a shared endpoint at less than 60 degrees */
-static int small_pair(const or_mesh* M, int64_t s1, int64_t s2) {
-    if (s1 == s2) return 0;
-    const int32_t* a = M->seg + 2 * s1;
-    const int32_t* b = M->seg + 2 * s2;
-    int64_t o = -1, p = -1, q = -1;
-    for (int i = 0; i < 2 && o < 0; ++i)
-        for (int j = 0; j < 2; ++j)
-            if (a[i] == b[j]) { o = a[i]; p = a[1 - i]; q = b[1 - j]; break; }
-    if (o < 0) return 0;
-    double ux = M->x[p] - M->x[o], uy = M->y[p] - M->y[o];
-    double wx = M->x[q] - M->x[o], wy = M->y[q] - M->y[o];
+/* C6/C10: the angle at a shared endpoint o between the directions to p and q
+ * is below 60 degrees iff cos > 1/2, i.e. 2 (u.w) > |u| |w| with u = p - o,
+ * w = q - o, evaluated in FP64 in this order (no contraction).  This only
+ * selects where the small-angle rules of Sec. 4.1 apply. */
+int or_small_angle(double ox, double oy, double px, double py, double qx, double qy) {
+    double ux = px - ox, uy = py - oy;
+    double wx = qx - ox, wy = qy - oy;
     double dot = ux * wx + uy * wy;
     double nn = sqrt(ux * ux + uy * uy) * sqrt(wx * wx + wy * wy);
     return 2.0 * dot > nn;
 }
 
-/* the segments a vertex lies on: its own segment for a Steiner vertex placed
- * on one, the incident segments for an input vertex */
-static int segs_of(const or_mesh* M, const seg_adj* A, int64_t v, int32_t* out, int cap) {
-    if (v < M->n_in) {
+/* two distinct input segments meeting at a shared endpoint at less than 60 degrees */
+static int small_pair_seg(const double* x, const double* y, const int32_t* seg, int64_t s1, int64_t s2) {
+    if (s1 == s2 || s1 < 0 || s2 < 0) return 0;
+    const int32_t* a = seg + 2 * s1;
+    const int32_t* b = seg + 2 * s2;
+    int64_t o = -1, p = -1, q = -1;
+    for (int i = 0; i < 2 && o < 0; ++i)
+        for (int j = 0; j < 2; ++j)
+            if (a[i] == b[j]) { o = a[i]; p = a[1 - i]; q = b[1 - j]; break; }
+    if (o < 0) return 0;
+    return or_small_angle(x[o], y[o], x[p], y[p], x[q], y[q]);
+}
+
+/* the segments a vertex lies on: the incident segments of an input vertex,
+ * the segment a Steiner vertex was placed on (vseg), else none */
+static int segs_of(const seg_adj* A, int64_t n_in, const int32_t* vseg, int64_t v, int32_t* out,
+                   int cap) {
+    if (v < n_in) {
         int n = 0;
         for (int64_t k = A->off[v]; k < A->off[v + 1] && n < cap; ++k) out[n++] = A->adj[k];
         return n;
     }
-    if (M->vseg[v] >= 0) { out[0] = M->vseg[v]; return 1; }
+    if (vseg[v] >= 0) { out[0] = vseg[v]; return 1; }
     return 0;
 }
 
-/* C10: a bad triangle is accepted when its shortest edge joins vertices on two
- * segments that meet at a small input angle */
-static int exempt(const or_mesh* M, const seg_adj* A, int64_t t) {
-    if (M->nseg < 2) return 0;
-    const int32_t* v = M->tv + 3 * t;
-    double best = -1;
-    int be = 0;
+/* C10: a bad triangle (a, b, c) is accepted when its shortest edge joins
+ * vertices on two segments that meet at a small input angle.  Where several
+ * edges are equally short each one is tried, so the decision does not depend
+ * on the order of a, b, c. */
+static int exempt_abc(const double* x, const double* y, const int32_t* seg, int64_t nseg,
+                      const seg_adj* A, int64_t n_in, const int32_t* vseg, const int64_t v[3]) {
+    if (nseg < 2) return 0;
+    double l[3];
     for (int e = 0; e < 3; ++e) {
         int64_t a = v[(e + 1) % 3], b = v[(e + 2) % 3];
-        double dx = M->x[b] - M->x[a], dy = M->y[b] - M->y[a];
-        double l = dx * dx + dy * dy;
-        if (best < 0 || l < best) { best = l; be = e; }
+        double dx = x[b] - x[a], dy = y[b] - y[a];
+        l[e] = dx * dx + dy * dy;
     }
-    int64_t u = v[(be + 1) % 3], w = v[(be + 2) % 3];
-    int32_t su[64], sw[64];
-    int nu = segs_of(M, A, u, su, 64), nw = segs_of(M, A, w, sw, 64);
-    for (int i = 0; i < nu; ++i)
-        for (int j = 0; j < nw; ++j)
-            if (small_pair(M, su[i], sw[j])) return 1;
+    double best = l[0];
+    if (l[1] < best) best = l[1];
+    if (l[2] < best) best = l[2];
+    for (int e = 0; e < 3; ++e) {
+        if (l[e] != best) continue;
+        int64_t u = v[(e + 1) % 3], w = v[(e + 2) % 3];
+        int32_t su[64], sw[64];
+        int nu = segs_of(A, n_in, vseg, u, su, 64), nw = segs_of(A, n_in, vseg, w, sw, 64);
+        for (int i = 0; i < nu; ++i)
+            for (int j = 0; j < nw; ++j)
+                if (small_pair_seg(x, y, seg, su[i], sw[j])) return 1;
+    }
     return 0;
 }
 
-/* C6: split point of subsegment (u,v) of input segment s.  If exactly one
- * endpoint is an input vertex where segments meet at a small angle, the point
- * sits at the power-of-two distance from it nearest to half the length
- * (concentric shells); otherwise the midpoint. */
+static int exempt(const or_mesh* M, const seg_adj* A, int64_t t) {
+    const int32_t* tv = M->tv + 3 * t;
+    int64_t v[3] = {tv[0], tv[1], tv[2]};
+    return exempt_abc(M->x, M->y, M->seg, M->nseg, A, M->n_in, M->vseg, v);
+}
+
+/* vertex ids as in or_export (the enclosing vertices left out) */
+int or_exempt_query(const or_mesh* M, int64_t a, int64_t b, int64_t c) {
+    int64_t v[3] = {a, b, c};
+    for (int k = 0; k < 3; ++k) {
+        if (v[k] < 0 || v[k] >= M->nv - 3) return -1;
+        if (v[k] >= M->super0) v[k] += 3;
+    }
+    seg_adj A;
+    build_adj(M, &A);
+    int r = exempt_abc(M->x, M->y, M->seg, M->nseg, &A, M->n_in, M->vseg, v);
+    free(A.off);
+    free(A.adj);
+    return r;
+}
+
+/* per triangle of a mesh given as arrays: 1 if it is bad (C1) and exempt
+ * (C10).  The segment a Steiner vertex lies on is read off the subsegments
+ * it ends (sub: (u, v, input segment id) triples). */
+void or_eval_exempt(const double* xy, int64_t nv, const int32_t* tri, int64_t nt, const int32_t* sub,
+                    int64_t ns, const int32_t* seg_in, int64_t m, int64_t n_in, double B2, int32_t* out) {
+    double* x = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    double* y = (double*)malloc(sizeof(double) * (size_t)(nv + 1));
+    int32_t* vseg = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nv + 1));
+    for (int64_t k = 0; k < nv; ++k) { x[k] = xy[2 * k]; y[k] = xy[2 * k + 1]; vseg[k] = -1; }
+    for (int64_t i = 0; i < ns; ++i)
+        for (int k = 0; k < 2; ++k)
+            if (sub[3 * i + k] >= n_in) vseg[sub[3 * i + k]] = sub[3 * i + 2];
+    or_mesh tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.n_in = n_in;
+    tmp.nseg = m;
+    tmp.seg = (int32_t*)seg_in;
+    seg_adj A;
+    build_adj(&tmp, &A);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int32_t* tv = tri + 3 * t;
+        int64_t v[3] = {tv[0], tv[1], tv[2]};
+        out[t] = or_is_bad(x[v[0]], y[v[0]], x[v[1]], y[v[1]], x[v[2]], y[v[2]], B2) &&
+                 exempt_abc(x, y, seg_in, m, &A, n_in, vseg, v);
+    }
+    free(A.off);
+    free(A.adj);
+    free(x);
+    free(y);
+    free(vseg);
+}
+
+/* C6: split point of subsegment ab.  If exactly one endpoint is an input
+ * vertex where segments meet at a small angle (apex_a / apex_b), the point
+ * sits at the power-of-two distance d from it nearest to half the length L
+ * in ratio (concentric shells): with L/2 = m 2^e, m in [1/2, 1), d = 2^(e-1)
+ * when m^2 < 1/2 (then L/2 is nearer 2^(e-1) than 2^e in ratio), else 2^e.
+ * Otherwise the midpoint. */
+void or_split_point(double ax, double ay, double bx, double by, int apex_a, int apex_b, double* px,
+                    double* py) {
+    if ((apex_a != 0) == (apex_b != 0)) {
+        or_midpoint(ax, ay, bx, by, px, py);
+        return;
+    }
+    double ox = apex_a ? ax : bx, oy = apex_a ? ay : by;
+    double qx = apex_a ? bx : ax, qy = apex_a ? by : ay;
+    double dx = qx - ox, dy = qy - oy;
+    double L = sqrt(dx * dx + dy * dy);
+    int e;
+    double m = frexp(0.5 * L, &e);
+    double d = (m * m < 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+    double r = d / L;
+    *px = ox + dx * r;
+    *py = oy + dy * r;
+}
+
 static void split_point(const or_mesh* M, int64_t u, int64_t v, double* px, double* py) {
     int au = (u < M->n_in) && M->apex && M->apex[u];
     int av = (v < M->n_in) && M->apex && M->apex[v];
-    if (au == av) {
-        or_midpoint(M->x[u], M->y[u], M->x[v], M->y[v], px, py);
-        return;
-    }
-    int64_t o = au ? u : v, q = au ? v : u;
-    double dx = M->x[q] - M->x[o], dy = M->y[q] - M->y[o];
-    double L = sqrt(dx * dx + dy * dy);
-    int e;
-    double m = frexp(0.5 * L, &e);           /* 0.5 L = m 2^e, m in [0.5,1) */
-    double d = (m * m < 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
-    double r = d / L;
-    *px = M->x[o] + dx * r;
-    *py = M->y[o] + dy * r;
+    or_split_point(M->x[u], M->y[u], M->x[v], M->y[v], au, av, px, py);
 }
 
 /* ---------------- work queues ---------------- */
@@ -403,7 +479,7 @@ int or_split_subsegments(or_mesh* M, const double* abxy, int64_t n) {
                 ids[k] = -1;
         if (ids[0] < 0 || ids[1] < 0 || !or_is_sub(M, ids[0], ids[1])) { st = OR_INPUT; break; }
         double px, py;
-        or_midpoint(M->x[ids[0]], M->y[ids[0]], M->x[ids[1]], M->y[ids[1]], &px, &py);
+        split_point(M, ids[0], ids[1], &px, &py);
         int32_t sid = (int32_t)or_map_get(&M->subs, or_ukey(ids[0], ids[1]));
         int64_t p = or_add_vertex(M, px, py, sid);
         uint64_t kx, ky;

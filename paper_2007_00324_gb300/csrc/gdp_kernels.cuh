@@ -153,7 +153,11 @@ __device__ int seg_of_sub(const Pool& P, const MeshInfo& M, int u, int v) {
   return -1;
 }
 
-// two distinct input segments sharing an endpoint at less than 60 degrees
+// two distinct input segments sharing an endpoint at less than 60 degrees:
+// cos > 1/2, i.e. 2 (u.w) > |u| |w| for the two directions u, w from the
+// shared vertex.  Every operation is rounded on its own (no contraction), so
+// the decision is the same bit for bit wherever this formula is evaluated in
+// this order; it is symmetric in the two segments.
 __device__ bool small_pair(const Pool& P, int s1, int s2) {
   if (s1 == s2 || s1 < 0 || s2 < 0) return false;
   const int2 a = P.seg[s1], b = P.seg[s2];
@@ -164,62 +168,72 @@ __device__ bool small_pair(const Pool& P, int s1, int s2) {
   else if (a.y == b.y) { o = a.y; p = a.x; q = b.x; }
   else return false;
   const double2 O = P.V[o], A = P.V[p], B = P.V[q];
-  const double ux = A.x - O.x, uy = A.y - O.y, wx = B.x - O.x, wy = B.y - O.y;
-  const double dot = ux * wx + uy * wy;
-  const double nn = sqrt(ux * ux + uy * uy) * sqrt(wx * wx + wy * wy);
-  return 2.0 * dot > nn;
+  const double ux = __dsub_rn(A.x, O.x), uy = __dsub_rn(A.y, O.y);
+  const double wx = __dsub_rn(B.x, O.x), wy = __dsub_rn(B.y, O.y);
+  const double dot = __dadd_rn(__dmul_rn(ux, wx), __dmul_rn(uy, wy));
+  const double nn = __dmul_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy))),
+                              __dsqrt_rn(__dadd_rn(__dmul_rn(wx, wx), __dmul_rn(wy, wy))));
+  return __dmul_rn(2.0, dot) > nn;
 }
 
-__device__ int segs_of(const Pool& P, const MeshInfo& M, int v, int* out) {
+// the k-th input segment vertex v lies on (an input vertex: its incident
+// segments; a Steiner vertex: the segment it was placed on), and how many
+__device__ __forceinline__ int n_segs_of(const Pool& P, const MeshInfo& M, int v) {
   if (is_input(M, v)) {
     const int l = v - M.vert_base;
-    int n = 0;
-    for (int k = P.adj_off[M.adj_base + l]; k < P.adj_off[M.adj_base + l + 1] && n < 16; ++k)
-      out[n++] = P.adj[k];
-    return n;
+    return P.adj_off[M.adj_base + l + 1] - P.adj_off[M.adj_base + l];
   }
-  const int s = P.vseg[v];
-  if (s >= 0) { out[0] = s; return 1; }
-  return 0;
+  return P.vseg[v] >= 0 ? 1 : 0;
+}
+__device__ __forceinline__ int seg_at(const Pool& P, const MeshInfo& M, int v, int k) {
+  if (is_input(M, v)) return P.adj[P.adj_off[M.adj_base + (v - M.vert_base)] + k];
+  return P.vseg[v];
 }
 
-// bad triangles whose shortest edge joins two segments meeting at a small
-// input angle are accepted in the output (Sec. 4.1)
+// Bad triangles whose shortest edge joins two segments meeting at a small
+// input angle are accepted in the output (Sec. 4.1).  When several edges
+// are shortest, each is tried, so the decision does not depend on where the
+// triangle's vertex list starts.
 __device__ bool exempt(const Pool& P, const MeshInfo& M, const int4& T4) {
   if (!M.has_apex) return false;
-  double best = -1.0;
-  int be = 0;
+  double l[3];
   for (int e = 0; e < 3; ++e) {
     const double2 a = P.V[comp(T4, mod3(e + 1))], b = P.V[comp(T4, mod3(e + 2))];
-    const double dx = b.x - a.x, dy = b.y - a.y;
-    const double l = dx * dx + dy * dy;
-    if (best < 0 || l < best) { best = l; be = e; }
+    const double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y);
+    l[e] = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
   }
-  int su[16], sw[16];
-  const int nu = segs_of(P, M, comp(T4, mod3(be + 1)), su);
-  const int nw = segs_of(P, M, comp(T4, mod3(be + 2)), sw);
-  for (int i = 0; i < nu; ++i)
-    for (int j = 0; j < nw; ++j)
-      if (small_pair(P, su[i], sw[j])) return true;
+  const double best = fmin(l[0], fmin(l[1], l[2]));
+  for (int e = 0; e < 3; ++e) {
+    if (l[e] != best) continue;
+    const int u = comp(T4, mod3(e + 1)), w = comp(T4, mod3(e + 2));
+    const int nu = n_segs_of(P, M, u), nw = n_segs_of(P, M, w);
+    for (int i = 0; i < nu; ++i) {
+      const int su = seg_at(P, M, u, i);
+      for (int j = 0; j < nw; ++j)
+        if (small_pair(P, su, seg_at(P, M, w, j))) return true;
+    }
+  }
   return false;
 }
 
-// splitting point of subsegment (u,v): the midpoint, or -- when exactly one
+// Splitting point of subsegment (u,v): the midpoint, or -- when exactly one
 // endpoint is an input vertex with a small input angle -- the point at the
-// power-of-two distance from it nearest to half the length (concentric shells)
+// power-of-two distance d from it nearest to half the length L in ratio
+// (concentric shells): with L/2 = m 2^e, m in [1/2, 1), d = 2^(e-1) when
+// m^2 < 1/2, else 2^e.  Each operation rounded on its own (no contraction).
 __device__ double2 split_point(const Pool& P, const MeshInfo& M, int u, int v) {
   const bool au = is_input(M, u) && P.apex[u];
   const bool av = is_input(M, v) && P.apex[v];
   if (au == av) return midpoint(P.V[u], P.V[v]);
   const int o = au ? u : v, q = au ? v : u;
   const double2 O = P.V[o], Q = P.V[q];
-  const double dx = Q.x - O.x, dy = Q.y - O.y;
-  const double L = sqrt(dx * dx + dy * dy);
+  const double dx = __dsub_rn(Q.x, O.x), dy = __dsub_rn(Q.y, O.y);
+  const double L = __dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
   int e;
-  const double m = frexp(0.5 * L, &e);
-  const double d = (m * m < 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
-  const double r = d / L;
-  return make_double2(O.x + dx * r, O.y + dy * r);
+  const double m = frexp(__dmul_rn(0.5, L), &e);
+  const double d = (__dmul_rn(m, m) < 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+  const double r = __ddiv_rn(d, L);
+  return make_double2(__dadd_rn(O.x, __dmul_rn(dx, r)), __dadd_rn(O.y, __dmul_rn(dy, r)));
 }
 
 // ---------------------------------------------------------------- scan
@@ -1821,8 +1835,9 @@ __global__ void __launch_bounds__(BS) k_check(Pool P, unsigned long long* cnt) {
 }
 
 // ---------------------------------------------------------------- scan report (test hook)
-// Every live triangle: its bad flag; every subsegment edge: encroachment by
-// this triangle's apex.  Output in slot order.
+// Every live bad triangle (kind 0, or 2 when the small-angle exemption
+// accepts it); every subsegment edge: encroachment by this triangle's apex
+// (kind 1) with its split point.  Output order is not defined.
 __global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int* kind, int* verts,
                                                     double2* spt, unsigned* meas, int cap,
                                                     int* count) {
@@ -1836,7 +1851,7 @@ __global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int* kind
     if (q > 0 || (q == 0 && is_bad(tt, B2))) {
       const int r = atomicAdd(count, 1);
       if (r < cap) {
-        kind[r] = 0;
+        kind[r] = exempt(P, M, T4) ? 2 : 0;
         verts[3 * r] = T4.x; verts[3 * r + 1] = T4.y; verts[3 * r + 2] = T4.z;
         spt[r] = circumcenter(tt);
         meas[r] = measure_bits(fabs(tt.cr));

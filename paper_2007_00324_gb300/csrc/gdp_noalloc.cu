@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NA_BS) k_na_write(const double2* V, const int4
         if (!((T4.w >> e) & 1)) continue;
         const int u = na_comp(T4, (e + 1) % 3), v = na_comp(T4, (e + 2) % 3);
         if (gdp::dot_sign(V[u], V[v], V[na_comp(T4, e)]) < 0) {
-          if (r < cap) {
+          if (r < cap) {   // the midpoint: there is no segment data for shells here
             kind[r] = 1;
             verts[3 * r] = u; verts[3 * r + 1] = v; verts[3 * r + 2] = -1;
             pt[r] = gdp::midpoint(V[u], V[v]);
@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(NA_BS) k_na_write(const double2* V, const int4
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) S->total = off;
 }
 
-// device address of the scratch array, looked up once per device
+// device address of the scratch array, looked up once per device (a reset of
+// the device between calls is not supported: the cached address would be stale)
 constexpr int NA_MAX_DEVICES = 64;
 NoallocScratch* g_addr[NA_MAX_DEVICES] = {};
 std::mutex g_addr_lock;
@@ -196,6 +197,8 @@ extern "C" int gdp_scan_noalloc(const double* xy_device, int64_t n_vert, const i
   if (n_tri > NA_MAX_TRI || n_vert > INT32_MAX || cap > INT32_MAX) return GDP_ERR_CAPACITY;
   if ((reinterpret_cast<uintptr_t>(tri_device) & 15) || (reinterpret_cast<uintptr_t>(xy_device) & 15))
     return GDP_ERR_INPUT;
+  // the points are written as 16-byte (x, y) pairs
+  if (cap > 0 && (reinterpret_cast<uintptr_t>(pt_device) & 15)) return GDP_ERR_INPUT;
   NoallocScratch* S = nullptr;
   const int st = scratch_for_current_device(&S);
   if (st != GDP_OK) return st;

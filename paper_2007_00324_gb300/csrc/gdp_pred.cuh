@@ -25,11 +25,21 @@ namespace gdp {
 
 constexpr double kU = 1.1102230246251565e-16;   // 2^-53
 
-// diagnostic counters (per translation unit): exact-path calls and maxima
+// diagnostic counters (per translation unit), written only in a build with
+// -DGDP_DIAG: exact-path calls and maxima
 // 0 orient_exact, 1 incircle_exact, 2 incircle tie (simulation of simplicity),
 // 3 dot_exact, 4 incircle_exact with inexact differences, 5 max walk steps,
 // 6 max cycles in one grow, 7 max cycles in one walk, 8 max cycles of one exact incircle
 static __device__ unsigned long long g_diag[16];
+#ifdef GDP_DIAG
+#define GDP_DIAG_ADD(i) atomicAdd(&g_diag[i], 1ull)
+#define GDP_DIAG_MAX(i, v) atomicMax(&g_diag[i], (unsigned long long)(v))
+#define GDP_DIAG_CLOCK() clock64()
+#else
+#define GDP_DIAG_ADD(i) ((void)0)
+#define GDP_DIAG_MAX(i, v) ((void)0)
+#define GDP_DIAG_CLOCK() 0ll
+#endif
 constexpr double kTiny = 1e-250;                // below: relative bounds unsafe -> exact
 
 // ---------------------------------------------------------------- EFTs
@@ -249,7 +259,7 @@ static __device__ __noinline__ int int_sign(const double* f, const double* sg, i
 static __device__ __noinline__ int orient_exact(double ax, double ay, double bx, double by, double cx,
                                          double cy) {
   // (ax-cx)(by-cy) - (ay-cy)(bx-cx) with each difference as an exact pair
-  atomicAdd(&g_diag[0], 1ull);
+  GDP_DIAG_ADD(0);
   double acxh, acxl, acyh, acyl, bcxh, bcxl, bcyh, bcyl;
   two_diff(ax, cx, acxh, acxl);
   two_diff(ay, cy, acyh, acyl);
@@ -296,8 +306,9 @@ __device__ __forceinline__ int orient(double2 a, double2 b, double2 c) {
 // with every difference relative to d.
 static __device__ __noinline__ int incircle_exact(double ax, double ay, double bx, double by, double cx,
                                            double cy, double dx, double dy) {
-  const long long c0 = clock64();
-  atomicAdd(&g_diag[1], 1ull);
+  const long long c0 = GDP_DIAG_CLOCK();
+  GDP_DIAG_ADD(1);
+  (void)c0;
   double h[6], l[6];   // adx ady bdx bdy cdx cdy as exact pairs
   two_diff(ax, dx, h[0], l[0]);
   two_diff(ay, dy, h[1], l[1]);
@@ -306,7 +317,7 @@ static __device__ __noinline__ int incircle_exact(double ax, double ay, double b
   two_diff(cx, dx, h[4], l[4]);
   two_diff(cy, dy, h[5], l[5]);
   if (l[0] != 0.0 || l[1] != 0.0 || l[2] != 0.0 || l[3] != 0.0 || l[4] != 0.0 || l[5] != 0.0) {
-    atomicAdd(&g_diag[4], 1ull);
+    GDP_DIAG_ADD(4);
   } else {
     // sum over the three points t (q, r the other two) of
     // (x_t^2 + y_t^2) (x_q y_r - x_r y_q): 12 monomials of degree 4
@@ -324,7 +335,7 @@ static __device__ __noinline__ int incircle_exact(double ax, double ay, double b
     }
     const int rr = int_sign(f, sg, n, 4);
     if (rr != 2) {
-      atomicMax(&g_diag[8], (unsigned long long)(clock64() - c0));
+      GDP_DIAG_MAX(8, GDP_DIAG_CLOCK() - c0);
       return rr;
     }
   }
@@ -366,7 +377,7 @@ static __device__ __noinline__ int incircle_exact(double ax, double ay, double b
       }
     }
   }
-  atomicMax(&g_diag[8], (unsigned long long)(clock64() - c0));
+  GDP_DIAG_MAX(8, GDP_DIAG_CLOCK() - c0);
   return X.sign();
 }
 
@@ -407,7 +418,7 @@ GDP_HD bool lex_less(double ax, double ay, double bx, double by) {
 // C_c = +orient(a,b,d), C_d = -orient(a,b,c).  Ranking by coordinates (not by
 // vertex number) makes the result independent of how vertices are numbered.
 static __device__ __noinline__ int incircle_sos_tie(double2 a, double2 b, double2 c, double2 d) {
-  atomicAdd(&g_diag[2], 1ull);
+  GDP_DIAG_ADD(2);
   double2 P[4] = {a, b, c, d};
   int ord[4] = {0, 1, 2, 3};
   for (int i = 1; i < 4; ++i) {       // decreasing lexicographic order
@@ -439,7 +450,7 @@ __device__ __forceinline__ int incircle(double2 a, double2 b, double2 c, double2
 // ---------------------------------------------------------------- diametral circle
 static __device__ __noinline__ int dot_exact(double ax, double ay, double bx, double by, double px,
                                       double py) {
-  atomicAdd(&g_diag[3], 1ull);
+  GDP_DIAG_ADD(3);
   double axh, axl, ayh, ayl, bxh, bxl, byh, byl;
   two_diff(ax, px, axh, axl);
   two_diff(ay, py, ayh, ayl);

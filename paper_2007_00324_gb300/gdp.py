@@ -426,6 +426,15 @@ def scan_noalloc(xy, tri4, B, kind, verts, pt, meas, stream=None):
     """gdp_scan_noalloc on caller-owned torch CUDA tensors: xy (n,2) float64,
     tri4 (t,4) int32, outputs kind (cap,) int32, verts (cap,3) int32,
     pt (cap,2) float64, meas (cap,) int32.  Returns the entry count."""
+    import torch
+    cap = int(kind.shape[0])
+    want = ((xy, torch.float64, (None, 2)), (tri4, torch.int32, (None, 4)), (kind, torch.int32, (cap,)),
+            (verts, torch.int32, (cap, 3)), (pt, torch.float64, (cap, 2)), (meas, torch.int32, (cap,)))
+    for t, dt, shape in want:
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == dt and t.dim() == len(shape) and
+                all(w is None or w == g for w, g in zip(shape, t.shape))):
+            raise ValueError(f"scan_noalloc: expected a contiguous CUDA {dt} tensor of shape {shape}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
     cnt = C.c_int64()
     st = load().gdp_scan_noalloc(C.c_void_p(xy.data_ptr()), int(xy.shape[0]),
                                  C.c_void_p(tri4.data_ptr()), int(tri4.shape[0]), float(B),

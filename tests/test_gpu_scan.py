@@ -37,9 +37,10 @@ def test_scan_matches_oracle(oracle, B):
     for k in range(len(kind)):
         if kind[k] == 0:
             got_t[canon_tri(xy, verts[k])] = (tuple(pt[k].tolist()), int(meas[k]))
-        else:
+        elif kind[k] == 1:
             a, b = sorted([tuple(xy[verts[k, 0]].tolist()), tuple(xy[verts[k, 1]].tolist())])
             got_s[(a, b)] = (tuple(pt[k].tolist()), int(meas[k]))
     assert len(want_t) > 100
+    assert set(kind.tolist()) <= {0, 1}   # no small input angles here, so nothing exempt
     assert got_t == want_t
     assert got_s == want_s

@@ -75,6 +75,16 @@ def test_noalloc_rejects_oversize_and_bad_ids():
     with pytest.raises(gdp.GdpError) as e:
         gdp.scan_noalloc(xy, t4, 1.5, out_i, out_v, out_p, out_i)
     assert e.value.status == gdp.ERR_INPUT
+    # a point buffer that is 8- but not 16-byte aligned: refused before any launch
+    ok_t4 = torch.tensor([[0, 1, 2, 0]], dtype=torch.int32, device=dev)
+    pbuf = torch.zeros((9,), dtype=torch.float64, device=dev)
+    L = gdp.load()
+    cnt = gdp.C.c_int64()
+    st = L.gdp_scan_noalloc(gdp.C.c_void_p(xy.data_ptr()), 3, gdp.C.c_void_p(ok_t4.data_ptr()), 1, 1.5,
+                            gdp.C.c_void_p(out_i.data_ptr()), gdp.C.c_void_p(out_v.data_ptr()),
+                            gdp.C.c_void_p(pbuf.data_ptr() + 8), gdp.C.c_void_p(out_i.data_ptr()), 4,
+                            gdp.C.byref(cnt), None)
+    assert st == gdp.ERR_INPUT
     big = torch.zeros(((1 << 22) + 1, 4), dtype=torch.int32, device=dev)
     with pytest.raises(gdp.GdpError) as e:
         gdp.scan_noalloc(xy, big, 1.5, out_i, out_v, out_p, out_i)
