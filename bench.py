@@ -2,13 +2,19 @@
 """Benchmark of the gDP2d hot path on GB300: Steiner points inserted per second.
 
 One step = the whole hot path on one synthetic PSLG: the GPU CDT (the first step of
-Algorithm 1) and the refinement loop (the rest of Algorithm 1) of the mid workload
-(unit square + 100,000 uniform points + 1,000 random segments, B = sqrt 2).
+Algorithm 1) and the refinement loop (the rest of Algorithm 1).  The default
+workload is the paper-shaped one, the largest single-GPU configuration:
+1,000,164 FP64 points (uniform, Gaussian clusters, circles), 10,000 random
+segments plus 20 fans of 8 segments 5 degrees apart, B = sqrt 2.
 
-  value   Steiner points / (CDT + refine) device time, inputs resident in HBM
-  e2e     the same through the C ABI with host buffers: create (H2D inside),
-          refine and export (D2H) all in the timed region
-  roofline  dominant kernel: algorithmic bytes / average launch time vs HBM peak
+  value     Steiner points / (CDT + refine) device time, inputs resident in HBM,
+            un-instrumented steps
+  e2e       the same through the C ABI with host buffers: create (H2D inside),
+            refine and export (D2H) all in the timed region
+  roofline  the cavity-growth kernel (the largest refinement kernel), timed by
+            CUDA events inside the graph in separate instrumented steps:
+            algorithmic bytes per launch / launch time vs the HBM peak, plus its
+            FP64 rate vs the measured FP64 peak and its L2 traffic
   cpu_baseline  the sequential C oracle on the machine's host cores
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -30,32 +36,41 @@ sys.path.insert(0, ROOT)
 
 SQ2 = math.sqrt(2.0)
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
-CONFIG = {"workload": "mid: unit square + 100,000 uniform FP64 points + 1,000 random "
-                      "segments, B=sqrt(2)", "points": 100_004, "segments": 1_004, "B": SQ2,
-          "l2": "flushed between steps (512 MB write)"}
+L2_NOTE = "flushed between steps (512 MB write)"
+WORKLOAD_NAMES = {
+    "paper_shaped": "paper-shaped: 1,000,164 FP64 points (500k uniform, 300k in 100 Gaussian clusters, "
+                    "200k on 50 circles), 10,000 random segments + 20 fans of 8 segments 5 deg apart, "
+                    "B=sqrt(2)",
+    "mid": "mid: unit square + 100,000 uniform FP64 points + 1,000 random segments, B=sqrt(2)",
+    "contours": "contours: unit square + 20 families x 25 nested closed polylines x 200 vertices "
+                "(100,004 points and segments)",
+}
+# the reference arm's bounded sample: the same recipe at a quarter of the size
+REF_SAMPLE = {"n_uniform": 125_000, "n_gauss": 75_000, "n_circle": 50_000, "n_seg": 2_500, "n_fans": 5}
 
 # Algorithmic bytes of the dominant step of the refinement, cavity growth
-# (k_grow_w<0>, or k_grow_t<0> above 32,768 candidates; Sec. 5.2-5.3): what
-# each grown candidate must read and write once,
-# from the device layout (triangle T/N 16 B each, vertex 16 B FP64 + 8 B FP32
-# copy, marks 8 B), with the work counters the library reports:
-#   per candidate  134 = element id 4 + element triangle 16 + its 3 vertices 48
-#                        + candidate record written 66
-#   per walk step   56 = T 16 + N 16 + one new vertex 24
-#   per cavity tri  84 = T + N 32 + neighbour test (T 16 + apex 24) + list 4 + mark 8
-#   per boundary edge 56 = neighbour test 40 + boundary record 16
-GROW_BYTES = {"candidate": 134, "walk_step": 56, "cavity_tri": 84, "boundary_edge": 56}
+# (k_grow_w<0>, or k_grow_t<0> above 32,768 candidates; Sec. 5.2-5.3), per unit of
+# work the library counts on the device:
+#   per cavity of k triangles: the k cavity triangles and the k + 2 triangles
+#   across its boundary edges are read, each 12 B of vertex ids + 48 B of FP64
+#   coordinates, (2k + 2) * 60 B, and each cavity triangle gets an 8 B mark
+#   written and read back, 16 k B:  120 B per grown candidate + 136 B per cavity
+#   triangle;
+#   per point-location walk step: one triangle and its neighbours, 76 B.
+GROW_BYTES = {"candidate": 120, "cavity_tri": 136, "walk_step": 76}
 GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
 # the kernels of one refinement iteration (launched once per iteration, so an ncu
 # launch list counts them in every step and their shares compare directly)
-REFINE_KERNELS = ("k_scan_eval", "k_scan_count", "k_scan_write", "k_grow_w<0>", "k_grow_t<0>", "k_grow_big<0>", "k_survive",
-                  "k_depend", "k_insert_w<0>", "k_insert_t<0>", "k_link<0>")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cavity_growth_mid_traffic.md")
+REFINE_KERNELS = ("k_scan_eval", "k_scan_count", "k_scan_write", "k_grow_w<0>", "k_grow_t<0>", "k_grow_big<0>",
+                  "k_survive", "k_depend", "k_insert_w<0>", "k_insert_t<0>", "k_link<0>")
+# ncu counters of the cavity-growth kernels over one whole refine of the bench
+# workload, per grown candidate (DRAM and L2 bytes, FP64 flops, FP64 pipe)
+COUNTERS_FILE = os.path.join(ROOT, "profiles", "cavity_growth_paper_shaped_counters.md")
 
 
 def grow_bytes(st) -> float:
-    return (GROW_BYTES["candidate"] * st["grown"] + GROW_BYTES["walk_step"] * st["walk_steps"] +
-            GROW_BYTES["cavity_tri"] * st["cavity_tris"] + GROW_BYTES["boundary_edge"] * st["cavity_edges"])
+    return (GROW_BYTES["candidate"] * st["grown"] + GROW_BYTES["cavity_tri"] * st["cavity_tris"] +
+            GROW_BYTES["walk_step"] * st["walk_steps"])
 
 
 def grow_source_hash() -> str:
@@ -67,19 +82,21 @@ def grow_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per timed cavity-growth launch pair from the committed ncu
-    summary, or None
-    when the kernel's sources changed since it was captured."""
+def measured_counters():
+    """per-grown-candidate ncu counters of the cavity-growth kernels from the
+    committed summary, or {} when the kernels' sources changed since"""
     try:
-        with open(TRAFFIC_FILE) as f:
-            kv = dict(line.split(":", 1) for line in f
-                      if line.startswith(("source-hash:", "dram-bytes-per-launch:")))
-        if kv["source-hash"].strip() != grow_source_hash():
-            return None
-        return float(kv["dram-bytes-per-launch"])
+        kv = {}
+        with open(COUNTERS_FILE) as f:
+            for line in f:
+                if line.startswith("counter:"):
+                    k, v = line[len("counter:"):].split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source-hash") != grow_source_hash():
+            return {}
+        return {k: float(v) for k, v in kv.items() if k != "source-hash"}
     except Exception:
-        return None
+        return {}
 
 
 def parse():
@@ -90,10 +107,16 @@ def parse():
     ap.add_argument("--impl", default="gdp", choices=["gdp", "reference"])
     ap.add_argument("--B", type=float, default=SQ2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="mid", choices=["mid", "paper_shaped", "contours", "batched", "served"],
-                    help="mid: the headline line; paper_shaped / contours (with --max-len): the same "
+    ap.add_argument("--workload", default="paper_shaped",
+                    choices=["paper_shaped", "mid", "contours", "batched", "served"],
+                    help="paper_shaped: the headline line; mid / contours (with --max-len): the same "
                          "step on those inputs; batched / served: the batching and serving "
                          "configurations (one JSON line each)")
+    ap.add_argument("--roof-steps", type=int, default=2,
+                    help="instrumented steps (cavity growth timed inside the graph) for the roofline")
+    ap.add_argument("--measure-step", action="store_true",
+                    help="run exactly one CDT + refine of the workload and print its counters "
+                         "(the command the ncu counter captures run)")
     ap.add_argument("--count", type=int, default=4096, help="batched: number of PSLGs")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
     ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
@@ -409,7 +432,23 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def cpu_baseline(p, B, reps=3, max_len=0.0, name="mid"):
+def load_workload(name):
+    from paper_2007_00324_gb300 import workloads
+    return {"mid": workloads.mid, "paper_shaped": workloads.paper_shaped, "contours": workloads.contours}[name]()
+
+
+def workload_config(args, p):
+    config = {"workload": WORKLOAD_NAMES[args.workload], "points": p.n, "segments": p.m, "B": args.B,
+              "l2": L2_NOTE}
+    if args.max_len > 0:
+        config["max_len"] = args.max_len
+    for k in ("cand_cap", "cand_block", "graph_iters"):
+        if getattr(args, k):
+            config[k] = getattr(args, k)
+    return config
+
+
+def cpu_baseline(p, B, reps=1, max_len=0.0, name="paper_shaped"):
     """the oracle as it stands: CDT + sequential Ruppert on the host, one thread"""
     from oracle import oracle
     oracle.build()
@@ -421,7 +460,7 @@ def cpu_baseline(p, B, reps=3, max_len=0.0, name="mid"):
         steiner += m.n_steiner
     dt = time.perf_counter() - t0
     return {"value": steiner / dt, "unit": "Steiner pts/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full runs of the {name} workload (CDT + refine, {steiner // reps} "
+            "sample": f"{reps} full run(s) of the {name} workload (CDT + refine, {steiner // reps} "
                       f"Steiner points each), {dt:.2f} s"}
 
 
@@ -440,35 +479,61 @@ def replica_totals(ms, steiner, world, device):
 
 
 def run_reference(args):
+    """The oracle (the sequential CPU program the GPU path is checked against)
+    timed on the host: every step is a bounded sample of the workload, the
+    same recipe at a quarter of its size, so that K + W steps take minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2007_00324_gb300 import workloads
     from oracle import oracle
     oracle.build()
-    p = workloads.mid()
+    if args.workload == "paper_shaped":
+        p = workloads.paper_shaped(**REF_SAMPLE)
+        sample = (f"paper-shaped recipe at a quarter of the size ({p.n:,} points, {p.m:,} segments incl. "
+                  f"{p.meta['fans']} fans), one full CDT + refine per step")
+    else:
+        p = load_workload(args.workload)
+        sample = f"one full run of the {args.workload} workload per step"
     for _ in range(args.warmup):
         m = oracle.Mesh(p.xy, p.seg)
-        m.refine(args.B)
+        m.refine_len(args.B, args.max_len)
     times, steiner = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
         m = oracle.Mesh(p.xy, p.seg)
-        assert m.refine(args.B) == 0
+        assert m.refine_len(args.B, args.max_len) == 0
         times.append(time.perf_counter() - t0)
         steiner += m.n_steiner
     tot = sum(times)
     v = steiner / tot
-    line = {"metric": "Steiner points inserted per second (CDT + refine, mid workload)",
+    config = workload_config(args, load_workload(args.workload))   # the GPU arm's config
+    line = {"metric": f"Steiner points inserted per second (CDT + refine, {args.workload} workload)",
             "value": v, "unit": "Steiner pts/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": CONFIG, "impl": "reference",
+            "data": "synthetic", "config": config, "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "Steiner pts/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full runs of the mid workload"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "Steiner pts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_measure_step(args):
+    """exactly one CDT + refine of the workload (the ncu counter captures run
+    this), then its work counters"""
+    import torch
+    from paper_2007_00324_gb300 import gdp
+    gdp.load()
+    p = load_workload(args.workload)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    m = gdp.Mesh(p.xy, p.seg, stream=stream)
+    s = m.refine(args.B, **refine_kwargs(args))
+    keys = ("n_steiner", "iterations", "candidates", "grown", "cavity_tris", "cavity_edges", "walk_steps")
+    print(json.dumps({"workload": args.workload, "source_hash": grow_source_hash(),
+                      **{k: s[k] for k in keys}}), flush=True)
 
 
 def main():
@@ -479,7 +544,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
-    import numpy as np
+    if args.measure_step:
+        return run_measure_step(args)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -489,32 +555,22 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2007_00324_gb300 import gdp, workloads
+    from paper_2007_00324_gb300 import gdp
     gdp.load()
-    p = {"mid": workloads.mid, "paper_shaped": workloads.paper_shaped, "contours": workloads.contours}[
-        args.workload]()
-    config = dict(CONFIG) if args.workload == "mid" else {
-        "workload": {"paper_shaped": "paper-shaped: 1,000,164 points (uniform, Gaussian clusters, circles), "
-                                     "10,164 segments incl. 20 small-angle fans",
-                     "contours": "contours: unit square + 20 families x 25 nested closed polylines x 200 "
-                                 "vertices (100,004 points and segments)"}[args.workload],
-        "points": p.n, "segments": p.m, "B": args.B, "l2": CONFIG["l2"]}
-    if args.max_len > 0:
-        config["max_len"] = args.max_len
-    for k in ("cand_cap", "cand_block", "graph_iters"):
-        if getattr(args, k):
-            config[k] = getattr(args, k)
+    p = load_workload(args.workload)
+    config = workload_config(args, p)
     stream = torch.cuda.current_stream(dev)
     xy_d = torch.from_numpy(p.xy).to(dev)
     seg_d = torch.from_numpy(p.seg).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    def step():
+    def step(flags=0):
         m = gdp.Mesh(xy_d, seg_d, stream=stream, device=True)
-        s = m.refine(args.B, flags=gdp.REFINE_TIME_GROW, **refine_kwargs(args))
+        s = m.refine(args.B, flags=flags, **refine_kwargs(args))
         return m, s
 
-    for _ in range(max(args.warmup, 3)):
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
 
@@ -523,10 +579,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the timed steps: nothing instrumented
     times, steiner, launches = [], 0, 0
     stats = None
-    grow = {"grow_ms": 0.0, "grow_launches": 0, "timed_grown": 0, "timed_walk_steps": 0,
-            "timed_cavity_tris": 0, "timed_cavity_edges": 0}
     barrier()
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
@@ -540,8 +595,6 @@ def main():
             times.append(e0.elapsed_time(e1))
             steiner += stats["n_steiner"]
             launches += stats["launches"]
-            for k in grow:
-                grow[k] += stats[k]
             del m
         barrier()
     tot_ms, steiner_all = replica_totals(sum(times), steiner, world, dev)
@@ -567,6 +620,19 @@ def main():
            "h2d_bytes_per_step": int(p.xy.nbytes + p.seg.nbytes), "d2h_bytes_per_step": int(d2h),
            "ms_per_step": sum(e2e_ms) / len(e2e_ms)}
 
+    # roofline of the cavity growth, from separate instrumented steps: the
+    # growth launch pair of the first iteration of every graph replay is
+    # bracketed by CUDA events inside the graph (the events stall the graph,
+    # which is why the timed steps above run without them)
+    grow = {"grow_ms": 0.0, "grow_launches": 0, "timed_grown": 0, "timed_walk_steps": 0,
+            "timed_cavity_tris": 0, "timed_cavity_edges": 0}
+    for _ in range(max(1, args.roof_steps)):
+        flush.fill_(1.0)
+        m, rs = step(gdp.REFINE_TIME_GROW)
+        for k in grow:
+            grow[k] += rs[k]
+        del m
+
     # per-kernel device times of one more step, every launch bracketed by events
     os.environ["GDP_PROFILE"] = "1"
     flush.fill_(1.0)
@@ -577,26 +643,39 @@ def main():
     tot_k = sum(v[0] for v in kt.values())
     top = max(kt.items(), key=lambda kv: kv[1][0])
     peak, peak_kind = peaks()
-    # roofline of the cavity growth over the timed steps: algorithmic bytes from the
-    # work counters / device time from the events recorded around each launch
+    fp64_peak = gdp.measure_fp64_peak(stream)
     n_l = max(grow["grow_launches"], 1)
     timed = {k[len("timed_"):]: v for k, v in grow.items() if k.startswith("timed_")}
     by = grow_bytes(timed)
-    gbs = by / (grow["grow_ms"] / 1000.0) / 1e9 if grow["grow_ms"] > 0 else None
-    tr = measured_traffic()
+    sec = grow["grow_ms"] / 1000.0
+    gbs = by / sec / 1e9 if sec > 0 else None
+    cnt = measured_counters()
+    per_launch = timed["grown"] / n_l
+    traffic = cnt["dram_bytes_per_grown"] * per_launch if "dram_bytes_per_grown" in cnt else None
+    fp64 = {"peak": fp64_peak, "unit": "TFLOP/s", "peak_source": "measured (gdp_measure_fp64_peak)"}
+    if "fp64_flops_per_grown" in cnt and sec > 0:
+        a = cnt["fp64_flops_per_grown"] * timed["grown"] / sec / 1e12
+        fp64.update({"achieved": a, "frac": a / fp64_peak if fp64_peak > 0 else None,
+                     "flops_per_grown_candidate": cnt["fp64_flops_per_grown"],
+                     "pipe_busy_ncu": cnt.get("fp64_pipe_busy")})
+    l2 = None
+    if "l2_bytes_per_grown" in cnt and sec > 0:
+        l2 = {"bytes_per_launch": cnt["l2_bytes_per_grown"] * per_launch,
+              "achieved": cnt["l2_bytes_per_grown"] * timed["grown"] / sec / 1e9, "unit": "GB/s"}
+    share = sum(kt.get(k, (0.0, 0))[0] for k in ("k_grow_w<0>", "k_grow_t<0>"))
     roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-            "frac": (gbs / peak) if gbs else None, "traffic": tr,
+            "frac": (gbs / peak) if gbs else None, "traffic": traffic,
             "kernel": "cavity growth: k_grow_w<0> + k_grow_t<0>", "algorithmic_bytes_per_launch": by / n_l,
             "kernel_ms_per_launch": grow["grow_ms"] / n_l, "launches": grow["grow_launches"],
-            "share_of_kernel_time": sum(kt.get(k, (0.0, 0))[0] for k in ("k_grow_w<0>", "k_grow_t<0>")) / tot_k,
-            "share_of_refine_kernel_time": sum(kt.get(k, (0.0, 0))[0] for k in ("k_grow_w<0>", "k_grow_t<0>")) /
-            max(sum(kt.get(k, (0.0, 0))[0] for k in REFINE_KERNELS), 1e-9),
+            "grown_candidates_per_launch": per_launch,
+            "share_of_kernel_time": share / tot_k,
+            "share_of_refine_kernel_time": share / max(sum(kt.get(k, (0.0, 0))[0] for k in REFINE_KERNELS), 1e-9),
             "largest_kernel": top[0],
             "peak_source": "measured (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
-            "timed_launches": "the first iteration of every 8-iteration graph replay",
+            "timed_launches": f"the first iteration of every graph replay, {args.roof_steps} instrumented steps",
             "mean_cavity_tris": timed["cavity_tris"] / max(timed["grown"], 1),
-            "mean_boundary_edges": timed["cavity_edges"] / max(timed["grown"], 1),
-            "mean_walk_steps": timed["walk_steps"] / max(timed["grown"], 1)}
+            "mean_walk_steps": timed["walk_steps"] / max(timed["grown"], 1),
+            "fp64": fp64, "l2": l2}
 
     if rank != 0:
         if world > 1:
@@ -604,7 +683,7 @@ def main():
         return
     line = {"metric": f"Steiner points inserted per second (CDT + refine, {args.workload} workload)",
             "value": value, "unit": "Steiner pts/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": tot_ms / args.steps,
+            "warmup": warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(config, parallelism=f"replicas x{world}"),
             "refine_ms": stats["refine_ms"], "cdt_ms": stats["cdt_ms"],
@@ -614,7 +693,7 @@ def main():
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk.summary(),
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(p, args.B, 3 if args.workload != "paper_shaped" else 1,
+        line["cpu_baseline"] = cpu_baseline(p, args.B, 1 if args.workload == "paper_shaped" else 3,
                                             args.max_len, args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -38,7 +38,8 @@ typedef enum {
     GDP_OK = 0,
     GDP_ERR_INPUT = 1,       /* NaN/inf coordinate, duplicate point, bad index, crossing
                                 segments, segment through a vertex, empty domain */
-    GDP_ERR_NOMEM = 2,       /* device allocation failed or a mesh ran out of slots */
+    GDP_ERR_NOMEM = 2,       /* device allocation failed, or a mesh ran out of slots and
+                                could not be given more (see gdp_mesh_refine) */
     GDP_ERR_ITER_LIMIT = 3,  /* refinement hit max_iter */
     GDP_ERR_WALK_LIMIT = 4,  /* a point-location walk exceeded its step bound */
     GDP_ERR_CUDA = 5,        /* CUDA runtime error or no device */
@@ -86,10 +87,30 @@ typedef struct {
     double grow_ms;
     int64_t grow_launches;
     int64_t timed_grown, timed_cavity_tris, timed_cavity_edges, timed_walk_steps;
+    /* capacity growth: times the pool was re-laid out with more slots for the
+     * meshes that ran short (each time doubling their Steiner capacity) */
+    int64_t grow_steps;
+    /* with GDP_REFINE_FLIPFLOP: flips, flops (point removals) and redundant
+     * points removed, summed over the iterations */
+    int64_t flips, flops, redundant_removed;
 } gdp_stats;
 
 /* gdp_refine_opts.flags */
 #define GDP_REFINE_TIME_GROW 1
+/* Chew's rule (Sec. 4.2): a subsegment is encroached by a vertex or splitting
+ * point strictly inside its diametral lens -- where the subsegment subtends
+ * more than 120 degrees -- instead of its diametral circle (Ruppert's rule,
+ * the default).  Only the encroachment region changes: split points, shells,
+ * priorities and the quality test stay those of the default mode. */
+#define GDP_REFINE_CHEW 2
+/* Flip-Flop insertion (Sec. 4.3, the paper's gDP2d): the splitting points that
+ * survive the cavity filter all go in by splitting their triangles, then
+ * parallel flips restore the constrained Delaunay property, and of two points
+ * of one iteration joined by an edge (Delaunay dependent, Sec. 4.2) the one
+ * with the lower priority is removed again by flips and a flop; the default
+ * is cavity (Bowyer-Watson) insertion with the dependence check before it.
+ * Iterations are driven from the host (no CUDA graph). */
+#define GDP_REFINE_FLIPFLOP 4
 
 /* Build the CDT of a PSLG on the GPU (the first step of Algorithm 1).
  *   xy:  2*n_pts doubles, host;   seg: 2*n_seg int32 indices, host (may be NULL if 0)
@@ -106,7 +127,15 @@ int gdp_mesh_create_device(const double* xy_device, int64_t n_pts, const int32_t
 
 /* Refine (the loop of Algorithm 1) until nothing is encroached and no
  * triangle is bad, bad triangles at small input angles excepted (Sec. 4.1).
- * opts may be NULL (defaults); stats may be NULL.  Blocks until done. */
+ * opts may be NULL (defaults); stats may be NULL.  Blocks until done.
+ * Slots: a mesh starts with room for 3 Steiner points per input point plus 64
+ * per segment (GDP_STEINER_PER_POINT / _PER_SEGMENT).  When it has used three
+ * quarters of them, or an iteration's insertions do not fit, the pool is laid
+ * out again between graph replays with twice the Steiner capacity for that
+ * mesh (at most 20 times, GDP_GROW_LIMIT); the deferred insertions are
+ * retried, so the result does not depend on the starting capacity.  If the
+ * larger pool cannot be allocated, the mesh stops with GDP_ERR_NOMEM and is
+ * still a valid CDT that can be exported. */
 int gdp_mesh_refine(gdp_mesh* mesh, const gdp_refine_opts* opts, gdp_stats* stats);
 
 /* Copy the mesh out.  Call with NULL buffers to get the sizes only.
@@ -145,6 +174,12 @@ int gdp_mesh_split_subsegments(gdp_mesh* mesh, const double* abxy, int64_t n);
  * *count receives the number of elements (all of them, even beyond cap). */
 int gdp_mesh_scan(gdp_mesh* mesh, double B, int32_t* kind, int32_t* verts, double* pt,
                   uint32_t* meas, int64_t cap, int64_t* count);
+
+/* The same with the encroachment region of flags (GDP_REFINE_CHEW: the
+ * diametral lens, Sec. 4.2; 0: the diametral circle, as gdp_mesh_scan).
+ * GDP_ERR_INPUT for B <= 0 or an unknown flag. */
+int gdp_mesh_scan_mode(gdp_mesh* mesh, double B, int32_t flags, int32_t* kind, int32_t* verts,
+                       double* pt, uint32_t* meas, int64_t cap, int64_t* count);
 
 /* Consistency of the device mesh (a test hook): counts[0..4] receive the
  * number of neighbour links that are not mutual, links whose shared edge does
@@ -294,6 +329,16 @@ int gdp_scan_noalloc(const double* xy_device, int64_t n_vert, const int32_t* tri
                      int64_t n_tri, double B, int32_t* kind_device, int32_t* verts_device,
                      double* pt_device, uint32_t* meas_device, int64_t cap, int64_t* count,
                      void* cuda_stream);
+
+/* ---------------- measurement ----------------
+ * Not a step of the paper: the FP64 throughput of the current device, the
+ * denominator of the FP64 roofline of the refinement kernels.  One kernel of
+ * independent fused multiply-add chains (two flops each) over 8 blocks of 256
+ * threads per SM, timed with CUDA events on cuda_stream (NULL: the legacy
+ * default stream); *tflops receives the best of three timed launches after a
+ * warm-up.  Allocates nothing.  Errors: GDP_ERR_INPUT (tflops NULL),
+ * GDP_ERR_CUDA. */
+int gdp_measure_fp64_peak(void* cuda_stream, double* tflops);
 
 const char* gdp_status_str(int status);
 

@@ -16,6 +16,7 @@
 
 #include "gdp.h"
 #include "gdp_cdt.cuh"
+#include "gdp_flipflop.cuh"
 
 using namespace gdp;
 
@@ -121,6 +122,57 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
   }
 }
 
+// Capacity growth: mesh m's triangles, vertices and links copied from the old
+// pool O into the new layout Q (new bases in nb: x = triangle, y = vertex),
+// every triangle and vertex id rebased; flags, dirty bits and priority buckets
+// move with their slots.  Mesh-local slot order is unchanged, so the
+// refinement continues exactly as it would have without the move.
+__global__ void k_regrow(Pool Q, Pool O, const int2* nb) {
+  for (int m = blockIdx.y; m < O.n_mesh; m += gridDim.y) {
+    const MeshInfo& M = O.mi[m];
+    const int ot = M.tri_base, ov = M.vert_base, qt = nb[m].x, qv = nb[m].y;
+    const int dv = qv - ov, dt = qt - ot;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (int t = gt; t < M.tri_count; t += gs) {
+      const int4 T4 = O.T[ot + t];
+      const int4 N4 = O.N[ot + t];
+      Q.T[qt + t] = T4.w < 0 ? T4 : make_int4(T4.x + dv, T4.y + dv, T4.z + dv, T4.w);
+      int r[3] = {N4.x, N4.y, N4.z};
+      for (int e = 0; e < 3; ++e)
+        if (r[e] >= 0) r[e] = (((r[e] >> 2) + dt) << 2) | (r[e] & 3);
+      Q.N[qt + t] = make_int4(r[0], r[1], r[2], N4.w);
+      Q.dirty[qt + t] = O.dirty[ot + t];
+      Q.flag[qt + t] = O.flag[ot + t];
+      Q.cbucket[qt + t] = O.cbucket[ot + t];
+    }
+    for (int v = gt; v < M.vert_count; v += gs) {
+      Q.V[qv + v] = O.V[ov + v];
+      Q.Vf[qv + v] = O.Vf[ov + v];
+      Q.vseg[qv + v] = O.vseg[ov + v];
+      const int tv = O.vtri[ov + v];
+      Q.vtri[qv + v] = tv >= 0 ? tv + dt : -1;
+      const int lc = O.loc[ov + v];
+      Q.loc[qv + v] = lc >= 0 ? lc + dt : -1;
+      Q.apex[qv + v] = O.apex[ov + v];
+    }
+    // input segments hold vertex ids: rebase them in place (one thread per segment)
+    for (int g = gt; g < M.n_seg; g += gs) {
+      const int2 sg = O.seg[M.seg_base + g];
+      Q.seg[M.seg_base + g] = make_int2(sg.x + dv, sg.y + dv);
+    }
+  }
+}
+
+// meshes taken out of the refinement (status set by the host): their flagged
+// elements would keep producing candidates, so their flags are cleared
+__global__ void k_drop_inactive(Pool P) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int t = gt; t < P.n_slots; t += gs) {
+    const int w = P.T[t].w;
+    if (w >= 0 && !P.mi[w >> 4].active) P.flag[t] = 0;
+  }
+}
+
 #define CK(x)                                                                         \
   do {                                                                                \
     cudaError_t e_ = (x);                                                             \
@@ -157,10 +209,19 @@ __global__ void k_set_loc(Pool P, const int* ids, int n, int t) {
     (h).prof_end();                                                  \
   } while (0)
 // candidate cavities: own slots, then the two spill tiers
+// (above warp_max candidates: a group of lanes per candidate, or one thread
+// per candidate with GDP_GROW_GROUP=0)
+#define LAUNCH_GROW_PAIR(h, MODE, P, timed)                          \
+  do {                                                               \
+    LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P, timed);       \
+    if ((h).grow_group)                                              \
+      LAUNCH_B(h, k_grow_g<MODE>, (h).n_sm * 16, 128, P, timed);     \
+    else                                                             \
+      LAUNCH_C(h, k_grow_t<MODE>, P, timed);                         \
+  } while (0)
 #define LAUNCH_GROW(h, MODE, P)                                      \
   do {                                                               \
-    LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P, 0);           \
-    LAUNCH_C(h, k_grow_t<MODE>, P, 0);                               \
+    LAUNCH_GROW_PAIR(h, MODE, P, 0);                                 \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_A / 4, 128, P, 0);           \
     LAUNCH_B(h, k_grow_big<MODE>, LANES_B / 4, 128, P, 1);                 \
   } while (0)
@@ -448,9 +509,20 @@ struct PoolHost {
     return GDP_OK;
   }
   int refine(const double* B, const gdp_refine_opts* o);
+  // capacity growth (refinement): meshes that asked for more slots get twice
+  // their Steiner capacity in a new pool layout, at most grow_limit times
+  int grow_meshes();
+  int grow_steps = 0, grow_limit = 20;
+  // Flip-Flop insertion (GDP_REFINE_FLIPFLOP): its arrays, sized for the pool
+  bool ff_ready = false;
+  int32_t *ffA = nullptr, *ffB = nullptr;   // the pass lists
+  int ff_alloc();
+  void ff_free();
+  int ff_iteration();
   int launch_iteration(int k);
   dim3 mesh_grid = dim3(1, 1);    // per-mesh kernels: (blocks per mesh, meshes)
   int bs_cand = 64;               // per-candidate kernels: threads per block
+  bool grow_group = true;         // above warp_max candidates: k_grow_g (else k_grow_t)
   bool capped = false;            // some mesh has a per-iteration candidate cap
   void set_cand_block(int b) {
     bs_cand = (b == 32 || b == 128 || b == 256) ? b : 64;
@@ -473,6 +545,8 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   G = 4 * n_sm;
   set_cand_block(64);
   prof = std::getenv("GDP_PROFILE") != nullptr;
+  grow_group = env_double("GDP_GROW_GROUP", 1.0) != 0.0;
+  grow_limit = (int)env_double("GDP_GROW_LIMIT", 20.0);
   if (!(hctrl = ctrl_get())) return GDP_ERR_NOMEM;
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
@@ -1043,8 +1117,7 @@ int PoolHost::launch_iteration(int k) {
   const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   const int timed = (time_grow && k == 0) ? 1 : 0;
   if (timed) CK(cudaEventRecordWithFlags(tg[0], stream, rec));
-  LAUNCH_B(*this, k_grow_w<0>, n_sm * 16, 128, P, timed);
-  LAUNCH_C(*this, k_grow_t<0>, P, timed);
+  LAUNCH_GROW_PAIR(*this, 0, P, timed);
   if (timed) CK(cudaEventRecordWithFlags(tg[1], stream, rec));
   LAUNCH_B(*this, k_grow_big<0>, LANES_A / 4, 128, P, 0);
   LAUNCH_B(*this, k_grow_big<0>, LANES_B / 4, 128, P, 1);
@@ -1067,6 +1140,202 @@ int PoolHost::add_grow_times(int iters) {
   return GDP_OK;
 }
 
+// ---------------------------------------------------------------- Flip-Flop insertion
+void PoolHost::ff_free() {
+  for (void* q : {(void*)P.tstamp, (void*)P.lstamp, (void*)P.fprop, (void*)P.fop, (void*)ffA, (void*)ffB,
+                  (void*)P.ffmark, (void*)P.vkey, (void*)P.vred, (void*)P.vmap})
+    if (q) release(q);
+  P.tstamp = P.lstamp = P.fprop = P.fop = nullptr;
+  ffA = ffB = nullptr;
+  P.ffmark = P.vkey = nullptr;
+  P.vred = P.vmap = nullptr;
+  ff_ready = false;
+}
+
+int PoolHost::ff_alloc() {
+  if (ff_ready) return GDP_OK;
+  int st;
+  const size_t T = (size_t)P.n_slots, V = (size_t)P.n_verts;
+  if ((st = alloc(&P.tstamp, T)) != GDP_OK || (st = alloc(&P.lstamp, T)) != GDP_OK ||
+      (st = alloc(&P.fprop, T)) != GDP_OK || (st = alloc(&P.fop, T)) != GDP_OK ||
+      (st = alloc(&ffA, T)) != GDP_OK || (st = alloc(&ffB, T)) != GDP_OK ||
+      (st = alloc(&P.ffmark, T)) != GDP_OK || (st = alloc(&P.vkey, V)) != GDP_OK ||
+      (st = alloc(&P.vred, V)) != GDP_OK || (st = alloc(&P.vmap, V)) != GDP_OK) {
+    ff_free();
+    return st;
+  }
+  ff_ready = true;
+  return GDP_OK;
+}
+
+// One iteration of Algorithm 1 with Flip-Flop insertion: the scan and the
+// cavity filter as in launch_iteration, then every survivor split in, then
+// passes of flips and flops until no edge is locally non-Delaunay and no
+// point of this iteration is redundant, then the removed points compacted
+// away.  Host-driven: the control block is read every four passes.
+int PoolHost::ff_iteration() {
+  const bool trace = std::getenv("GDP_TRACE") != nullptr;
+  LAUNCH(*this, k_scan_eval, G, P);
+  LAUNCH(*this, k_scan_count, G, P, capped ? 1 : 0);
+  if (capped) {
+    LAUNCH(*this, k_cap_select, G, P);
+    LAUNCH(*this, k_cap_count, G, P);
+  }
+  LAUNCH(*this, k_scan_write, G, P, capped ? 1 : 0);
+  LAUNCH_GROW_PAIR(*this, 0, P, 0);
+  LAUNCH_B(*this, k_grow_big<0>, LANES_A / 4, 128, P, 0);
+  LAUNCH_B(*this, k_grow_big<0>, LANES_B / 4, 128, P, 1);
+  LAUNCH_C(*this, k_survive, P);
+  LAUNCH(*this, k_ff_prep, G, P);
+  LAUNCH(*this, k_offsets, G, P);
+  int32_t *cur = ffA, *nxt = ffB;
+  Pool Q = P;
+  Q.fl_cur = cur;
+  Q.fl_nxt = nxt;
+  LAUNCH_C(*this, k_ff_split, Q);
+  LAUNCH_C(*this, k_ff_split_link, Q);
+  LAUNCH_B(*this, k_fl_next, 1, 1, Q);
+  std::swap(cur, nxt);
+  CK(cudaGetLastError());
+  int passes = 0;
+  for (int check = 0;; ++check) {
+    for (;;) {
+      for (int k = 0; k < 4; ++k) {
+        Q.fl_cur = cur;
+        Q.fl_nxt = nxt;
+        LAUNCH(*this, k_ff_propose, G, Q);
+        LAUNCH(*this, k_ff_do, G, Q);
+        LAUNCH(*this, k_ff_link, G, Q);
+        LAUNCH_B(*this, k_fl_next, 1, 1, Q);
+        std::swap(cur, nxt);
+      }
+      passes += 4;
+      if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (hctrl->err) return GDP_OK;   // the caller reads the error
+      if (hctrl->n_fl == 0) break;
+      if (trace && passes == 2000) {
+        std::fprintf(stderr, "[ff] iteration %llu: list still %d after %d passes\n",
+                     (unsigned long long)hctrl->iters, hctrl->n_fl, passes);
+        Q.fl_cur = cur;
+        LAUNCH_B(*this, k_ff_debug, 1, 1, Q, 12);
+        CK(cudaStreamSynchronize(stream));
+      }
+      if (passes > 100000) {
+        if (set_ctrl_field(offsetof(Ctrl, dbg), 4) != GDP_OK) return GDP_ERR_CUDA;
+        return set_ctrl_field(offsetof(Ctrl, err), S_INTERNAL);
+      }
+    }
+    // no edge left to flip: is any point of this iteration redundant?
+    CK(cudaMemsetAsync(&P.ctrl->ff_marked, 0, sizeof(int), stream));
+    Q.fl_cur = cur;
+    Q.fl_nxt = nxt;
+    LAUNCH(*this, k_ff_check, G, Q);
+    LAUNCH(*this, k_ff_push_stars, G, Q);
+    LAUNCH_B(*this, k_fl_next, 1, 1, Q);
+    std::swap(cur, nxt);
+    if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+    if (hctrl->err) return GDP_OK;
+    if (trace)
+      std::fprintf(stderr, "[ff] iteration %llu check %d: %d redundant, %d passes, flips %llu flops %llu\n",
+                   (unsigned long long)hctrl->iters, check, hctrl->ff_marked, passes,
+                   (unsigned long long)hctrl->ff_flips, (unsigned long long)hctrl->ff_flops);
+    if (hctrl->ff_marked == 0) break;
+    if (check > 10000) {
+      if (set_ctrl_field(offsetof(Ctrl, dbg), 5) != GDP_OK) return GDP_ERR_CUDA;
+      return set_ctrl_field(offsetof(Ctrl, err), S_INTERNAL);
+    }
+  }
+  const int mb = std::min(n_mesh, 4096);
+  LAUNCH_B(*this, k_ff_vmap, mb, FF_CT, P);
+  LAUNCH(*this, k_ff_rename, G, P);
+  LAUNCH_B(*this, k_ff_move, mb, FF_CT, P);
+  return cudaGetLastError() == cudaSuccess ? GDP_OK : GDP_ERR_CUDA;
+}
+
+int PoolHost::grow_meshes() {
+  if (pull_mi() != GDP_OK) return GDP_ERR_CUDA;
+  std::vector<int> need(n_mesh);
+  bool any = false;
+  for (int m = 0; m < n_mesh; ++m) {
+    need[m] = hmi[m].need_grow;
+    hmi[m].need_grow = 0;
+    any |= need[m] != 0;
+  }
+  // the new layout: twice the Steiner capacity for every mesh that asked
+  std::vector<MeshInfo> nmi = hmi;
+  long long tb = 0, vb = 0;
+  for (int m = 0; m < n_mesh; ++m) {
+    MeshInfo& M = nmi[m];
+    if (need[m]) {
+      const long long fixed = (long long)M.n_in + N_AUX;
+      const long long vcap = fixed + 2 * ((long long)M.vert_cap - fixed);
+      M.vert_cap = (int)std::min<long long>(vcap, (1ll << 30));
+      M.tri_cap = (int)std::min<long long>(2ll * M.vert_cap + 16, (1ll << 29));
+    }
+    M.tri_base = (int)tb;
+    M.vert_base = (int)vb;
+    tb += M.tri_cap;
+    vb += M.vert_cap;
+  }
+  Pool Q = P;
+  std::vector<void*> fresh;
+  int st = (any && grow_steps < grow_limit && tb < (1ll << 29) && vb < (1ll << 31) - 1) ? GDP_OK : GDP_ERR_NOMEM;
+  auto take = [&](auto** ptr, size_t n, int fill) {
+    if (st != GDP_OK) return;
+    st = alloc(ptr, n, fill);
+    if (st == GDP_OK) fresh.push_back((void*)*ptr);
+  };
+  take(&Q.V, vb, 0); take(&Q.Vf, vb, 0); take(&Q.vseg, vb, 0xff); take(&Q.vtri, vb, 0xff);
+  take(&Q.apex, vb, 0); take(&Q.loc, vb, 0xff);
+  take(&Q.T, tb, 0xff); take(&Q.N, tb, 0xff); take(&Q.mark, tb, 0); take(&Q.newref, 4 * (size_t)tb, 0xff);
+  take(&Q.dirty, tb, 0); take(&Q.flag, tb, 0); take(&Q.cbucket, tb, 0); take(&Q.tbest, tb, 0);
+  int2* nb = nullptr;
+  take(&nb, n_mesh, 0);
+  if (st != GDP_OK) {
+    // no room for a larger pool (or the limit is reached): the meshes whose
+    // insertions no longer fit stop with GDP_ERR_NOMEM and stay valid CDTs
+    for (void* q : fresh) release(q);
+    bool dropped = false;
+    for (int m = 0; m < n_mesh; ++m)
+      if (need[m] == 2) {
+        hmi[m].status = S_NOMEM;
+        hmi[m].active = 0;
+        dropped = true;
+      }
+    if (push_mi() != GDP_OK) return GDP_ERR_CUDA;
+    if (dropped) LAUNCH(*this, k_drop_inactive, G, P);
+    return set_ctrl_field(offsetof(Ctrl, grow), 0);
+  }
+  std::vector<int2> hb(n_mesh);
+  for (int m = 0; m < n_mesh; ++m) hb[m] = make_int2(nmi[m].tri_base, nmi[m].vert_base);
+  CK(cudaMemcpyAsync(nb, hb.data(), sizeof(int2) * n_mesh, cudaMemcpyHostToDevice, stream));
+  Q.n_slots = (int)tb;
+  Q.n_verts = (int)vb;
+  int most = 1;
+  for (const MeshInfo& M : hmi) most = std::max(most, std::max(M.tri_count, M.vert_count));
+  LAUNCH(*this, k_regrow, dim3(std::min(256, (most + 1023) / 1024), std::min(n_mesh, 65535)), Q, P, nb);
+  CK(cudaGetLastError());
+  for (void* q : {(void*)P.V, (void*)P.Vf, (void*)P.vseg, (void*)P.vtri, (void*)P.apex, (void*)P.loc,
+                  (void*)P.T, (void*)P.N, (void*)P.mark, (void*)P.newref, (void*)P.dirty, (void*)P.flag,
+                  (void*)P.cbucket, (void*)P.tbest})
+    release(q);
+  release(nb);
+  P = Q;
+  hmi = nmi;
+  if (push_mi() != GDP_OK) return GDP_ERR_CUDA;
+  if (ff_ready) {   // per-pass scratch only: a fresh set for the new sizes
+    ff_free();
+    const int fs = ff_alloc();
+    if (fs != GDP_OK) return fs;
+  }
+  // the last iteration's marks were left behind in the old pool
+  if (set_ctrl_field(offsetof(Ctrl, prev_cand), 0) != GDP_OK) return GDP_ERR_CUDA;
+  if (set_ctrl_field(offsetof(Ctrl, grow), 0) != GDP_OK) return GDP_ERR_CUDA;
+  ++grow_steps;
+  stats.grow_steps = grow_steps;
+  return GDP_OK;
+}
+
 int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   gdp_refine_opts d{};
   if (o) d = *o;
@@ -1084,10 +1353,21 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
     M.active = M.status == S_OK ? 1 : 0;
     M.steiner = 0;
     M.cand_cap = d.cand_cap;
+    M.lens = (d.flags & GDP_REFINE_CHEW) ? 1 : 0;
+    M.need_grow = 0;
   }
   if (push_mi() != GDP_OK) return GDP_ERR_CUDA;
+  const bool ff = (d.flags & GDP_REFINE_FLIPFLOP) != 0;
+  if (ff) {
+    const int fs = ff_alloc();
+    if (fs != GDP_OK) return fs;
+    CK(cudaMemsetAsync(P.ffmark, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
+    CK(cudaMemsetAsync(P.tstamp, 0, sizeof(int32_t) * (size_t)P.n_slots, stream));
+    CK(cudaMemsetAsync(P.lstamp, 0, sizeof(int32_t) * (size_t)P.n_slots, stream));
+  }
   std::memset(hctrl, 0, sizeof(Ctrl));
   hctrl->need_eval = 1;   // every triangle is evaluated with this call's bounds
+  hctrl->step = 1;        // Flip-Flop passes: slot stamps start at 0, below every pass
   CK(cudaMemcpyAsync(P.ctrl, hctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
   CK(cudaEventRecord(ev0, stream));
   // a call that stopped with candidates (iteration limit, error) leaves their
@@ -1107,7 +1387,25 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
       tg.push_back(e);
     }
   }
-  if (giters > 0 && !prof) {
+  if (ff) {
+    for (;;) {
+      if (ff_iteration() != GDP_OK) return GDP_ERR_CUDA;
+      if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (hctrl->err) {
+        if (std::getenv("GDP_TRACE"))
+          std::fprintf(stderr, "[ff] error %d at check site %d, iteration %llu\n", hctrl->err, hctrl->dbg,
+                       (unsigned long long)hctrl->iters);
+        status = hctrl->err;
+        break;
+      }
+      if (hctrl->grow) {
+        const int g = grow_meshes();
+        if (g != GDP_OK) return g;
+      }
+      if (hctrl->n_cand == 0) break;
+      if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
+    }
+  } else if (giters > 0 && !prof) {
     for (;;) {
       const int tag = ((giters * 2 + (time_grow ? 1 : 0)) * 2 + (capped ? 1 : 0)) * 512 + bs_cand;
       const int st = replay(g_refine, tag, [&] {
@@ -1121,6 +1419,10 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
       if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
       if (add_grow_times(giters) != GDP_OK) return GDP_ERR_CUDA;
       if (hctrl->err) { status = hctrl->err; break; }
+      if (hctrl->grow) {   // deferred insertions are retried in the next iterations
+        const int g = grow_meshes();
+        if (g != GDP_OK) return g;
+      }
       if (hctrl->n_cand == 0) break;
       if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
     }
@@ -1130,6 +1432,10 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
       if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
       if (add_grow_times(1) != GDP_OK) return GDP_ERR_CUDA;
       if (hctrl->err) { status = hctrl->err; break; }
+      if (hctrl->grow) {   // deferred insertions are retried in the next iterations
+        const int g = grow_meshes();
+        if (g != GDP_OK) return g;
+      }
       if (hctrl->n_cand == 0) break;
       if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
     }
@@ -1152,6 +1458,9 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   stats.timed_cavity_tris = (int64_t)hctrl->t_cav;
   stats.timed_cavity_edges = (int64_t)hctrl->t_bnd;
   stats.timed_walk_steps = (int64_t)hctrl->t_walk;
+  stats.flips = (int64_t)hctrl->ff_flips;
+  stats.flops = (int64_t)hctrl->ff_flops;
+  stats.redundant_removed = (int64_t)hctrl->ff_removed;
   long long st = 0, nt = 0;
   for (auto& M : hmi) {
     st += M.steiner;
@@ -1386,7 +1695,12 @@ int gdp_mesh_split_subsegments(gdp_mesh* g, const double* abxy, int64_t n) {
 
 int gdp_mesh_scan(gdp_mesh* g, double B, int32_t* kind, int32_t* verts, double* pt, uint32_t* meas,
                   int64_t cap, int64_t* count) {
-  if (!g || !count) return GDP_ERR_INPUT;
+  return gdp_mesh_scan_mode(g, B, 0, kind, verts, pt, meas, cap, count);
+}
+
+int gdp_mesh_scan_mode(gdp_mesh* g, double B, int32_t flags, int32_t* kind, int32_t* verts, double* pt,
+                       uint32_t* meas, int64_t cap, int64_t* count) {
+  if (!g || !count || !(B > 0) || (flags & ~GDP_REFINE_CHEW)) return GDP_ERR_INPUT;
   PoolHost& h = g->h;
   if (h.pull_mi() != GDP_OK) return GDP_ERR_CUDA;
   const MeshInfo& M = h.hmi[0];
@@ -1398,7 +1712,7 @@ int gdp_mesh_scan(gdp_mesh* g, double B, int32_t* kind, int32_t* verts, double* 
   if ((st = h.alloc(&dk, c)) || (st = h.alloc(&dv, 3 * c)) || (st = h.alloc(&dp, c)) ||
       (st = h.alloc(&dm, c)) || (st = h.alloc(&dc, 1)))
     return st;
-  LAUNCH(h, k_scan_report, h.G, h.P, B * B, dk, dv, dp, dm, (int)cap, dc);
+  LAUNCH(h, k_scan_report, h.G, h.P, B * B, (flags & GDP_REFINE_CHEW) ? 1 : 0, dk, dv, dp, dm, (int)cap, dc);
   CK(cudaGetLastError());
   int cnt = 0;
   CK(cudaMemcpyAsync(&cnt, dc, sizeof(int), cudaMemcpyDeviceToHost, h.stream));

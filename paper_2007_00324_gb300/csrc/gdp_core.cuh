@@ -59,6 +59,11 @@ struct MeshInfo {
   int32_t steiner;       // Steiner points inserted by refinement
   int32_t has_apex;      // some input angle below 60 degrees
   int32_t cand_cap;      // per-iteration candidate cap (0 = none)
+  int32_t lens;          // encroachment by the diametral lens (Chew), else the circle
+  int32_t need_grow;     // refinement: 1 = under a quarter of the slots left, 2 = an
+                         // iteration's insertions did not fit (the host grows the pool)
+  int32_t ff_v0;         // Flip-Flop: vert_count at the start of this iteration (the
+                         // vertices from here on were inserted in this iteration)
   int32_t pts_base;      // offset of this mesh's points in the construction list
   int32_t tmp;           // scratch for per-mesh reductions
   double B2;
@@ -91,6 +96,10 @@ struct Ctrl {
   unsigned long long t_grown, t_cav, t_bnd, t_walk;
   int32_t grow_next;     // k_grow_t: next candidate to hand out
   int32_t need_eval;     // some triangles are marked dirty (construction, relocation)
+  int32_t grow;          // some mesh asks for more slots (MeshInfo::need_grow)
+  int32_t ff_marked;     // Flip-Flop: points found redundant by the last check
+  int32_t dbg;           // which internal check failed first (GDP_TRACE reports it)
+  unsigned long long ff_flips, ff_flops, ff_removed;   // Flip-Flop work counters
 };
 
 struct Pool {
@@ -164,6 +173,12 @@ struct Pool {
   unsigned long long* segmark;
   uint8_t* ext;
   int32_t* remap;
+  // Flip-Flop insertion (refinement with GDP_REFINE_FLIPFLOP; allocated on first use)
+  unsigned long long* vkey;    // per vertex: priority key of a point inserted this iteration
+  int32_t* vred;               // per vertex: bit 0 redundant, bit 1 removed
+  int32_t* vmap;               // per vertex: id after the removed points are compacted away
+  unsigned long long* ffmark;  // per slot: flip / flop ownership marks
+  int32_t* fop;                // per list entry: operation kind of the proposal
 };
 
 }  // namespace gdp

@@ -250,7 +250,7 @@ __device__ int eval_tri(const Pool& P, int t) {
     for (int e = 0; e < 3; ++e) {
       if (!((cons >> e) & 1)) continue;
       const P2 u = pt(P, comp(T4, mod3(e + 1))), v = pt(P, comp(T4, mod3(e + 2)));
-      if (dot_sign(u, v, pt(P, comp(T4, e))) < 0) {
+      if (encroaches(u, v, pt(P, comp(T4, e)), M.lens)) {
         const double l = seg_measure(u.d, v.d);
         if (l > bl) { bl = l; best = e; }
       }
@@ -613,8 +613,8 @@ __device__ __forceinline__ bool cav_add(const CavBuf& B, int& k, int t) {
   return true;
 }
 
-__device__ int grow(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1, bool conv, int& nc,
-                    int& nb, int& ct, int& ce) {
+__device__ int grow(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1, bool conv, bool lens,
+                    int& nc, int& nb, int& ct, int& ce) {
   if (B.hash)
     for (int j = 0; j <= B.hmask; ++j) B.hash[j] = -1;
   int k = 0, b = 0;
@@ -634,7 +634,7 @@ __device__ int grow(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1,
       if (!cons && ref >= 0) {
         const int4 Tn = P.T[ref >> 2];
         inside = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
-      } else if (cons && conv && dot_sign(pt(P, u), pt(P, v), p) < 0) {
+      } else if (cons && conv && encroaches(pt(P, u), pt(P, v), p, lens)) {
         ct = t;
         ce = e;
         return G_CONV;
@@ -812,14 +812,15 @@ __device__ int grow_cand(const Pool& P, int i, const CavBuf& B, GrowAcc& acc) {
 #ifdef GDP_DIAG
   const long long gc0 = clock64();
 #endif
-  int g = grow(P, B, pp, s.t0, s.t1, s.conv, nc, nb, ct, ce);
+  const bool lens = P.mi[s.m].lens != 0;
+  int g = grow(P, B, pp, s.t0, s.t1, s.conv, lens, nc, nb, ct, ce);
 #ifdef GDP_DIAG
   atomicMax(&g_diag[6], (unsigned long long)(clock64() - gc0));
 #endif
   if (g == G_CONV) {
     cand_conv(P, i, s, ct, ce);
     pp = P2{s.p, s.pf};
-    g = grow(P, B, pp, s.t0, s.t1, false, nc, nb, ct, ce);
+    g = grow(P, B, pp, s.t0, s.t1, false, lens, nc, nb, ct, ce);
   }
   if (g == G_OVF) return G_OVF;
   bool ok = true;
@@ -834,20 +835,42 @@ __device__ int grow_cand(const Pool& P, int i, const CavBuf& B, GrowAcc& acc) {
   return G_OK;
 }
 
-// ---------------------------------------------------------------- warp-cooperative growth
-// The cavity of one candidate grown by one warp, level by level: the lanes
-// test the (cavity triangle, edge) tuples of a level in parallel (the
-// tuple-list expansion of Sec. 5.3).  New triangles and boundary records
-// are appended in (parent, edge) order, and a tuple sees the triangles that
-// tuples before it added as cavity members, so the cavity list, the boundary
-// records, the first encroached subsegment and the overflow point are those
-// of the sequential breadth-first growth (grow) above.  Capacity CMAX = 32
-// triangles (the warp width), BMAX boundary edges; the list of the cavity so
-// far sits in shared memory (wc).
+// ---------------------------------------------------------------- cooperative growth
+// The cavity of one candidate grown by a group of W lanes (W = 32: a whole
+// warp; W = 8: a quarter warp), level by level: the lanes test the (cavity
+// triangle, edge) tuples of a level in parallel, W at a time (the tuple-list
+// expansion of Sec. 5.3).  New triangles and boundary records are appended
+// in (parent, edge) order, and a tuple sees the triangles that tuples before
+// it added as cavity members, so the cavity list, the boundary records, the
+// first encroached subsegment and the overflow point are those of the
+// sequential breadth-first growth (grow) above, whatever W is.  Capacity
+// CMAX = 32 triangles, BMAX boundary edges; the list of the cavity so far
+// sits in shared memory (wc).
+template <int W>
+struct Group {
+  int gl;          // lane within the group
+  int gb;          // first warp lane of the group
+  unsigned mask;   // the group's lanes in the warp
+  __device__ __forceinline__ Group() {
+    const int lane = threadIdx.x & 31;
+    gl = lane & (W - 1);
+    gb = lane - gl;
+    mask = W == 32 ? 0xffffffffu : (((1u << W) - 1u) << gb);
+  }
+  // group-local bits (bit j = lane gb + j)
+  __device__ __forceinline__ unsigned ballot(bool x) const { return __ballot_sync(mask, x) >> gb; }
+  __device__ __forceinline__ unsigned match(int v) const { return __match_any_sync(mask, v) >> gb; }
+  template <class X>
+  __device__ __forceinline__ X shfl(X v, int src) const { return __shfl_sync(mask, v, gb + src); }
+  __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+  __device__ __forceinline__ bool any(bool x) const { return ballot(x) != 0u; }
+};
+
+template <int W>
 __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, int t0, int t1,
-                     bool conv, int& nc, int& nb, int& ct, int& ce) {
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
+                     bool conv, bool lens, int& nc, int& nb, int& ct, int& ce) {
+  const Group<W> g;
+  const int lane = g.gl;
   const unsigned lt_mask = (1u << lane) - 1u;
   int k = 1, b = 0;
   if (lane == 0) {
@@ -861,11 +884,11 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
     }
     k = 2;
   }
-  __syncwarp();
+  g.sync();
   int lb = 0;
   while (lb < k) {
     const int le = k;
-    for (int base = 3 * lb; base < 3 * le; base += 32) {
+    for (int base = 3 * lb; base < 3 * le; base += W) {
       const int slot = base + lane;
       const bool act = slot < 3 * le;
       int e = 0, ref = -1, cons = 0, u = -1, v = -1, tn = -1, t = -1;
@@ -885,38 +908,38 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
       for (int j = 0; j < k; ++j) member |= (wc[j] == tn);
       // one incircle test per distinct neighbour (the lowest lane's)
       const bool test = act && !member && tn >= 0 && !cons;
-      const unsigned same = __match_any_sync(FULL, test ? tn : -2 - lane);
+      const unsigned same = g.match(test ? tn : -2 - lane);
       const int leader = __ffs(same) - 1;
       bool in = false;
       if (test && lane == leader) {
         const int4 Tn = P.T[tn];
         in = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
       }
-      in = __shfl_sync(FULL, in, leader);
-      const unsigned adders = __ballot_sync(FULL, test && lane == leader && in);
+      in = g.shfl(in, leader);
+      const unsigned adders = g.ballot(test && lane == leader && in);
       // a triangle added by an earlier tuple of this chunk is a cavity member
-      const unsigned same_all = __match_any_sync(FULL, (act && tn >= 0) ? tn : -2 - lane);
+      const unsigned same_all = g.match((act && tn >= 0) ? tn : -2 - lane);
       if (act && tn >= 0 && (same_all & adders & lt_mask)) member = true;
       // 1 add, 2 boundary record, 3 encroached subsegment (the circumcentre gives way)
       int ev = 0;
       if (act && !member) {
         if (test) ev = (lane == leader && in) ? 1 : (in ? 0 : 2);
-        else if (cons && conv && dot_sign(pt(P, u), pt(P, v), p) < 0) ev = 3;
+        else if (cons && conv && encroaches(pt(P, u), pt(P, v), p, lens)) ev = 3;
         else ev = 2;
       }
-      const unsigned am = __ballot_sync(FULL, ev == 1);
-      const unsigned rm = __ballot_sync(FULL, ev == 2);
-      const unsigned cm = __ballot_sync(FULL, ev == 3);
+      const unsigned am = g.ballot(ev == 1);
+      const unsigned rm = g.ballot(ev == 2);
+      const unsigned cm = g.ballot(ev == 3);
       const int ar = __popc(am & lt_mask), rr = __popc(rm & lt_mask);
-      const unsigned ovf = __ballot_sync(FULL, (ev == 1 && k + ar >= CMAX) || (ev == 2 && b + rr >= BMAX));
-      const int first_conv = cm ? __ffs(cm) - 1 : 32;
-      const int first_ovf = ovf ? __ffs(ovf) - 1 : 32;
+      const unsigned ovf = g.ballot((ev == 1 && k + ar >= CMAX) || (ev == 2 && b + rr >= BMAX));
+      const int first_conv = cm ? __ffs(cm) - 1 : W;
+      const int first_ovf = ovf ? __ffs(ovf) - 1 : W;
       if (first_conv < first_ovf) {
-        ct = __shfl_sync(FULL, t, first_conv);
-        ce = __shfl_sync(FULL, e, first_conv);
+        ct = g.shfl(t, first_conv);
+        ce = g.shfl(e, first_conv);
         return G_CONV;
       }
-      if (first_ovf < 32) return G_OVF;
+      if (first_ovf < W) return G_OVF;
       if (ev == 1) {
         wc[k + ar] = tn;
         cav[k + ar] = tn;
@@ -925,13 +948,56 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
       }
       k += __popc(am);
       b += __popc(rm);
-      __syncwarp();
+      g.sync();
     }
     lb = le;
   }
   nc = k;
   nb = b;
   return G_OK;
+}
+
+// One candidate grown by the group (all W lanes call it): splitting point,
+// walk and key by the group's first lane, then the cavity, the visibility
+// check of its boundary and the marks.  ws: the group's CandSetup slot.
+template <int MODE, int W>
+__device__ __forceinline__ void group_grow_cand(const Pool& P, int i, int* wc, CandSetup* ws, GrowAcc& acc) {
+  const Group<W> g;
+  int ok = 1;
+  if (g.gl == 0) {
+    P.c_big[i] = -1;
+    ok = cand_setup<MODE>(P, i, *ws, acc) ? 1 : 0;
+  }
+  g.sync();
+  if (!g.shfl(ok, 0)) return;
+  CandSetup s = *ws;
+  int* cav = P.c_cav + (size_t)i * CMAX;
+  int4* bnd = P.c_bnd + (size_t)i * BMAX;
+  int nc = 0, nb = 0, ct = -1, ce = -1;
+  const bool lens = P.mi[s.m].lens != 0;
+  int r = wgrow<W>(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, s.conv, lens, nc, nb, ct, ce);
+  if (r == G_CONV) {
+    if (g.gl == 0) cand_conv(P, i, *ws, ct, ce);
+    g.sync();
+    s = *ws;
+    r = wgrow<W>(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, false, lens, nc, nb, ct, ce);
+  }
+  if (r == G_OVF) {
+    if (g.gl == 0) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+    g.sync();
+    return;
+  }
+  g.sync();
+  const P2 pp{s.p, s.pf};
+  bool bad = false;
+  for (int q = g.gl; q < nb; q += W) {
+    const int4 rec = bnd[q];
+    if (!is_split_edge(rec, s.sub) && orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) bad = true;
+  }
+  if (g.any(bad)) return;
+  for (int j = g.gl; j < nc; j += W) atomicMax(&P.mark[cav[j]], s.key);
+  if (g.gl == 0) cand_record(P, i, s, nc, nb, acc);
+  g.sync();
 }
 
 // Cavity growth of the candidates in their own slots of CMAX triangles
@@ -947,53 +1013,41 @@ template <int MODE>
 __global__ void __maxnreg__(128) k_grow_w(Pool P, int timed) {
   __shared__ int wcs[4][32];
   __shared__ CandSetup ws[4];
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int wib = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n = P.ctrl->n_cand;
-  int* wc = wcs[wib];
   if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->grow_next = 0;   // k_grow_t's counter
-  if (n > P.warp_max) return;   // k_grow_t's case
+  if (n > P.warp_max) return;   // the per-group or per-thread kernel's case
   GrowAcc acc;
-  for (int i = gw; i < n; i += nw) {
-    int ok = 1;
-    if (lane == 0) {
-      P.c_big[i] = -1;
-      ok = cand_setup<MODE>(P, i, ws[wib], acc) ? 1 : 0;
-    }
-    __syncwarp();
-    if (!__shfl_sync(FULL, ok, 0)) continue;
-    CandSetup s = ws[wib];
-    int* cav = P.c_cav + (size_t)i * CMAX;
-    int4* bnd = P.c_bnd + (size_t)i * BMAX;
-    int nc = 0, nb = 0, ct = -1, ce = -1;
-    int g = wgrow(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, s.conv, nc, nb, ct, ce);
-    if (g == G_CONV) {
-      if (lane == 0) cand_conv(P, i, ws[wib], ct, ce);
-      __syncwarp();
-      s = ws[wib];
-      g = wgrow(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, false, nc, nb, ct, ce);
-    }
-    if (g == G_OVF) {
-      if (lane == 0) atomicMin(&P.lane[i & (LANES_A - 1)], i);
-      __syncwarp();
-      continue;
-    }
-    __syncwarp();
-    const P2 pp{s.p, s.pf};
-    bool bad = false;
-    for (int r = lane; r < nb; r += 32) {
-      const int4 rec = bnd[r];
-      if (!is_split_edge(rec, s.sub) && orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) bad = true;
-    }
-    if (__any_sync(FULL, bad)) continue;
-    for (int j = lane; j < nc; j += 32) atomicMax(&P.mark[cav[j]], s.key);
-    if (lane == 0) cand_record(P, i, s, nc, nb, acc);
-    __syncwarp();
-  }
+  for (int i = gw; i < n; i += nw) group_grow_cand<MODE, 32>(P, i, wcs[wib], &ws[wib], acc);
   if (MODE == 0) acc_flush(P, acc, timed);
 }
 
+// The same above P.warp_max candidates, where the launch is throughput-bound:
+// a group of GROW_GROUP lanes per candidate (four candidates per warp), so that
+// a level's few tuples keep most lanes busy and the lanes of a warp run the
+// same instruction stream.  The grid covers the candidates in place.
+constexpr int GROW_GROUP = 8;
+#ifndef GDP_GROW_G_REGS
+#define GDP_GROW_G_REGS 64
+#endif
+template <int MODE>
+__global__ void __maxnreg__(GDP_GROW_G_REGS) k_grow_g(Pool P, int timed) {
+  constexpr int GPB = 128 / GROW_GROUP;   // groups per 128-thread block
+  __shared__ int wcs[GPB][32];
+  __shared__ CandSetup ws[GPB];
+  const int gib = threadIdx.x / GROW_GROUP;
+  const int gg = (blockIdx.x * blockDim.x + threadIdx.x) / GROW_GROUP;
+  const int ng = (gridDim.x * blockDim.x) / GROW_GROUP;
+  const int n = P.ctrl->n_cand;
+  if (n <= P.warp_max) return;   // k_grow_w's case
+  GrowAcc acc;
+  for (int i0 = gg - (gg & (32 / GROW_GROUP - 1)); i0 < n; i0 += ng) {   // whole warps
+    const int i = i0 + (gg & (32 / GROW_GROUP - 1));
+    if (i < n) group_grow_cand<MODE, GROW_GROUP>(P, i, wcs[gib], &ws[gib], acc);
+  }
+  if (MODE == 0) acc_flush(P, acc, timed);
+}
 
 // the same, one thread per candidate, when there are more than
 // P.warp_max candidates (a separate kernel keeps each version's register
@@ -1048,8 +1102,8 @@ __device__ __forceinline__ void hash_put(const CavBuf& B, int t) {
   }
 }
 
-__device__ int wgrow_h(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1, bool conv, int& nc,
-                       int& nb, int& ct, int& ce) {
+__device__ int wgrow_h(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1, bool conv, bool lens,
+                       int& nc, int& nb, int& ct, int& ce) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -1101,7 +1155,7 @@ __device__ int wgrow_h(const Pool& P, const CavBuf& B, const P2& p, int t0, int 
       int ev = 0;
       if (act && !member) {
         if (test) ev = (lane == leader && in) ? 1 : (in ? 0 : 2);
-        else if (cons && conv && dot_sign(pt(P, u), pt(P, v), p) < 0) ev = 3;
+        else if (cons && conv && encroaches(pt(P, u), pt(P, v), p, lens)) ev = 3;
         else ev = 2;
       }
       const unsigned am = __ballot_sync(FULL, ev == 1);
@@ -1165,12 +1219,13 @@ __global__ void __maxnreg__(128) k_grow_big(Pool P, int TIER) {
     if (!__shfl_sync(FULL, ok, 0)) continue;
     CandSetup s = ws[wib];
     int nc = 0, nb = 0, ct = -1, ce = -1;
-    int g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, s.conv, nc, nb, ct, ce);
+    const bool lens = P.mi[s.m].lens != 0;
+    int g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, s.conv, lens, nc, nb, ct, ce);
     if (g == G_CONV) {
       if (lane == 0) cand_conv(P, i, ws[wib], ct, ce);
       __syncwarp();
       s = ws[wib];
-      g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, false, nc, nb, ct, ce);
+      g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, false, lens, nc, nb, ct, ce);
     }
     if (g == G_OVF) {
       if (lane == 0) {
@@ -1336,6 +1391,20 @@ __device__ __forceinline__ void new_tri_code(const Pool& P, int s) {
   else P.dirty[s] = 1;
 }
 
+// A mesh whose insertions of this iteration do not fit its slots: in
+// refinement the iteration inserts nothing for it (its elements stay flagged)
+// and the host grows the pool after the graph replay; elsewhere it is out of
+// memory.
+template <int MODE>
+__device__ __forceinline__ void no_room(const Pool& P, int m) {
+  if (MODE == 0) {
+    P.mi[m].need_grow = 2;
+    atomicOr(&P.ctrl->grow, 1);
+  } else {
+    P.mi[m].status = S_NOMEM;
+  }
+}
+
 // ---------------------------------------------------------------- spill-tier cavities, one warp each
 // Cavities of the spill tiers have hundreds to tens of thousands of triangles.
 // The thread-per-candidate kernels hand them to their whole warp (ballot, then
@@ -1480,7 +1549,7 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
       const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
       if (i == f) {
         P.mi[m].ins_ok = ok ? 1 : 0;
-        if (!ok) P.mi[m].status = S_NOMEM;
+        if (!ok) no_room<MODE>(P, m);
       }
       if (P.c_final[i] && ok) {
         base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
@@ -1563,7 +1632,7 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
     const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
     if (lane == 0 && i == f) {
       P.mi[m].ins_ok = ok ? 1 : 0;
-      if (!ok) P.mi[m].status = S_NOMEM;
+      if (!ok) no_room<MODE>(P, m);
     }
     if (!P.c_final[i] || !ok) continue;
     const int base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
@@ -1675,9 +1744,17 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
       if (i == M.last_cand && ok) {
         int totE, totV;
         mesh_totals(P, M.first_cand, i, totE, totV);
-        P.mi[m].tri_count = M.tri_count + totE;
-        P.mi[m].vert_count = M.vert_count + totV;
-        if (MODE == 0) P.mi[m].steiner = M.steiner + totV;
+        const int tc = M.tri_count + totE, vc = M.vert_count + totV;
+        P.mi[m].tri_count = tc;
+        P.mi[m].vert_count = vc;
+        if (MODE == 0) {
+          P.mi[m].steiner = M.steiner + totV;
+          // under a quarter of the slots left: ask for more before they run out
+          if (4ll * (M.tri_cap - tc) < M.tri_cap || 4ll * (M.vert_cap - vc) < M.vert_cap) {
+            if (!M.need_grow) P.mi[m].need_grow = 1;
+            atomicOr(&P.ctrl->grow, 1);
+          }
+        }
       }
     }
     unsigned bm = __ballot_sync(FULL, big);
@@ -1838,7 +1915,7 @@ __global__ void __launch_bounds__(BS) k_check(Pool P, unsigned long long* cnt) {
 // Every live bad triangle (kind 0, or 2 when the small-angle exemption
 // accepts it); every subsegment edge: encroachment by this triangle's apex
 // (kind 1) with its split point.  Output order is not defined.
-__global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int* kind, int* verts,
+__global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int lens, int* kind, int* verts,
                                                     double2* spt, unsigned* meas, int cap,
                                                     int* count) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
@@ -1860,7 +1937,7 @@ __global__ void __launch_bounds__(BS) k_scan_report(Pool P, double B2, int* kind
     for (int e = 0; e < 3; ++e) {
       if (!((T4.w >> e) & 1)) continue;
       const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
-      if (dot_sign(pt(P, u), pt(P, v), pt(P, comp(T4, e))) < 0) {
+      if (encroaches(pt(P, u), pt(P, v), pt(P, comp(T4, e)), lens != 0)) {
         const int r = atomicAdd(count, 1);
         if (r < cap) {
           kind[r] = 1;

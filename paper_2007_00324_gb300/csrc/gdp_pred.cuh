@@ -482,6 +482,91 @@ __device__ __forceinline__ int dot_sign(double2 a, double2 b, double2 p) {
   return dot_exact(a.x, a.y, b.x, b.y, p.x, p.y);
 }
 
+// ---------------------------------------------------------------- diametral lens
+// p strictly inside the diametral lens of ab (Chew's rule, Sec. 4.2): the
+// segment subtends more than 120 degrees at p.  With u = a - p, w = b - p,
+// D = u.w and C = u x w, Lagrange's identity |u|^2 |w|^2 = D^2 + C^2 turns
+// cos(angle) < -1/2 into D < 0 and Q = 3 D^2 - C^2 > 0, where
+//   Q = 3 ux^2 wx^2 + 3 uy^2 wy^2 - ux^2 wy^2 - uy^2 wx^2 + 8 ux uy wx wy.
+// Exact sign of Q: every difference as an exact pair (h + l); with no tails,
+// the 16 degree-4 monomials (coefficients as repeated terms) go to the integer
+// accumulator, otherwise the products of all h / l choices are summed as a
+// floating-point expansion.
+static __device__ __noinline__ int lens_q_exact(double ax, double ay, double bx, double by, double px,
+                                                double py) {
+  GDP_DIAG_ADD(3);
+  double h[4], l[4];   // ux uy wx wy
+  two_diff(ax, px, h[0], l[0]);
+  two_diff(ay, py, h[1], l[1]);
+  two_diff(bx, px, h[2], l[2]);
+  two_diff(by, py, h[3], l[3]);
+  // (coefficient, four factor indices)
+  const int T[5][5] = {{3, 0, 0, 2, 2}, {3, 1, 1, 3, 3}, {-1, 0, 0, 3, 3}, {-1, 1, 1, 2, 2},
+                       {8, 0, 1, 2, 3}};
+  if (l[0] == 0.0 && l[1] == 0.0 && l[2] == 0.0 && l[3] == 0.0) {
+    double f[64], sg[16];
+    int n = 0;
+    for (int t = 0; t < 5; ++t) {
+      const int c = T[t][0] < 0 ? -T[t][0] : T[t][0];
+      for (int r = 0; r < c; ++r) {
+        for (int j = 0; j < 4; ++j) f[4 * n + j] = h[T[t][1 + j]];
+        sg[n++] = T[t][0] < 0 ? -1.0 : 1.0;
+      }
+    }
+    const int r = int_sign(f, sg, n, 4);
+    if (r != 2) return r;
+  }
+  Expansion<64> X;
+  for (int t = 0; t < 5; ++t) {
+    for (int m = 0; m < 16; ++m) {   // bit j of m: the tail of factor j
+      double f[4];
+      bool zero = false;
+      for (int j = 0; j < 4; ++j) {
+        const int v = T[t][1 + j];
+        f[j] = ((m >> j) & 1) ? l[v] : h[v];
+        zero |= f[j] == 0.0;
+      }
+      if (zero) continue;
+      double x, y, z, w;
+      two_prod(f[0], f[1], x, y);
+      two_prod(f[2], f[3], z, w);
+      const int c = T[t][0];
+      if (c == 3) {   // 3 = 2 + 1, each a power of two
+        add_prod2(X, x, y, z, w, 2.0);
+        add_prod2(X, x, y, z, w, 1.0);
+      } else {
+        add_prod2(X, x, y, z, w, (double)c);
+      }
+      if (X.n > 40) X.compress();
+    }
+  }
+  return X.sign();
+}
+
+// FP64 filter for the sign of Q when D < 0 is known: D and C with forward
+// error bounds (difference, product and sum roundings: 4.5 u of the sum of
+// the absolute products), then Q over the intervals with the rounding of
+// that last evaluation folded into the factors 1 -+ 8u.  0 when unsure.
+__device__ __forceinline__ int lens_q_f64(double2 a, double2 b, double2 p) {
+  const double ux = __dsub_rn(a.x, p.x), uy = __dsub_rn(a.y, p.y);
+  const double wx = __dsub_rn(b.x, p.x), wy = __dsub_rn(b.y, p.y);
+  const double t1 = __dmul_rn(ux, wx), t2 = __dmul_rn(uy, wy);
+  const double t3 = __dmul_rn(ux, wy), t4 = __dmul_rn(uy, wx);
+  const double aD = fabs(__dadd_rn(t1, t2)), aC = fabs(__dsub_rn(t3, t4));
+  const double eD = __dmul_rn(4.5 * kU, __dadd_rn(fabs(t1), fabs(t2)));
+  const double eC = __dmul_rn(4.5 * kU, __dadd_rn(fabs(t3), fabs(t4)));
+  constexpr double kSmall = 1e-150;   // squares of larger values do not underflow
+  if (!(aD > eD) || !(aD - eD > kSmall) || !(aD + eD < 1e150) || !(aC + eC < 1e150)) return 0;
+  const double dlo = __dsub_rn(aD, eD), dhi = __dadd_rn(aD, eD);
+  const double clo = (aC - eC > kSmall) ? __dsub_rn(aC, eC) : 0.0;
+  const double chi = fmax(__dadd_rn(aC, eC), kSmall);
+  const double lo = __dsub_rn(__dmul_rn(__dmul_rn(3.0 * (1.0 - 8.0 * kU), dlo), dlo),
+                              __dmul_rn(__dmul_rn(1.0 + 8.0 * kU, chi), chi));
+  const double hi = __dsub_rn(__dmul_rn(__dmul_rn(3.0 * (1.0 + 8.0 * kU), dhi), dhi),
+                              __dmul_rn(__dmul_rn(1.0 - 8.0 * kU, clo), clo));
+  return lo > 0.0 ? 1 : (hi < 0.0 ? -1 : 0);
+}
+
 // ---------------------------------------------------------------- FP32 filter stage
 // GB300 executes FP64 at 1/64 of the FP32 rate, so every predicate first runs
 // in FP32 on float copies of the coordinates, translated to the mesh's
@@ -559,6 +644,34 @@ __device__ __forceinline__ int dot_f32(float2 a, float2 b, float2 p) {
   return s > err ? 1 : (-s > err ? -1 : 0);
 }
 
+// FP32 filter for the sign of Q = 3 D^2 - C^2 when D < 0 is known (see
+// lens_q_exact): D and C from the float copies with the bound of dot_f32
+// (input error E per difference plus rounding), then Q over the intervals
+// with the float rounding folded into the factors 1 -+ 8v.  0 when unsure.
+__device__ __forceinline__ int lens_q_f32(float2 a, float2 b, float2 p) {
+  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(p.x), fabsf(p.y));
+  if (!(M < 1e8f) || M < 1e-15f) return 0;
+  const float ux = __fsub_rn(a.x, p.x), uy = __fsub_rn(a.y, p.y);
+  const float wx = __fsub_rn(b.x, p.x), wy = __fsub_rn(b.y, p.y);
+  const float t1 = __fmul_rn(ux, wx), t2 = __fmul_rn(uy, wy);
+  const float t3 = __fmul_rn(ux, wy), t4 = __fmul_rn(uy, wx);
+  const float aD = fabsf(__fadd_rn(t1, t2)), aC = fabsf(__fsub_rn(t3, t4));
+  const float E = 4.001f * kV * M;
+  const float es = E * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy) + 2.0f * E);
+  const float eD = (es + 2.0001f * kV * (fabsf(t1) + fabsf(t2))) * 1.001f + 1e-37f;
+  const float eC = (es + 2.0001f * kV * (fabsf(t3) + fabsf(t4))) * 1.001f + 1e-37f;
+  constexpr float kSmall = 1e-17f;   // squares of larger values stay normal
+  if (!(aD - eD > kSmall) || !(aD + eD < 1e17f) || !(aC + eC < 1e17f)) return 0;
+  const float dlo = aD - eD, dhi = aD + eD;
+  const float clo = (aC - eC > kSmall) ? aC - eC : 0.0f;
+  const float chi = fmaxf(aC + eC, kSmall);
+  const float lo = __fsub_rn(__fmul_rn(__fmul_rn(3.0f * (1.0f - 8.0f * kV), dlo), dlo),
+                             __fmul_rn(__fmul_rn(1.0f + 8.0f * kV, chi), chi));
+  const float hi = __fsub_rn(__fmul_rn(__fmul_rn(3.0f * (1.0f + 8.0f * kV), dhi), dhi),
+                             __fmul_rn(__fmul_rn(1.0f - 8.0f * kV, clo), clo));
+  return lo > 0.0f ? 1 : (hi < 0.0f ? -1 : 0);
+}
+
 __device__ __forceinline__ int orient(const P2& a, const P2& b, const P2& c) {
   const int s = orient_f32(a.f, b.f, c.f);
   return s ? s : orient(a.d, b.d, c.d);
@@ -567,6 +680,24 @@ __device__ __forceinline__ int orient(const P2& a, const P2& b, const P2& c) {
 __device__ __forceinline__ int dot_sign(const P2& a, const P2& b, const P2& p) {
   const int s = dot_f32(a.f, b.f, p.f);
   return s ? s : dot_sign(a.d, b.d, p.d);
+}
+
+// -1: p strictly inside the diametral lens of ab (Chew's rule, Sec. 4.2),
+// 0: p is a or b, or exactly on the lens boundary, +1: outside
+__device__ __forceinline__ int lens_sign(const P2& a, const P2& b, const P2& p) {
+  const int d = dot_sign(a, b, p);
+  if (d > 0) return 1;
+  if (d == 0) return ((p.d.x == a.d.x && p.d.y == a.d.y) || (p.d.x == b.d.x && p.d.y == b.d.y)) ? 0 : 1;
+  int q = lens_q_f32(a.f, b.f, p.f);
+  if (!q) q = lens_q_f64(a.d, b.d, p.d);
+  if (!q) q = lens_q_exact(a.d.x, a.d.y, b.d.x, b.d.y, p.d.x, p.d.y);
+  return q > 0 ? -1 : (q < 0 ? 1 : 0);
+}
+
+// p encroaches subsegment ab: strictly inside its diametral circle (Ruppert's
+// rule) or, with lens, strictly inside its diametral lens (Chew's rule)
+__device__ __forceinline__ bool encroaches(const P2& a, const P2& b, const P2& p, bool lens) {
+  return lens ? lens_sign(a, b, p) < 0 : dot_sign(a, b, p) < 0;
 }
 
 __device__ __forceinline__ int incircle(const P2& a, const P2& b, const P2& c, const P2& d) {

@@ -369,6 +369,7 @@ static int server_admit(gdp_server* s) {
       M.L2 = (s->opts.max_len > 0 && std::isfinite(s->opts.max_len)) ? s->opts.max_len * s->opts.max_len : 0.0;
       M.steiner = 0;
       M.cand_cap = s->opts.cand_cap;
+      M.lens = (s->opts.flags & GDP_REFINE_CHEW) ? 1 : 0;
       M.first_cand = M.last_cand = -1;
       M.pending = 0;
       h.hmi[md] = M;
@@ -400,14 +401,16 @@ static int server_retire(gdp_server* s) {
   std::vector<int> fin;
   for (auto& kv : s->live) {
     const MeshInfo& M = h.hmi[kv.first];
-    if (M.status != S_OK || (M.first_cand < 0 && M.pending == 0)) fin.push_back(kv.first);
+    // a request whose region ran out of slots (need_grow 2) ends with GDP_ERR_NOMEM:
+    // resident regions are fixed, so the server does not grow them
+    if (M.status != S_OK || M.need_grow == 2 || (M.first_cand < 0 && M.pending == 0)) fin.push_back(kv.first);
   }
   for (int md : fin) {
     gdp_server::Live L = s->live[md];
     gdp_server::Done d{};
     const MeshInfo M = h.hmi[md];
     d.info.ticket = L.ticket;
-    d.info.status = M.status;
+    d.info.status = (M.status == S_OK && M.need_grow == 2) ? S_NOMEM : M.status;
     d.info.n_in_pts = L.n_in;
     d.info.n_steiner = M.steiner;
     int64_t np = 0, nt = 0, ns = 0;

@@ -41,19 +41,20 @@ class Stats(C.Structure):
                 ("cavity_tris", C.c_int64), ("cavity_edges", C.c_int64), ("walk_steps", C.c_int64),
                 ("grow_ms", C.c_double), ("grow_launches", C.c_int64), ("timed_grown", C.c_int64),
                 ("timed_cavity_tris", C.c_int64), ("timed_cavity_edges", C.c_int64),
-                ("timed_walk_steps", C.c_int64)]
+                ("timed_walk_steps", C.c_int64), ("grow_steps", C.c_int64), ("flips", C.c_int64),
+                ("flops", C.c_int64), ("redundant_removed", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 SYMBOLS = ["gdp_mesh_create", "gdp_mesh_create_device", "gdp_mesh_refine", "gdp_mesh_export",
-           "gdp_mesh_insert_points", "gdp_mesh_split_subsegments", "gdp_mesh_scan",
+           "gdp_mesh_insert_points", "gdp_mesh_split_subsegments", "gdp_mesh_scan", "gdp_mesh_scan_mode",
            "gdp_mesh_stats", "gdp_mesh_check", "gdp_mesh_profile", "gdp_mesh_kernel_time", "gdp_mesh_destroy",
            "gdp_batch_create", "gdp_batch_refine",
            "gdp_batch_info", "gdp_batch_export", "gdp_batch_destroy", "gdp_scan_noalloc",
            "gdp_autotune", "gdp_server_create", "gdp_server_submit", "gdp_server_step", "gdp_server_result",
-           "gdp_server_destroy", "gdp_status_str"]
+           "gdp_server_destroy", "gdp_measure_fp64_peak", "gdp_status_str"]
 
 
 def load(build_if_missing: bool = True):
@@ -76,6 +77,7 @@ def load(build_if_missing: bool = True):
             L.gdp_mesh_insert_points.argtypes = [vp, vp, i64]
             L.gdp_mesh_split_subsegments.argtypes = [vp, vp, i64]
             L.gdp_mesh_scan.argtypes = [vp, d, vp, vp, vp, vp, i64, C.POINTER(i64)]
+            L.gdp_mesh_scan_mode.argtypes = [vp, d, i32, vp, vp, vp, vp, i64, C.POINTER(i64)]
             L.gdp_mesh_stats.argtypes = [vp, C.POINTER(Stats)]
             L.gdp_mesh_check.argtypes = [vp, vp]
             L.gdp_mesh_profile.argtypes = [vp, C.c_int]
@@ -99,6 +101,7 @@ def load(build_if_missing: bool = True):
             L.gdp_server_result.argtypes = [vp, C.POINTER(ResultInfo), vp, i64, vp, i64, vp, i64]
             L.gdp_server_destroy.argtypes = [vp]
             L.gdp_server_destroy.restype = None
+            L.gdp_measure_fp64_peak.argtypes = [vp, C.POINTER(d)]
             L.gdp_status_str.argtypes = [C.c_int]
             L.gdp_status_str.restype = C.c_char_p
             for n in SYMBOLS:
@@ -106,6 +109,15 @@ def load(build_if_missing: bool = True):
                     getattr(L, n).restype = C.c_int
             _lib = L
     return _lib
+
+
+def measure_fp64_peak(stream=None) -> float:
+    """gdp_measure_fp64_peak: the device's FP64 FMA throughput in TFLOP/s"""
+    t = C.c_double()
+    st = load().gdp_measure_fp64_peak(_stream_handle(stream), C.byref(t))
+    if st != OK:
+        raise GdpError(st, "gdp_measure_fp64_peak")
+    return t.value
 
 
 def status_str(s: int) -> str:
@@ -119,7 +131,9 @@ def _p(a):
     return C.c_void_p(a.ctypes.data) if a is not None else None
 
 
-REFINE_TIME_GROW = 1   # gdp_refine_opts.flags: time every k_grow launch with CUDA events
+REFINE_TIME_GROW = 1   # gdp_refine_opts.flags: time the first k_grow launch pair of each replay
+REFINE_CHEW = 2        # gdp_refine_opts.flags: encroachment by the diametral lens (Chew's rule)
+REFINE_FLIPFLOP = 4    # gdp_refine_opts.flags: Flip-Flop insertion instead of cavity insertion
 
 
 def _opts(B=math.sqrt(2.0), max_iter=0, cand_cap=0, graph_iters=0, flags=0, cand_block=0, max_len=0.0):
@@ -237,10 +251,10 @@ class Mesh:
         if st != OK:
             raise GdpError(st, "gdp_mesh_split_subsegments")
 
-    def scan(self, B=math.sqrt(2.0), cap=None):
+    def scan(self, B=math.sqrt(2.0), cap=None, flags=0):
         L = load()
         cnt = C.c_int64()
-        st = L.gdp_mesh_scan(self._h, B, None, None, None, None, 0, C.byref(cnt))
+        st = L.gdp_mesh_scan_mode(self._h, B, flags, None, None, None, None, 0, C.byref(cnt))
         if st != OK:
             raise GdpError(st, "gdp_mesh_scan")
         n = cnt.value if cap is None else min(cap, cnt.value)
@@ -248,7 +262,7 @@ class Mesh:
         verts = np.zeros((n, 3), np.int32)
         pt = np.zeros((n, 2), np.float64)
         meas = np.zeros(n, np.uint32)
-        st = L.gdp_mesh_scan(self._h, B, _p(kind), _p(verts), _p(pt), _p(meas), n, C.byref(cnt))
+        st = L.gdp_mesh_scan_mode(self._h, B, flags, _p(kind), _p(verts), _p(pt), _p(meas), n, C.byref(cnt))
         if st != OK:
             raise GdpError(st, "gdp_mesh_scan")
         return kind, verts, pt, meas
