@@ -640,6 +640,31 @@ def main():
     kt = m.kernel_times()
     del os.environ["GDP_PROFILE"]
     del m
+    # the same step with Flip-Flop insertion (Sec. 4.3), for the A/B against cavity insertion
+    ff_ms, ff, ff_err = [], None, None
+    for _ in range(2):
+        flush.fill_(1.0)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        try:
+            m, ff = step(gdp.REFINE_FLIPFLOP)
+        except gdp.GdpError as e:   # reported in the line, never fatal to it
+            ff_err = str(e)
+            break
+        f1.record(stream)
+        f1.synchronize()
+        ff_ms.append(f0.elapsed_time(f1))
+        del m
+    if ff_err:
+        flipflop = {"error": ff_err}
+    else:
+        flipflop = {"value": ff["n_steiner"] / (min(ff_ms) / 1000.0), "unit": "Steiner pts/s",
+                    "ms_per_step": min(ff_ms), "refine_ms": ff["refine_ms"], "steiner_per_step": ff["n_steiner"],
+                    "iterations": ff["iterations"], "inserted": ff["inserted"], "flips": ff["flips"],
+                    "flops": ff["flops"], "redundant_removed": ff["redundant_removed"],
+                    "note": "the same step with GDP_REFINE_FLIPFLOP (host-driven passes, no CUDA graph); "
+                            "best of 2 steps"}
     tot_k = sum(v[0] for v in kt.values())
     top = max(kt.items(), key=lambda kv: kv[1][0])
     peak, peak_kind = peaks()
@@ -691,6 +716,7 @@ def main():
             "cdt_rounds": stats["cdt_rounds"],
             "refine_only_steiner_per_s": stats["n_steiner"] / (stats["refine_ms"] / 1000.0),
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk.summary(),
+            "flipflop": flipflop,
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.B, 1 if args.workload == "paper_shaped" else 3,

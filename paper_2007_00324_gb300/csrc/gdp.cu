@@ -242,8 +242,8 @@ static void print_diag(const char* where) {
                "[%s] orient_exact %llu incircle_exact %llu (inexact diffs %llu, max %llu cyc) sos %llu "
                "dot_exact %llu | max walk steps %llu, max walk cyc %llu, max grow cyc %llu\n",
                where, d[0], d[1], d[4], d[8], d[2], d[3], d[5], d[7], d[6]);
-  std::fprintf(stderr, "[%s] grow cycles histogram <4k %llu <8k %llu <16k %llu <32k %llu <64k %llu <128k %llu more %llu\n",
-               where, d[9], d[10], d[11], d[12], d[13], d[14], d[15]);
+  std::fprintf(stderr, "[%s] calls orient %llu incircle %llu dot %llu; past the FP32 filter: orient %llu incircle %llu dot %llu\n",
+               where, d[9], d[10], d[11], d[12], d[13], d[14]);
   unsigned long long z[16] = {};
   cudaMemcpyToSymbol(g_diag, z, sizeof(z));
 }
@@ -1186,7 +1186,7 @@ int PoolHost::ff_iteration() {
   LAUNCH_B(*this, k_grow_big<0>, LANES_A / 4, 128, P, 0);
   LAUNCH_B(*this, k_grow_big<0>, LANES_B / 4, 128, P, 1);
   LAUNCH_C(*this, k_survive, P);
-  LAUNCH(*this, k_ff_prep, G, P);
+  LAUNCH(*this, k_ff_prep, G, P, trace ? 1 : 0);
   LAUNCH(*this, k_offsets, G, P);
   int32_t *cur = ffA, *nxt = ffB;
   Pool Q = P;

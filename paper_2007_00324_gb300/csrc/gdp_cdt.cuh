@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(BS) k_cdt_vf(Pool P) {
 __device__ __forceinline__ uint32_t pick_measure(const Pool& P, const MeshInfo& M, int v,
                                                  const int4& T4) {
   if (is_aux(M, v)) return 0xfffffu;
-  const float2 a = P.Vf[T4.x], b = P.Vf[T4.y], c = P.Vf[T4.z], q = P.Vf[v];
+  const float4 a = P.Vf[T4.x], b = P.Vf[T4.y], c = P.Vf[T4.z], q = P.Vf[v];
   const float dx = b.x - a.x, dy = b.y - a.y, ex = c.x - a.x, ey = c.y - a.y;
   const float d2 = dx * dx + dy * dy, e2 = ex * ex + ey * ey;
   const float D = 2.0f * (dx * ey - dy * ex);

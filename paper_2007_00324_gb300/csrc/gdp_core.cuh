@@ -105,7 +105,7 @@ struct Ctrl {
 struct Pool {
   // mesh
   double2* V;
-  float2* Vf;            // float copies of V - org (FP32 filter stage)
+  float4* Vf;            // float copies of V - org (FP32 filter stage)
   int32_t* vseg;
   int32_t* vtri;
   uint8_t* apex;
@@ -133,7 +133,7 @@ struct Pool {
   int32_t* c_vseg;
   int2* c_sub;
   double2* c_pt;
-  float2* c_ptf;
+  float4* c_ptf;
   unsigned long long* c_key;
   int32_t* c_ncav;
   int32_t* c_nbnd;

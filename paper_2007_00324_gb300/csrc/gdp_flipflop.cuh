@@ -37,7 +37,8 @@
 namespace gdp {
 
 // operation kinds (Pool::fop), FF_EXEC once done
-constexpr int FF_NONE = -1, FF_FLIP = 0, FF_FLOP = 1, FF_UNSPLIT = 2, FF_EXEC = 16;
+constexpr int FF_NONE = -1, FF_FLIP = 0, FF_FLOP = 1, FF_UNSPLIT = 2, FF_RETRI = 3, FF_EXEC = 16;
+constexpr int FF_RETRI_MAX = 6;   // stars up to this size are removed by re-triangulation
 constexpr int FF_DEG_MAX = 64;    // star walks are bounded (a larger star waits)
 
 __device__ __forceinline__ unsigned long long ff_key(const Pool& P, int step, int cls, int t, int x) {
@@ -75,7 +76,7 @@ __device__ __forceinline__ int ff_first_redundant(const Pool& P, const int4& T4)
 // per surviving candidate: how it goes in (c_loc = t << 2 | e: split edge e
 // of t; e = 3: split t in three) and its new slots (c_extra), with block sums
 // for k_offsets; every mesh records where this iteration's vertices start
-__global__ void __launch_bounds__(BS) k_ff_prep(Pool P) {
+__global__ void __launch_bounds__(BS) k_ff_prep(Pool P, int trace) {
   __shared__ int sm[33];
   const int n = P.ctrl->n_cand;
   {
@@ -112,6 +113,15 @@ __global__ void __launch_bounds__(BS) k_ff_prep(Pool P) {
       if (e < 0) {   // cannot happen for a located, filtered point
         set_err(P.ctrl, S_INTERNAL);
         atomicCAS(&P.ctrl->dbg, 0, 1);
+        if (trace) {
+          const double2 p = P.c_pt[i];
+          printf("ff prep: candidate %d elem %d t0=%d (%d %d %d w=%x) N=(%d %d %d) sub=(%d %d) p=(%.17g %.17g) "
+                 "o=(%d %d %d) big=%d\n", i, P.c_elem[i], t0, T4.x, T4.y, T4.z, T4.w, N4.x, N4.y, N4.z, sub.x,
+                 sub.y, p.x, p.y,
+                 orient(pt(P, T4.y), pt(P, T4.z), P2{p, P.c_ptf[i]}),
+                 orient(pt(P, T4.z), pt(P, T4.x), P2{p, P.c_ptf[i]}),
+                 orient(pt(P, T4.x), pt(P, T4.y), P2{p, P.c_ptf[i]}), P.c_big[i]);
+        }
         fin = false;
       } else {
         code = (t0 << 2) | e;
@@ -293,42 +303,59 @@ __device__ __forceinline__ Corner step_around(const Pool& P, Corner c, int v, bo
 // degree three is flopped (proposed by the lowest slot of its star); a
 // midpoint whose sides are down to two triangles each is unsplit (the lowest
 // slot of the four, or two on the hull); otherwise t proposes to flip its
-// edge after v when the quadrilateral is strictly convex.  A point waits while
-// an adjacent redundant point has a lower key.  Returns the kind proposed
-// (fprop[k] = the slot that carries it out).
+// edge after v when the quadrilateral is strictly convex (a star of any size).
+// Order among adjacent redundant points: an operation of v never rewrites a
+// triangle that holds a redundant point of lower key -- a flop or unsplit
+// waits while any vertex of its (small) star is one, a flip while a vertex of
+// its two triangles is one -- so the point of lowest key in any group always
+// proceeds and the passes end.  Returns the kind proposed (fprop[k] = the
+// slot that carries it out).
+__device__ __forceinline__ bool ff_blocks(const Pool& P, int x, unsigned long long kv) {
+  return ff_redundant(P, x) && P.vkey[x] < kv;
+}
+
 __device__ int ff_propose_removal(const Pool& P, int k, int t, int j, int v, int step) {
   const unsigned long long kv = P.vkey[v];
-  // the star (one side of it for a midpoint): walk after-v edges, then before-v
+  // the star (one side of it for a midpoint), as far as FF_DEG_MAX triangles:
+  // after-v edges clockwise, then before-v edges
   int side[FF_DEG_MAX], ns = 0;
   bool closed = false, wait = false;
   side[ns++] = t;
   Corner c{t, j};
   for (int s = 0; s < FF_DEG_MAX - 1; ++s) {
     const int4 T4 = P.T[c.t];
-    const int x = comp(T4, mod3(c.j + 1));
-    if (ff_redundant(P, x) && P.vkey[x] < kv) wait = true;
+    if (ff_blocks(P, comp(T4, mod3(c.j + 1)), kv)) wait = true;
     c = step_around(P, c, v, true, true);
     if (c.t < 0) break;
     if (c.t == t) { closed = true; break; }
     side[ns++] = c.t;
   }
   Corner first{t, j};
-  if (!closed) {
+  bool whole = closed;   // the walk saw the whole star (or the whole side)
+  if (!closed && ns < FF_DEG_MAX) {
     Corner b{t, j};
     for (int s = 0; s < FF_DEG_MAX && ns < FF_DEG_MAX; ++s) {
       const int4 T4 = P.T[b.t];
-      const int y = comp(T4, mod3(b.j + 2));
-      if (ff_redundant(P, y) && P.vkey[y] < kv) wait = true;
+      if (ff_blocks(P, comp(T4, mod3(b.j + 2)), kv)) wait = true;
       const Corner nb = step_around(P, b, v, false, true);
-      if (nb.t < 0) break;
+      if (nb.t < 0) { whole = true; break; }
       b = nb;
       side[ns++] = b.t;
     }
     first = b;   // the end whose before-v edge is a subsegment (or the hull)
   }
-  if (wait || ns >= FF_DEG_MAX) return FF_NONE;
-  const bool on_seg = !closed;   // a midpoint's star is cut by its two subsegments
-  if (!on_seg && ns == 3) {   // flop
+  if (whole && closed && ns > 3 && ns <= FF_RETRI_MAX) {   // a small star: re-triangulated
+    if (wait) return FF_NONE;
+    int tmin = side[0];
+    for (int q = 1; q < ns; ++q) tmin = min(tmin, side[q]);
+    if (t != tmin) return FF_NONE;
+    const unsigned long long key = ff_key(P, step, 2, tmin, 3);
+    for (int q = 0; q < ns; ++q) atomicMax(&P.ffmark[side[q]], key);
+    P.fprop[k] = tmin;
+    return FF_RETRI;
+  }
+  if (whole && closed && ns == 3) {   // flop of a free point of degree three
+    if (wait) return FF_NONE;
     int tmin = side[0];
     for (int q = 1; q < 3; ++q) tmin = min(tmin, side[q]);
     if (t != tmin) return FF_NONE;
@@ -337,24 +364,27 @@ __device__ int ff_propose_removal(const Pool& P, int k, int t, int j, int v, int
     P.fprop[k] = tmin;
     return FF_FLOP;
   }
-  if (on_seg && !closed && ns == 2) {
-    // the other side: across the subsegment before v of the first triangle
+  if (whole && !closed && ns == 2) {   // a midpoint: unsplit once both sides have two triangles
     const int e = before_edge(first.j);
     const int r = comp(P.N[first.t], e);
-    int other[FF_DEG_MAX], no = 0;
+    int other[4], no = 0;
     if (r >= 0) {
       // (v, p2, d) across the subsegment, then counter-clockwise to (v, d, p1)
       Corner o{r >> 2, pos_of(P.T[r >> 2], v)};
       other[no++] = o.t;
-      for (int s = 0; s < FF_DEG_MAX - 1; ++s) {
+      for (int s = 0; s < 3; ++s) {
+        if (ff_blocks(P, comp(P.T[o.t], mod3(o.j + 1)), kv) || ff_blocks(P, comp(P.T[o.t], mod3(o.j + 2)), kv))
+          wait = true;
         o = step_around(P, o, v, false, true);
         if (o.t < 0) break;
+        if (no == 4) { no = 5; break; }
         other[no++] = o.t;
       }
     }
-    if (no != 0 && no != 2) return FF_NONE;   // the other side flips first
-    int tmin = side[0];
-    tmin = min(tmin, side[1]);
+    // a side of two triangles cannot lose another edge: it waits for the other
+    if (no != 0 && no != 2) return FF_NONE;
+    if (wait) return FF_NONE;
+    int tmin = min(side[0], side[1]);
     for (int q = 0; q < no; ++q) tmin = min(tmin, other[q]);
     if (t != tmin) return FF_NONE;
     const unsigned long long key = ff_key(P, step, 2, tmin, 3);
@@ -371,7 +401,19 @@ __device__ int ff_propose_removal(const Pool& P, int k, int t, int j, int v, int
   const int r = comp(P.N[t], ea);
   if (r < 0) return FF_NONE;
   const int x = comp(T4, mod3(j + 1)), y = comp(T4, mod3(j + 2));
-  const int w = comp(P.T[r >> 2], r & 3);
+  const int4 U4 = P.T[r >> 2];
+  const int w = comp(U4, r & 3);
+  if (ff_blocks(P, x, kv) || ff_blocks(P, y, kv) || ff_blocks(P, w, kv)) return FF_NONE;
+  // The flip makes (y, v, w) and (y, w, x).  Neither may get the two halves of
+  // a split subsegment as two of its edges (a sliver through a split point a
+  // rounding error off its segment): not at v (edges (y, v) and (v, w)), not
+  // at x when x is a split point (edges (x, y) and (w, x)).
+  const int jw = pos_of(U4, v);
+  if (jw < 0) return FF_NONE;
+  const bool c_yv = cbit(T4, before_edge(j)), c_vw = cbit(U4, after_edge(jw));
+  const bool c_xy = cbit(T4, j), c_wx = cbit(U4, jw);
+  if (c_yv && c_vw) return FF_NONE;
+  if (P.vseg[x] >= 0 && c_xy && c_wx) return FF_NONE;
   if (orient(pt(P, y), pt(P, v), pt(P, w)) <= 0 || orient(pt(P, y), pt(P, w), pt(P, x)) <= 0) return FF_NONE;
   const unsigned long long key = ff_key(P, step, 1, t, ea);
   atomicMax(&P.ffmark[t], key);
@@ -577,6 +619,136 @@ __device__ int ff_unsplit(const Pool& P, int t, int v, unsigned long long key, i
   return e1.t;
 }
 
+// The star of free point v (4 to FF_RETRI_MAX triangles, found
+// counter-clockwise from t, each owned) is removed with v and its link
+// polygon triangulated by ear clipping: an ear is a strictly convex corner
+// whose triangle holds no other polygon vertex, inside or on its edges
+// (exact orient), so collinear link vertices -- split points along a
+// subsegment -- are handled where no flip is strictly convex.  In general
+// position this gives a triangulation that flips and a flop also reach; the
+// Lawson flips that follow make it Delaunay.  The new triangles take the
+// lowest slots of the star; the two highest die and keep, for the link pass,
+// the list of new slots (T.x = count, T.y, T.z, N.x, N.y of the first dead
+// slot).  Returns that slot, or -1 when a triangle is not owned.
+__device__ int ff_retri(const Pool& P, int t, int v, unsigned long long key, int step) {
+  int st[FF_RETRI_MAX], sj[FF_RETRI_MAX], ns = 0;
+  Corner c{t, pos_of(P.T[t], v)};
+  for (int q = 0; q < FF_RETRI_MAX; ++q) {
+    if (c.t < 0 || __ldcg(&P.ffmark[c.t]) != key) return -1;
+    if (c.j < 0) {
+      set_err(P.ctrl, S_INTERNAL);
+      atomicCAS(&P.ctrl->dbg, 0, 6);
+      return -1;
+    }
+    st[ns] = c.t;
+    sj[ns] = c.j;
+    ++ns;
+    c = step_around(P, c, v, false, false);
+    if (c.t == t) break;
+  }
+  if (c.t != t || ns < 4) return -1;
+  // link polygon x[0..ns) counter-clockwise; edge i = (x_i, x_{i+1}) is the
+  // edge opposite v in st[i]: its outer ref, subsegment bit and origin
+  int x[FF_RETRI_MAX], er[FF_RETRI_MAX], ec[FF_RETRI_MAX], eo[FF_RETRI_MAX];
+  for (int q = 0; q < ns; ++q) {
+    x[q] = comp(P.T[st[q]], mod3(sj[q] + 1));
+    er[q] = comp(P.N[st[q]], sj[q]);
+    ec[q] = cbit(P.T[st[q]], sj[q]);
+    eo[q] = (st[q] << 2) | sj[q];   // where the outside refers to this edge
+  }
+  const int m = P.T[t].w >> 4;
+  int slot[FF_RETRI_MAX];
+  for (int q = 0; q < ns; ++q) slot[q] = st[q];
+  for (int a = 1; a < ns; ++a)   // ascending slots
+    for (int b = a; b > 0 && slot[b] < slot[b - 1]; --b) {
+      const int tmp = slot[b];
+      slot[b] = slot[b - 1];
+      slot[b - 1] = tmp;
+    }
+  // polygon edges: outer (internal = -1) or an edge (s << 2 | e) of a new triangle
+  int in_e[FF_RETRI_MAX], nxt[FF_RETRI_MAX], prv[FF_RETRI_MAX];
+  for (int q = 0; q < ns; ++q) {
+    in_e[q] = -1;
+    nxt[q] = q + 1 < ns ? q + 1 : 0;
+    prv[q] = q > 0 ? q - 1 : ns - 1;
+  }
+  int4 NT[FF_RETRI_MAX - 2], NN[FF_RETRI_MAX - 2];
+  int used = 0, left = ns, start = 0;
+  // set edge e of new triangle u from polygon edge i
+  auto put = [&](int u, int e, int i) {
+    int* nref = comp_ptr(&NN[u], e);
+    if (in_e[i] < 0) {
+      *nref = er[i];
+      NT[u].w |= ec[i] << e;
+      P.newref[eo[i]] = (slot[u] << 2) | e;
+    } else {
+      *nref = in_e[i];
+      const int ou = in_e[i] >> 2, oe = in_e[i] & 3;   // ou: index of a new triangle
+      *comp_ptr(&NN[ou], oe) = (slot[u] << 2) | e;
+      *nref = (slot[ou] << 2) | oe;
+    }
+  };
+  int guard = 0;
+  while (left > 3 && guard++ < 64) {
+    int b = start, found = -1;
+    for (int r = 0; r < left; ++r, b = nxt[b]) {
+      const int a = prv[b], cc = nxt[b];
+      if (orient(pt(P, x[a]), pt(P, x[b]), pt(P, x[cc])) <= 0) continue;
+      bool ear = true;
+      for (int q = nxt[cc]; q != a && ear; q = nxt[q]) {
+        const P2 pq = pt(P, x[q]);
+        if (orient(pt(P, x[a]), pt(P, x[b]), pq) >= 0 && orient(pt(P, x[b]), pt(P, x[cc]), pq) >= 0 &&
+            orient(pt(P, x[cc]), pt(P, x[a]), pq) >= 0)
+          ear = false;
+      }
+      if (ear) { found = b; break; }
+    }
+    if (found < 0) {   // a star-shaped polygon always has an ear
+      set_err(P.ctrl, S_INTERNAL);
+      atomicCAS(&P.ctrl->dbg, 0, 7);
+      return -1;
+    }
+    const int a = prv[found], cc = nxt[found];
+    const int u = used++;
+    // ear (x_a, x_b, x_c): edge 0 = (x_b, x_c) polygon edge found, edge 1 = (x_c, x_a)
+    // the new diagonal, edge 2 = (x_a, x_b) polygon edge a
+    NT[u] = make_int4(x[a], x[found], x[cc], m << 4);
+    NN[u] = make_int4(-1, -1, -1, 0);
+    put(u, 0, found);
+    put(u, 2, a);
+    in_e[a] = (u << 2) | 1;   // the diagonal is now polygon edge a
+    nxt[a] = cc;
+    prv[cc] = a;
+    start = cc;
+    --left;
+  }
+  {
+    const int a = start, b = nxt[a], cc = nxt[b];
+    const int u = used++;
+    NT[u] = make_int4(x[a], x[b], x[cc], m << 4);
+    NN[u] = make_int4(-1, -1, -1, 0);
+    put(u, 0, b);
+    put(u, 1, cc);
+    put(u, 2, a);
+  }
+  for (int q = 0; q < ns; ++q) P.tstamp[st[q]] = step;
+  for (int u = 0; u < used; ++u) {
+    P.T[slot[u]] = NT[u];
+    P.N[slot[u]] = NN[u];
+    ff_touch(P, slot[u], step);
+    for (int e = 0; e < 3; ++e) P.vtri[comp(NT[u], e)] = slot[u];
+  }
+  const int d1 = slot[ns - 2], d2 = slot[ns - 1];
+  ff_kill(P, d1, step);
+  ff_kill(P, d2, step);
+  // the record of the new slots for the link pass, in the first dead slot
+  P.T[d1] = make_int4(used, used > 0 ? slot[0] : -1, used > 1 ? slot[1] : -1, (m << 4) | INFO_DEAD);
+  P.N[d1] = make_int4(used > 2 ? slot[2] : -1, used > 3 ? slot[3] : -1, -1, 0);
+  ff_removed(P, v, m);
+  atomicAdd(&P.ctrl->ff_flops, 1ull);
+  return d1;
+}
+
 // the triangle t of list entry k goes to the next pass unless its work is done
 __device__ __forceinline__ void ff_retry(const Pool& P, int t, int step) {
   const int4 T4 = P.T[t];
@@ -616,6 +788,14 @@ __global__ void __launch_bounds__(BS) k_ff_do(Pool P) {
     if (kind == FF_FLOP) {
       if (v >= 0 && ff_flop(P, t, v, key, step)) P.fop[k] = op | FF_EXEC;
       else ff_retry(P, t, step);
+    } else if (kind == FF_RETRI) {
+      const int d1 = v >= 0 ? ff_retri(P, t, v, key, step) : -1;
+      if (d1 >= 0) {
+        P.fprop[k] = d1;
+        P.fop[k] = op | FF_EXEC;
+      } else {
+        ff_retry(P, t, step);
+      }
     } else {
       const int up = v >= 0 ? ff_unsplit(P, t, v, key, step) : -1;
       if (up >= 0) {
@@ -647,6 +827,23 @@ __global__ void __launch_bounds__(BS) k_ff_link(Pool P) {
     } else if (kind == FF_FLOP) {
       const int t = P.fl_cur[k];
       for (int e = 0; e < 3; ++e) flip_fix(P, t, e, step);
+    } else if (kind == FF_RETRI) {
+      // the new slots from the record in the first dead slot; edges between
+      // two of them were linked by the operation itself
+      const int d1 = P.fprop[k];
+      const int4 R = P.T[d1];
+      const int4 R2 = P.N[d1];
+      const int ns[4] = {R.y, R.z, R2.x, R2.y};
+      const int cnt = min(R.x, 4);
+      for (int u = 0; u < cnt; ++u) {
+        const int su = ns[u];
+        for (int e = 0; e < 3; ++e) {
+          const int r = comp(P.N[su], e);
+          bool inner = false;
+          for (int q = 0; q < cnt; ++q) inner |= (r >= 0 && (r >> 2) == ns[q]);
+          if (!inner) flip_fix(P, su, e, step);
+        }
+      }
     } else {
       const int up = P.fprop[k];
       flip_fix(P, up, 0, step);
@@ -775,7 +972,7 @@ __global__ void __launch_bounds__(FF_CT) k_ff_move(Pool P) {
         const int v = base + threadIdx.x;
         const int to = v < v1 ? P.vmap[v] : -1;
         double2 V = make_double2(0, 0);
-        float2 Vf = make_float2(0, 0);
+        float4 Vf = make_float4(0, 0, 0, 0);
         int vs = -1, vt = -1;
         if (to >= 0) {
           V = P.V[v];

@@ -109,8 +109,12 @@ __device__ __forceinline__ Chunk chunk_of(int n) {
 }
 
 __device__ __forceinline__ P2 pt(const Pool& P, int v) { return P2{P.V[v], P.Vf[v]}; }
-__device__ __forceinline__ float2 to_f(double2 p, double2 org) {
-  return make_float2(__double2float_rn(__dsub_rn(p.x, org.x)), __double2float_rn(__dsub_rn(p.y, org.y)));
+// the two-float copy of p - org (see the FP32 filter stage of the predicates)
+__device__ __forceinline__ float4 to_f(double2 p, double2 org) {
+  const double tx = __dsub_rn(p.x, org.x), ty = __dsub_rn(p.y, org.y);
+  const float hx = __double2float_rn(tx), hy = __double2float_rn(ty);
+  return make_float4(hx, hy, __double2float_rn(__dsub_rn(tx, (double)hx)),
+                     __double2float_rn(__dsub_rn(ty, (double)hy)));
 }
 
 // ---------------------------------------------------------------- mesh queries
@@ -274,10 +278,10 @@ __device__ int eval_tri(const Pool& P, int t) {
 __device__ __forceinline__ int cap_bucket(const Pool& P, const int4& T4, int code) {
   float v;
   if (code == 4) {
-    const float2 a = P.Vf[T4.x], b = P.Vf[T4.y], c = P.Vf[T4.z];
+    const float4 a = P.Vf[T4.x], b = P.Vf[T4.y], c = P.Vf[T4.z];
     v = fabsf((b.x - a.x) * (c.y - a.y) - (b.y - a.y) * (c.x - a.x));
   } else {
-    const float2 u = P.Vf[comp(T4, mod3(code))], w = P.Vf[comp(T4, mod3(code + 1))];
+    const float4 u = P.Vf[comp(T4, mod3(code))], w = P.Vf[comp(T4, mod3(code + 1))];
     v = (w.x - u.x) * (w.x - u.x) + (w.y - u.y) * (w.y - u.y);
   }
   const uint32_t b = (v >= 0.0f && v < INFINITY) ? (__float_as_uint(v) >> 22) : 0x1ffu;
@@ -696,7 +700,7 @@ __device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a, int timed =
 // vertex id, c_loc = located triangle).  False when the walk failed.
 struct CandSetup {
   double2 p;
-  float2 pf;
+  float4 pf;
   unsigned long long key;
   int t0, t1, m, vid;
   int2 sub;

@@ -29,7 +29,8 @@ constexpr double kU = 1.1102230246251565e-16;   // 2^-53
 // -DGDP_DIAG: exact-path calls and maxima
 // 0 orient_exact, 1 incircle_exact, 2 incircle tie (simulation of simplicity),
 // 3 dot_exact, 4 incircle_exact with inexact differences, 5 max walk steps,
-// 6 max cycles in one grow, 7 max cycles in one walk, 8 max cycles of one exact incircle
+// 6 max cycles in one grow, 7 max cycles in one walk, 8 max cycles of one exact incircle,
+// 9/10/11 orient / incircle / dot calls, 12/13/14 of them past the FP32 filter
 static __device__ unsigned long long g_diag[16];
 #ifdef GDP_DIAG
 #define GDP_DIAG_ADD(i) atomicAdd(&g_diag[i], 1ull)
@@ -569,47 +570,72 @@ __device__ __forceinline__ int lens_q_f64(double2 a, double2 b, double2 p) {
 
 // ---------------------------------------------------------------- FP32 filter stage
 // GB300 executes FP64 at 1/64 of the FP32 rate, so every predicate first runs
-// in FP32 on float copies of the coordinates, translated to the mesh's
-// bounding-box centre: f = fl32(fl64(x - origin)).  Each float coordinate is
-// within v*M*(1+3v) of the exact translated value (v = 2^-24, M the largest
-// |float coordinate| of the test), so each float difference is within
-// E = 4.001 v M of the exact difference.  The bounds below add that input
-// error to the rounding error of the float evaluation; when the float value
-// cannot decide, the FP64 filter and then exact arithmetic do.
+// in FP32.  Each vertex keeps its coordinates translated to the mesh's
+// bounding-box centre o as two floats: t = fl64(x - o), hi = fl32(t),
+// lo = fl32(t - hi) (t - hi is exact in FP64), so hi + lo is within
+// 2^-48 |t| of t and within 1.04 * 2^-48 M of x - o (M the largest |hi| of a
+// test).  A coordinate difference is taken as s = fl32(fl32(hi_a - hi_b) +
+// fl32(lo_a - lo_b)); working through the three roundings, s is within
+//   delta(s) = 2.0001 v |s| + E3,   v = 2^-24,  E3 = 2^-44 M
+// of the exact difference: relative to the difference itself, not to the
+// coordinates, so small features far from the centre still filter well.
+// Each filter adds the effect of delta on its products to the rounding error
+// of its float evaluation; when the float value cannot decide, the FP64
+// filter and then exact arithmetic do.
 constexpr float kV = 5.9604645e-8f;   // 2^-24
+constexpr float kE3 = 5.6843419e-14f;  // 2^-44
 
 struct P2 {
   double2 d;   // exact (FP64) coordinates
-  float2 f;    // translated float copy
+  float4 f;    // translated copy as two floats: (hi.x, hi.y, lo.x, lo.y)
 };
 
 __device__ __forceinline__ float fmax6(float a, float b, float c, float d, float e, float g) {
   return fmaxf(fmaxf(fmaxf(a, b), fmaxf(c, d)), fmaxf(e, g));
 }
 
-// sign of (ax-cx)(by-cy) - (ay-cy)(bx-cx) when certain, else 0
-__device__ __forceinline__ int orient_f32(float2 a, float2 b, float2 c) {
-  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(c.x), fabsf(c.y));
-  if (!(M < 1e8f) || M < 1e-15f) return 0;
-  const float d1 = __fsub_rn(a.x, c.x), d2 = __fsub_rn(b.y, c.y);
-  const float d3 = __fsub_rn(a.y, c.y), d4 = __fsub_rn(b.x, c.x);
-  const float l = __fmul_rn(d1, d2), r = __fmul_rn(d3, d4);
-  const float det = __fsub_rn(l, r);
-  const float E = 4.001f * kV * M;
-  // |det - exact| <= E (|d1|+|d2|+|d3|+|d4| + 2E) + (2v + v^2)(|l| + |r|)
-  const float err = (E * (fabsf(d1) + fabsf(d2) + fabsf(d3) + fabsf(d4) + 2.0f * E) +
-                     2.0001f * kV * (fabsf(l) + fabsf(r))) * 1.001f + 1e-37f;
-  return det > err ? 1 : (-det > err ? -1 : 0);
+// the two float differences a - b (x, y)
+__device__ __forceinline__ float dfx(const float4& a, const float4& b) {
+  return __fadd_rn(__fsub_rn(a.x, b.x), __fsub_rn(a.z, b.z));
+}
+__device__ __forceinline__ float dfy(const float4& a, const float4& b) {
+  return __fadd_rn(__fsub_rn(a.y, b.y), __fsub_rn(a.w, b.w));
+}
+__device__ __forceinline__ float hmax3(const float4& a, const float4& b, const float4& c) {
+  return fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(c.x), fabsf(c.y));
 }
 
-// sign of the incircle determinant (same evaluation order as the FP64 filter)
-__device__ __forceinline__ int incircle_f32(float2 a, float2 b, float2 c, float2 d) {
-  const float M = fmaxf(fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(c.x), fabsf(c.y)),
-                        fmaxf(fabsf(d.x), fabsf(d.y)));
+// sign of s1 s2 - s3 s4 (sg = -1) or s1 s2 + s3 s4 (sg = +1) from four
+// differences, when certain, else 0.  Input error: each product is off by at
+// most 4.0003 v |s_i s_j| + E3 (|s_i| + |s_j|) + E3^2 from the differences;
+// rounding of the two products and the sum: 2.0001 v (|p| + |q|).
+__device__ __forceinline__ int sign2_f32(float s1, float s2, float s3, float s4, float sg, float M) {
+  const float p = __fmul_rn(s1, s2), q = __fmul_rn(s3, s4);
+  const float val = sg > 0.0f ? __fadd_rn(p, q) : __fsub_rn(p, q);
+  const float E3 = kE3 * M;
+  const float err = (6.0005f * kV * (fabsf(p) + fabsf(q)) +
+                     E3 * (fabsf(s1) + fabsf(s2) + fabsf(s3) + fabsf(s4) + 2.0f * E3)) * 1.001f + 1e-37f;
+  return val > err ? 1 : (-val > err ? -1 : 0);
+}
+
+// sign of (ax-cx)(by-cy) - (ay-cy)(bx-cx) when certain, else 0
+__device__ __forceinline__ int orient_f32(float4 a, float4 b, float4 c) {
+  const float M = hmax3(a, b, c);
+  if (!(M < 1e8f) || M < 1e-15f) return 0;
+  return sign2_f32(dfx(a, c), dfy(b, c), dfy(a, c), dfx(b, c), -1.0f, M);
+}
+
+// sign of the incircle determinant (same evaluation order as the FP64 filter).
+// Input error: each of the 12 degree-4 monomials is off by at most
+// ((1 + 2.0001 v)^4 - 1) |monomial| + 4 E3 (L' + E3)^3 (L' the largest |s|
+// grown by 2.0001 v), in all 8.0013 v perm + 48 E3 (L' + E3)^3; rounding of
+// the float evaluation: 12.5 v perm (11 v to first order).
+__device__ __forceinline__ int incircle_f32(float4 a, float4 b, float4 c, float4 d) {
+  const float M = fmaxf(hmax3(a, b, c), fmaxf(fabsf(d.x), fabsf(d.y)));
   if (!(M < 1e7f) || M < 1e-7f) return 0;
-  const float adx = __fsub_rn(a.x, d.x), ady = __fsub_rn(a.y, d.y);
-  const float bdx = __fsub_rn(b.x, d.x), bdy = __fsub_rn(b.y, d.y);
-  const float cdx = __fsub_rn(c.x, d.x), cdy = __fsub_rn(c.y, d.y);
+  const float adx = dfx(a, d), ady = dfy(a, d);
+  const float bdx = dfx(b, d), bdy = dfy(b, d);
+  const float cdx = dfx(c, d), cdy = dfy(c, d);
   const float p1 = __fmul_rn(bdx, cdy), p2 = __fmul_rn(cdx, bdy);
   const float p3 = __fmul_rn(cdx, ady), p4 = __fmul_rn(adx, cdy);
   const float p5 = __fmul_rn(adx, bdy), p6 = __fmul_rn(bdx, ady);
@@ -621,45 +647,36 @@ __device__ __forceinline__ int incircle_f32(float2 a, float2 b, float2 c, float2
   const float perm = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(p1), fabsf(p2)), al),
                                          __fmul_rn(__fadd_rn(fabsf(p3), fabsf(p4)), bl)),
                                __fmul_rn(__fadd_rn(fabsf(p5), fabsf(p6)), cl));
-  const float L = fmax6(fabsf(adx), fabsf(ady), fabsf(bdx), fabsf(bdy), fabsf(cdx), fabsf(cdy));
-  const float E = 4.001f * kV * M;
-  const float LE = L + E;
-  // input error: 12 degree-4 monomials, each off by <= (L+E)^4 - L^4 <= 4E(L+E)^3;
-  // rounding of the float evaluation: <= 11v perm to first order
-  const float err = (48.0f * E * LE * LE * LE + 12.5f * kV * perm) * 1.001f + 1e-37f;
+  const float L = fmax6(fabsf(adx), fabsf(ady), fabsf(bdx), fabsf(bdy), fabsf(cdx), fabsf(cdy)) * (1.0f + 2.0002f * kV);
+  const float E3 = kE3 * M;
+  const float LE = L + E3;
+  const float err = (20.6f * kV * perm + 48.0f * E3 * LE * LE * LE) * 1.001f + 1e-37f;
   return det > err ? 1 : (-det > err ? -1 : 0);
 }
 
 // sign of (a-p).(b-p) when certain, else 0
-__device__ __forceinline__ int dot_f32(float2 a, float2 b, float2 p) {
-  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(p.x), fabsf(p.y));
+__device__ __forceinline__ int dot_f32(float4 a, float4 b, float4 p) {
+  const float M = hmax3(a, b, p);
   if (!(M < 1e8f) || M < 1e-15f) return 0;
-  const float d1 = __fsub_rn(a.x, p.x), d2 = __fsub_rn(b.x, p.x);
-  const float d3 = __fsub_rn(a.y, p.y), d4 = __fsub_rn(b.y, p.y);
-  const float t1 = __fmul_rn(d1, d2), t2 = __fmul_rn(d3, d4);
-  const float s = __fadd_rn(t1, t2);
-  const float E = 4.001f * kV * M;
-  const float err = (E * (fabsf(d1) + fabsf(d2) + fabsf(d3) + fabsf(d4) + 2.0f * E) +
-                     2.0001f * kV * (fabsf(t1) + fabsf(t2))) * 1.001f + 1e-37f;
-  return s > err ? 1 : (-s > err ? -1 : 0);
+  return sign2_f32(dfx(a, p), dfx(b, p), dfy(a, p), dfy(b, p), 1.0f, M);
 }
 
 // FP32 filter for the sign of Q = 3 D^2 - C^2 when D < 0 is known (see
-// lens_q_exact): D and C from the float copies with the bound of dot_f32
-// (input error E per difference plus rounding), then Q over the intervals
-// with the float rounding folded into the factors 1 -+ 8v.  0 when unsure.
-__device__ __forceinline__ int lens_q_f32(float2 a, float2 b, float2 p) {
-  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(p.x), fabsf(p.y));
+// lens_q_exact): D and C from the float differences with the bound of
+// sign2_f32, then Q over the intervals with the float rounding folded into
+// the factors 1 -+ 8v.  0 when unsure.
+__device__ __forceinline__ int lens_q_f32(float4 a, float4 b, float4 p) {
+  const float M = hmax3(a, b, p);
   if (!(M < 1e8f) || M < 1e-15f) return 0;
-  const float ux = __fsub_rn(a.x, p.x), uy = __fsub_rn(a.y, p.y);
-  const float wx = __fsub_rn(b.x, p.x), wy = __fsub_rn(b.y, p.y);
+  const float ux = dfx(a, p), uy = dfy(a, p);
+  const float wx = dfx(b, p), wy = dfy(b, p);
   const float t1 = __fmul_rn(ux, wx), t2 = __fmul_rn(uy, wy);
   const float t3 = __fmul_rn(ux, wy), t4 = __fmul_rn(uy, wx);
   const float aD = fabsf(__fadd_rn(t1, t2)), aC = fabsf(__fsub_rn(t3, t4));
-  const float E = 4.001f * kV * M;
-  const float es = E * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy) + 2.0f * E);
-  const float eD = (es + 2.0001f * kV * (fabsf(t1) + fabsf(t2))) * 1.001f + 1e-37f;
-  const float eC = (es + 2.0001f * kV * (fabsf(t3) + fabsf(t4))) * 1.001f + 1e-37f;
+  const float E3 = kE3 * M;
+  const float es = E3 * (fabsf(ux) + fabsf(uy) + fabsf(wx) + fabsf(wy) + 2.0f * E3);
+  const float eD = (es + 6.0005f * kV * (fabsf(t1) + fabsf(t2))) * 1.001f + 1e-37f;
+  const float eC = (es + 6.0005f * kV * (fabsf(t3) + fabsf(t4))) * 1.001f + 1e-37f;
   constexpr float kSmall = 1e-17f;   // squares of larger values stay normal
   if (!(aD - eD > kSmall) || !(aD + eD < 1e17f) || !(aC + eC < 1e17f)) return 0;
   const float dlo = aD - eD, dhi = aD + eD;
@@ -674,11 +691,15 @@ __device__ __forceinline__ int lens_q_f32(float2 a, float2 b, float2 p) {
 
 __device__ __forceinline__ int orient(const P2& a, const P2& b, const P2& c) {
   const int s = orient_f32(a.f, b.f, c.f);
+  GDP_DIAG_ADD(9);
+  if (!s) GDP_DIAG_ADD(12);
   return s ? s : orient(a.d, b.d, c.d);
 }
 
 __device__ __forceinline__ int dot_sign(const P2& a, const P2& b, const P2& p) {
   const int s = dot_f32(a.f, b.f, p.f);
+  GDP_DIAG_ADD(11);
+  if (!s) GDP_DIAG_ADD(14);
   return s ? s : dot_sign(a.d, b.d, p.d);
 }
 
@@ -702,6 +723,8 @@ __device__ __forceinline__ bool encroaches(const P2& a, const P2& b, const P2& p
 
 __device__ __forceinline__ int incircle(const P2& a, const P2& b, const P2& c, const P2& d) {
   const int s = incircle_f32(a.f, b.f, c.f, d.f);
+  GDP_DIAG_ADD(10);
+  if (!s) GDP_DIAG_ADD(13);
   return s ? s : incircle(a.d, b.d, c.d, d.d);
 }
 
@@ -743,25 +766,27 @@ __device__ __forceinline__ bool is_bad(const TriTerms& t, double B2) {
 // FP32 pre-check of is_bad: +1 when the FP64 formula above surely says bad,
 // -1 when it surely says good, 0 when the float intervals overlap.  Interval
 // bounds for the exact squared lengths and doubled area come from the float
-// differences (input error E each, as in the predicates); the FP64 formula is
-// within ~20 u of the exact quantities, far inside the float margins.
-__device__ __forceinline__ int bad_f32(float2 a, float2 b, float2 c, float B2f) {
-  const float M = fmax6(fabsf(a.x), fabsf(a.y), fabsf(b.x), fabsf(b.y), fabsf(c.x), fabsf(c.y));
+// differences (error delta(s) each, as in the predicates): a squared length
+// x^2 + y^2 is off by at most 6.01 v (x^2 + y^2) + 2.01 E3 (|x| + |y|) + 2 E3^2
+// with its own rounding, the doubled area as in sign2_f32; the FP64 formula
+// is within ~20 u of the exact quantities, far inside the float margins.
+__device__ __forceinline__ int bad_f32(float4 a, float4 b, float4 c, float B2f) {
+  const float M = hmax3(a, b, c);
   if (!(M < 1e7f) || M < 1e-6f) return 0;
-  const float E = 4.001f * kV * M;
-  const float x1 = __fsub_rn(b.x, a.x), y1 = __fsub_rn(b.y, a.y);
-  const float x2 = __fsub_rn(c.x, a.x), y2 = __fsub_rn(c.y, a.y);
-  const float x3 = __fsub_rn(c.x, b.x), y3 = __fsub_rn(c.y, b.y);
+  const float E3 = kE3 * M;
+  const float x1 = dfx(b, a), y1 = dfy(b, a);
+  const float x2 = dfx(c, a), y2 = dfy(c, a);
+  const float x3 = dfx(c, b), y3 = dfy(c, b);
   const float la = __fadd_rn(__fmul_rn(x1, x1), __fmul_rn(y1, y1));
   const float lb = __fadd_rn(__fmul_rn(x2, x2), __fmul_rn(y2, y2));
   const float lc = __fadd_rn(__fmul_rn(x3, x3), __fmul_rn(y3, y3));
-  const float ea = E * (2.0f * (fabsf(x1) + fabsf(y1)) + 2.0f * E) + 2.001f * kV * la;
-  const float eb = E * (2.0f * (fabsf(x2) + fabsf(y2)) + 2.0f * E) + 2.001f * kV * lb;
-  const float ec = E * (2.0f * (fabsf(x3) + fabsf(y3)) + 2.0f * E) + 2.001f * kV * lc;
+  const float ea = 6.01f * kV * la + 2.01f * E3 * (fabsf(x1) + fabsf(y1)) + 2.0f * E3 * E3;
+  const float eb = 6.01f * kV * lb + 2.01f * E3 * (fabsf(x2) + fabsf(y2)) + 2.0f * E3 * E3;
+  const float ec = 6.01f * kV * lc + 2.01f * E3 * (fabsf(x3) + fabsf(y3)) + 2.0f * E3 * E3;
   const float t1 = __fmul_rn(x1, y2), t2 = __fmul_rn(y1, x2);
   const float cr = fabsf(__fsub_rn(t1, t2));
-  const float ecr = E * (fabsf(x1) + fabsf(y2) + fabsf(y1) + fabsf(x2) + 2.0f * E) +
-                    2.001f * kV * (fabsf(t1) + fabsf(t2));
+  const float ecr = 6.0005f * kV * (fabsf(t1) + fabsf(t2)) +
+                    E3 * (fabsf(x1) + fabsf(y2) + fabsf(y1) + fabsf(x2) + 2.0f * E3);
   if (!(la > ea && lb > eb && lc > ec && cr > ecr)) return 0;
   const float lo = 1.0f - 16.0f * kV, hi = 1.0f + 16.0f * kV;
   const float lhs_lo = (la - ea) * (lb - eb) * (lc - ec) * lo;
