@@ -49,7 +49,7 @@ WORKLOAD_NAMES = {
 REF_SAMPLE = {"n_uniform": 125_000, "n_gauss": 75_000, "n_circle": 50_000, "n_seg": 2_500, "n_fans": 5}
 
 # Algorithmic bytes of the dominant step of the refinement, cavity growth
-# (k_grow_w<0>, or k_grow_t<0> above 32,768 candidates; Sec. 5.2-5.3), per unit of
+# (k_grow_w<0>, or k_grow_g<0> above 32,768 candidates; Sec. 5.2-5.3), per unit of
 # work the library counts on the device:
 #   per cavity of k triangles: the k cavity triangles and the k + 2 triangles
 #   across its boundary edges are read, each 12 B of vertex ids + 48 B of FP64
@@ -61,8 +61,10 @@ GROW_BYTES = {"candidate": 120, "cavity_tri": 136, "walk_step": 76}
 GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
 # the kernels of one refinement iteration (launched once per iteration, so an ncu
 # launch list counts them in every step and their shares compare directly)
-REFINE_KERNELS = ("k_scan_eval", "k_scan_count", "k_scan_write", "k_grow_w<0>", "k_grow_t<0>", "k_grow_big<0>",
-                  "k_survive", "k_depend", "k_insert_w<0>", "k_insert_t<0>", "k_link<0>")
+GROW_KERNELS = ("k_grow_w<0>", "k_grow_g<0>", "k_grow_t<0>")
+REFINE_KERNELS = ("k_scan_eval", "k_scan_count", "k_scan_write") + GROW_KERNELS + (
+    "k_grow_big<0>", "k_survive", "k_depend", "k_offsets", "k_insert_w<0>", "k_insert_g<0>", "k_insert_t<0>",
+    "k_link<0>")
 # ncu counters of the cavity-growth kernels over one whole refine of the bench
 # workload, per grown candidate (DRAM and L2 bytes, FP64 flops, FP64 pipe)
 COUNTERS_FILE = os.path.join(ROOT, "profiles", "cavity_growth_paper_shaped_counters.md")
@@ -687,10 +689,11 @@ def main():
     if "l2_bytes_per_grown" in cnt and sec > 0:
         l2 = {"bytes_per_launch": cnt["l2_bytes_per_grown"] * per_launch,
               "achieved": cnt["l2_bytes_per_grown"] * timed["grown"] / sec / 1e9, "unit": "GB/s"}
-    share = sum(kt.get(k, (0.0, 0))[0] for k in ("k_grow_w<0>", "k_grow_t<0>"))
+    share = sum(kt.get(k, (0.0, 0))[0] for k in GROW_KERNELS)
+    grow_names = " + ".join(k for k in GROW_KERNELS if k in kt) or "k_grow_w<0>"
     roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
             "frac": (gbs / peak) if gbs else None, "traffic": traffic,
-            "kernel": "cavity growth: k_grow_w<0> + k_grow_t<0>", "algorithmic_bytes_per_launch": by / n_l,
+            "kernel": f"cavity growth: {grow_names}", "algorithmic_bytes_per_launch": by / n_l,
             "kernel_ms_per_launch": grow["grow_ms"] / n_l, "launches": grow["grow_launches"],
             "grown_candidates_per_launch": per_launch,
             "share_of_kernel_time": share / tot_k,

@@ -1125,7 +1125,8 @@ int PoolHost::launch_iteration(int k) {
   LAUNCH(*this, k_depend, G, P);
   LAUNCH(*this, k_offsets, G, P);
   LAUNCH_B(*this, k_insert_w<0>, n_sm * 16, 128, P);
-  LAUNCH_C(*this, k_insert_t<0>, P);
+  if (grow_group) LAUNCH_B(*this, k_insert_g<0>, n_sm * 16, 128, P);
+  else LAUNCH_C(*this, k_insert_t<0>, P);
   LAUNCH_C(*this, k_link<0>, P);
   return cudaGetLastError() == cudaSuccess ? GDP_OK : GDP_ERR_CUDA;
 }
@@ -1684,7 +1685,8 @@ int gdp_mesh_split_subsegments(gdp_mesh* g, const double* abxy, int64_t n) {
     LAUNCH(h, k_depend, h.G, h.P);
     LAUNCH(h, k_offsets, h.G, h.P);
     LAUNCH_B(h, k_insert_w<0>, h.n_sm * 16, 128, h.P);
-    LAUNCH_C(h, k_insert_t<0>, h.P);
+    if (h.grow_group) LAUNCH_B(h, k_insert_g<0>, h.n_sm * 16, 128, h.P);
+    else LAUNCH_C(h, k_insert_t<0>, h.P);
     LAUNCH_C(h, k_link<0>, h.P);
     CK(cudaGetLastError());
     if (h.sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;

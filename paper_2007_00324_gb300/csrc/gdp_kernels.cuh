@@ -1709,6 +1709,121 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
   }
 }
 
+// The same above P.warp_max candidates by groups of GROW_GROUP lanes (four
+// candidates per warp): a group takes its cavity's boundary records (up to
+// BMAX, ceil(BMAX / 8) per lane), finds the fan neighbours by shuffles within
+// the group and writes and evaluates the new triangles in parallel.  A
+// spill-tier cavity is written by the whole warp (fan_big) after the groups.
+// Identical output to k_insert_t.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_insert_g(Pool P) {
+  constexpr int W = GROW_GROUP;
+  constexpr int R = (BMAX + W - 1) / W;   // records per lane
+  const unsigned FULL = 0xffffffffu;
+  const int n = P.ctrl->n_cand;
+  if (n <= P.warp_max) return;   // k_insert_w's case
+  const Group<W> g;
+  const unsigned lt_mask = (1u << g.gl) - 1u;
+  const int gg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
+  const int ng = (gridDim.x * blockDim.x) / W;
+  for (int i0 = gg - (gg & (32 / W - 1)); i0 < n; i0 += ng) {   // whole warps: spill tiers below
+    const int i = i0 + (gg & (32 / W - 1));
+    bool big = false;
+    int m = 0, base = 0, vid = 0;
+    if (i < n) {
+      m = P.c_mesh[i];
+      const MeshInfo& M = P.mi[m];
+      const int f = M.first_cand, l = M.last_cand;
+      int totE, totV;
+      mesh_totals(P, f, l, totE, totV);
+      const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
+      if (g.gl == 0 && i == f) {
+        P.mi[m].ins_ok = ok ? 1 : 0;
+        if (!ok) no_room<MODE>(P, m);
+      }
+      if (P.c_final[i] && ok) {
+        base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
+        vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
+        if (g.gl == 0) {
+          P.c_base[i] = base;
+          P.V[vid] = P.c_pt[i];
+          P.Vf[vid] = P.c_ptf[i];
+          P.vseg[vid] = P.c_vseg[i];
+          if (MODE == 1) P.loc[vid] = -1;
+        }
+        g.sync();   // the new vertex is read by every lane (new_tri_code)
+        big = P.c_big[i] >= 0;
+        if (!big) {
+          const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+          const int* cav = P.c_cav + (size_t)i * CMAX;
+          const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
+          const int2 sub = P.c_sub[i];
+          const bool is_mid = sub.x >= 0;
+          int4 rec[R];
+          bool keep[R];
+          int slot[R];
+          int done = 0;   // kept records before chunk h
+          for (int h = 0; h < R; ++h) {
+            const int r = g.gl + W * h;
+            rec[h] = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
+            keep[h] = r < nb && !is_split_edge(rec[h], sub);
+            const unsigned km = g.ballot(keep[h]);
+            const int j = done + __popc(km & lt_mask);
+            slot[h] = j < nc ? cav[j] : base + (j - nc);
+            done += __popc(km);
+          }
+          // fan neighbours: the record starting where mine ends (edge 2) and
+          // the one ending where mine starts (edge 1); the last match wins
+          int n1[R], n2[R];
+          for (int h = 0; h < R; ++h) n1[h] = n2[h] = -1;
+          for (int q = 0; q < nb; ++q) {
+            const int hq = q / W, src = q - W * hq;
+            int qx = -1, qy = -1, qs = -1, qk = 0;
+            for (int h = 0; h < R; ++h)
+              if (h == hq) { qx = rec[h].x; qy = rec[h].y; qs = slot[h]; qk = keep[h] ? 1 : 0; }
+            qx = g.shfl(qx, src);
+            qy = g.shfl(qy, src);
+            qs = g.shfl(qs, src);
+            qk = g.shfl(qk, src);
+            if (!qk) continue;
+            for (int h = 0; h < R; ++h) {
+              if (qx == rec[h].y) n1[h] = (qs << 2) | 2;
+              if (qy == rec[h].x) n2[h] = (qs << 2) | 1;
+            }
+          }
+          for (int h = 0; h < R; ++h) {
+            if (!keep[h]) continue;
+            const int s = slot[h];
+            const int u = rec[h].x, v = rec[h].y;
+            int cb = rec[h].w < 0 ? 1 : 0;
+            if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
+            if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
+            int n0 = rec[h].z;
+            if (n0 >= 0) {
+              if (replaced(P, n0, n)) n0 = -1;   // linked by k_link
+              else *comp_ptr(&P.N[n0 >> 2], n0 & 3) = s << 2;
+            }
+            P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
+            P.N[s] = make_int4(n0, n1[h], n2[h], 0);
+            P.newref[rec[h].w & 0x7fffffff] = s << 2;
+            new_tri_code<MODE>(P, s);
+            P.vtri[u] = s;
+            P.vtri[v] = s;
+            P.vtri[vid] = s;
+          }
+        }
+      }
+    }
+    unsigned bm = __ballot_sync(FULL, big && g.gl == 0);
+    while (bm) {
+      const int src = __ffs(bm) - 1;
+      bm &= bm - 1;
+      fan_big<MODE>(P, __shfl_sync(FULL, i, src), __shfl_sync(FULL, m, src), __shfl_sync(FULL, base, src),
+                    __shfl_sync(FULL, vid, src), n);
+    }
+  }
+}
+
 // links between adjacent cavities, then per-mesh counters
 template <int MODE>
 __global__ void __launch_bounds__(BS) k_link(Pool P) {
