@@ -431,9 +431,14 @@ struct PoolHost {
     }
   }
 
+  bool err_reported = false;
   int sync_ctrl() {
     CK(cudaMemcpyAsync(hctrl, P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
+    if (hctrl->err && !err_reported && std::getenv("GDP_TRACE")) {
+      std::fprintf(stderr, "[gdp] device error %d, first failing check site %d\n", hctrl->err, hctrl->dbg);
+      err_reported = true;
+    }
     return GDP_OK;
   }
   int pull_mi() {
@@ -1428,9 +1433,16 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
       if ((long long)hctrl->iters >= max_iter) { status = GDP_ERR_ITER_LIMIT; break; }
     }
   } else {
+    // GDP_TRACE_GROW: the running growth-work totals after every iteration
+    // (to normalise per-launch profiler counters by the work of that launch)
+    const bool trace_grow = std::getenv("GDP_TRACE_GROW") != nullptr;
     for (;;) {
       if (launch_iteration(0) != GDP_OK) return GDP_ERR_CUDA;
       if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
+      if (trace_grow)
+        std::fprintf(stderr, "[grow] iteration %llu grown %llu cavity_tris %llu walk_steps %llu\n",
+                     (unsigned long long)hctrl->iters, (unsigned long long)hctrl->n_grown,
+                     (unsigned long long)hctrl->sum_cav, (unsigned long long)hctrl->sum_walk);
       if (add_grow_times(1) != GDP_OK) return GDP_ERR_CUDA;
       if (hctrl->err) { status = hctrl->err; break; }
       if (hctrl->grow) {   // deferred insertions are retried in the next iterations

@@ -48,6 +48,22 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
 
 __device__ __forceinline__ void set_err(Ctrl* C, int code) { atomicCAS(&C->err, 0, code); }
 
+// Index checks of a checking build (-DGDP_CHECKS) on the growth and insertion
+// paths: an index outside its array is recorded (the first failing site's
+// code in ctrl->dbg, GDP_ERR_INTERNAL) and replaced by 0, so that the access
+// stays in bounds.  A plain build compiles them away.
+#ifdef GDP_CHECKS
+__device__ __forceinline__ long long cidx_(Ctrl* C, long long x, long long lim, int site) {
+  if (x >= 0 && x < lim) return x;
+  atomicCAS(&C->dbg, 0, site);
+  set_err(C, S_INTERNAL);
+  return 0;
+}
+#define CI(x, lim, site) cidx_(P.ctrl, (long long)(x), (long long)(lim), (site))
+#else
+#define CI(x, lim, site) (x)
+#endif
+
 __device__ __forceinline__ int block_sum(int v, int* sm) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -109,6 +125,45 @@ __device__ __forceinline__ Chunk chunk_of(int n) {
 }
 
 __device__ __forceinline__ P2 pt(const Pool& P, int v) { return P2{P.V[v], P.Vf[v]}; }
+
+// Predicates on mesh vertices given by id.  The FP32 two-float filter reads
+// only Vf; when it cannot decide, the FP64 coordinates are read and the FP64
+// and exact stages run in separate, non-inlined functions, so that the common
+// path neither loads nor holds FP64 coordinates.
+static __device__ __noinline__ int orient_v64(const double2* V, int a, int b, double cx, double cy) {
+  return orient(V[a], V[b], make_double2(cx, cy));
+}
+static __device__ __noinline__ int incircle_v64(const double2* V, int a, int b, int c, double dx, double dy) {
+  return incircle(V[a], V[b], V[c], make_double2(dx, dy));
+}
+// circle (p, u, v) against the point of candidate j (Delaunay dependence)
+static __device__ __noinline__ int incircle_dep64(const double2* V, const double2* cpt, double px, double py,
+                                                  int u, int v, int j) {
+  return incircle(make_double2(px, py), V[u], V[v], cpt[j]);
+}
+__device__ __forceinline__ int orient_ids(const Pool& P, int a, int b, const P2& c) {
+  a = CI(a, P.n_verts, 127);
+  b = CI(b, P.n_verts, 127);
+  const int s = orient_f32(P.Vf[a], P.Vf[b], c.f);
+  GDP_DIAG_ADD(9);
+  if (!s) GDP_DIAG_ADD(12);
+  return s ? s : orient_v64(P.V, a, b, c.d.x, c.d.y);
+}
+__device__ __forceinline__ int incircle_ids(const Pool& P, int a, int b, int c, const P2& d) {
+  a = CI(a, P.n_verts, 105);
+  b = CI(b, P.n_verts, 105);
+  c = CI(c, P.n_verts, 105);
+  const int s = incircle_f32(P.Vf[a], P.Vf[b], P.Vf[c], d.f);
+  GDP_DIAG_ADD(10);
+  if (!s) GDP_DIAG_ADD(13);
+  return s ? s : incircle_v64(P.V, a, b, c, d.d.x, d.d.y);
+}
+__device__ __forceinline__ int incircle_dep(const Pool& P, const P2& p, int u, int v, int j) {
+  const int s = incircle_f32(p.f, P.Vf[u], P.Vf[v], P.c_ptf[j]);
+  GDP_DIAG_ADD(10);
+  if (!s) GDP_DIAG_ADD(13);
+  return s ? s : incircle_dep64(P.V, P.c_pt, p.d.x, p.d.y, u, v, j);
+}
 // the two-float copy of p - org (see the FP32 filter stage of the predicates)
 __device__ __forceinline__ float4 to_f(double2 p, double2 org) {
   const double tx = __dsub_rn(p.x, org.x), ty = __dsub_rn(p.y, org.y);
@@ -532,13 +587,13 @@ __device__ int walk(const Pool& P, int t, const P2& p, bool stop_cons, int& bt, 
 #ifdef GDP_DIAG
     if (s > 0 && (s & 7) == 0) atomicMax(&g_diag[5], (unsigned long long)s);
 #endif
-    const int4 T4 = P.T[t];
-    const int4 N4 = P.N[t];
+    const int4 T4 = P.T[CI(t, P.n_slots, 122)];
+    const int4 N4 = P.N[CI(t, P.n_slots, 122)];
     int next = -1, nfrom = -1, blk = -1;
     for (int e = 0; e < 3 && next < 0; ++e) {
       const int nb = comp(N4, e);
       if (nb >= 0 && (nb >> 2) == from) continue;   // p is on this side of the entry edge
-      if (orient(pt(P, comp(T4, mod3(e + 1))), pt(P, comp(T4, mod3(e + 2))), p) < 0) {
+      if (orient_ids(P, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), p) < 0) {
         if ((stop_cons && ((T4.w >> e) & 1)) || nb < 0) {
           if (blk < 0) blk = e;
         } else {
@@ -626,8 +681,8 @@ __device__ int grow(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1,
   if (t1 >= 0) cav_add(B, k, t1);
   for (int q = 0; q < k; ++q) {
     const int t = B.cav[q];
-    const int4 T4 = P.T[t];
-    const int4 N4 = P.N[t];
+    const int4 T4 = P.T[CI(t, P.n_slots, 131)];
+    const int4 N4 = P.N[CI(t, P.n_slots, 131)];
     for (int e = 0; e < 3; ++e) {
       const int ref = comp(N4, e);
       const int cons = (T4.w >> e) & 1;
@@ -636,9 +691,9 @@ __device__ int grow(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1,
       const int u = comp(T4, mod3(e + 1)), v = comp(T4, mod3(e + 2));
       bool inside = false;
       if (!cons && ref >= 0) {
-        const int4 Tn = P.T[ref >> 2];
-        inside = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
-      } else if (cons && conv && encroaches(pt(P, u), pt(P, v), p, lens)) {
+        const int4 Tn = P.T[CI(ref >> 2, P.n_slots, 132)];
+        inside = incircle_ids(P, Tn.x, Tn.y, Tn.z, p) > 0;
+      } else if (cons && conv && encroaches(pt(P, CI(u, P.n_verts, 133)), pt(P, CI(v, P.n_verts, 133)), p, lens)) {
         ct = t;
         ce = e;
         return G_CONV;
@@ -669,27 +724,30 @@ __device__ __forceinline__ bool is_split_edge(const int4& rec, int2 sub) {
 // Returns G_OVF when the cavity does not fit B, else G_OK (c_state tells
 // whether the candidate was grown).
 // work of the grown candidates, summed per thread (see k_grow)
+// (32-bit per thread: a thread's share of one launch stays far below 2^32;
+// the warp sums are taken in 64 bits)
 struct GrowAcc {
-  unsigned long long grown = 0, cav = 0, bnd = 0, walk = 0;
+  unsigned grown = 0, cav = 0, bnd = 0, walk = 0;
 };
 
-__device__ __forceinline__ void acc_flush(const Pool& P, GrowAcc& a, int timed = 0) {
+__device__ __forceinline__ void acc_flush(const Pool& P, const GrowAcc& a, int timed = 0) {
+  unsigned long long grown = a.grown, cav = a.cav, bnd = a.bnd, walk = a.walk;
   for (int o = 16; o; o >>= 1) {
-    a.grown += __shfl_xor_sync(0xffffffffu, a.grown, o);
-    a.cav += __shfl_xor_sync(0xffffffffu, a.cav, o);
-    a.bnd += __shfl_xor_sync(0xffffffffu, a.bnd, o);
-    a.walk += __shfl_xor_sync(0xffffffffu, a.walk, o);
+    grown += __shfl_xor_sync(0xffffffffu, grown, o);
+    cav += __shfl_xor_sync(0xffffffffu, cav, o);
+    bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+    walk += __shfl_xor_sync(0xffffffffu, walk, o);
   }
-  if ((threadIdx.x & 31) == 0 && a.grown + a.walk) {
-    atomicAdd(&P.ctrl->n_grown, a.grown);
-    atomicAdd(&P.ctrl->sum_cav, a.cav);
-    atomicAdd(&P.ctrl->sum_bnd, a.bnd);
-    atomicAdd(&P.ctrl->sum_walk, a.walk);
+  if ((threadIdx.x & 31) == 0 && grown + walk) {
+    atomicAdd(&P.ctrl->n_grown, grown);
+    atomicAdd(&P.ctrl->sum_cav, cav);
+    atomicAdd(&P.ctrl->sum_bnd, bnd);
+    atomicAdd(&P.ctrl->sum_walk, walk);
     if (timed) {
-      atomicAdd(&P.ctrl->t_grown, a.grown);
-      atomicAdd(&P.ctrl->t_cav, a.cav);
-      atomicAdd(&P.ctrl->t_bnd, a.bnd);
-      atomicAdd(&P.ctrl->t_walk, a.walk);
+      atomicAdd(&P.ctrl->t_grown, grown);
+      atomicAdd(&P.ctrl->t_cav, cav);
+      atomicAdd(&P.ctrl->t_bnd, bnd);
+      atomicAdd(&P.ctrl->t_walk, walk);
     }
   }
 }
@@ -707,8 +765,28 @@ struct CandSetup {
   bool conv;
 };
 
+// the predicates of incircle_ids / orient_ids with the candidate's point
+// read from its CandSetup slot (the FP64 point only on the fallback path)
+__device__ __forceinline__ int incircle_cs(const Pool& P, int a, int b, int c, const CandSetup* ws) {
+  a = CI(a, P.n_verts, 105);
+  b = CI(b, P.n_verts, 105);
+  c = CI(c, P.n_verts, 105);
+  const int s = incircle_f32(P.Vf[a], P.Vf[b], P.Vf[c], ws->pf);
+  GDP_DIAG_ADD(10);
+  if (!s) GDP_DIAG_ADD(13);
+  return s ? s : incircle_v64(P.V, a, b, c, ws->p.x, ws->p.y);
+}
+__device__ __forceinline__ int orient_cs(const Pool& P, int a, int b, const CandSetup* ws) {
+  a = CI(a, P.n_verts, 127);
+  b = CI(b, P.n_verts, 127);
+  const int s = orient_f32(P.Vf[a], P.Vf[b], ws->pf);
+  GDP_DIAG_ADD(9);
+  if (!s) GDP_DIAG_ADD(12);
+  return s ? s : orient_v64(P.V, a, b, ws->p.x, ws->p.y);
+}
+
 template <int MODE>
-__device__ bool cand_setup(const Pool& P, int i, CandSetup& s, GrowAcc& acc) {
+__device__ __noinline__ bool cand_setup(const Pool& P, int i, CandSetup& s, GrowAcc& acc) {
   P.c_ncav[i] = 0;
   P.c_nbnd[i] = 0;
   P.c_state[i] = C_FAIL;
@@ -719,18 +797,19 @@ __device__ bool cand_setup(const Pool& P, int i, CandSetup& s, GrowAcc& acc) {
   s.conv = false;
   s.sub = make_int2(-1, -1);
   if (MODE == 1) {
-    s.vid = elem;
-    s.t0 = P.c_loc[i];
+    s.vid = CI(elem, P.n_verts, 126);
+    s.t0 = CI(P.c_loc[i], P.n_slots, 125);
     s.m = P.T[s.t0].w >> 4;
     s.p = P.V[s.vid];
     s.key = ((unsigned long long)insert_prio(P.mi[s.m], s.vid) << 32) | (unsigned)i;
   } else {
-    const int t = elem >> 2, k = elem & 3;
+    const int t = CI(elem >> 2, P.n_slots, 120), k = elem & 3;
     const int4 T4 = P.T[t];
     s.m = T4.w >> 4;
     const MeshInfo& M = P.mi[s.m];
     if (k == 3) {
-      const TriTerms tt = tri_terms(P.V[T4.x], P.V[T4.y], P.V[T4.z]);
+      const TriTerms tt = tri_terms(P.V[CI(T4.x, P.n_verts, 121)], P.V[CI(T4.y, P.n_verts, 121)],
+                                    P.V[CI(T4.z, P.n_verts, 121)]);
       s.p = circumcenter(tt);
       s.key = ((unsigned long long)measure_bits(fabs(tt.cr)) << 32) | (unsigned)i;
       int bt = -1, be = -1;
@@ -744,8 +823,8 @@ __device__ bool cand_setup(const Pool& P, int i, CandSetup& s, GrowAcc& acc) {
       }
       if (r == -1) {
         // the walk meets a subsegment: split it instead (Sec. 4.3)
-        const int4 B4 = P.T[bt];
-        const int u = comp(B4, mod3(be + 1)), v = comp(B4, mod3(be + 2));
+        const int4 B4 = P.T[CI(bt, P.n_slots, 123)];
+        const int u = CI(comp(B4, mod3(be + 1)), P.n_verts, 124), v = CI(comp(B4, mod3(be + 2)), P.n_verts, 124);
         s.p = split_point(P, M, u, v);
         s.key = KEY_MID | ((unsigned long long)measure_bits(seg_measure(P.V[u], P.V[v])) << 32) |
                 (unsigned)i;
@@ -776,6 +855,7 @@ __device__ bool cand_setup(const Pool& P, int i, CandSetup& s, GrowAcc& acc) {
 // the circumcentre encroaches subsegment edge ce of triangle ct on its
 // cavity boundary: that subsegment's split point replaces it (Sec. 4.2)
 __device__ void cand_conv(const Pool& P, int i, CandSetup& s, int ct, int ce) {
+  ct = CI(ct, P.n_slots, 128);
   const int4 B4 = P.T[ct];
   const int u = comp(B4, mod3(ce + 1)), v = comp(B4, mod3(ce + 2));
   s.p = split_point(P, P.mi[s.m], u, v);
@@ -831,7 +911,7 @@ __device__ int grow_cand(const Pool& P, int i, const CavBuf& B, GrowAcc& acc) {
   for (int r = 0; r < nb && ok; ++r) {
     const int4 rec = B.bnd[r];
     if (is_split_edge(rec, s.sub)) continue;
-    if (orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) ok = false;
+    if (orient_ids(P, rec.x, rec.y, pp) <= 0) ok = false;
   }
   if (!ok) return G_OK;
   for (int j = 0; j < nc; ++j) atomicMax(&P.mark[B.cav[j]], s.key);
@@ -870,12 +950,15 @@ struct Group {
   __device__ __forceinline__ bool any(bool x) const { return ballot(x) != 0u; }
 };
 
+// The candidate (point, start triangles, conv) is read from its shared slot
+// ws where it is used rather than held in registers for the whole growth.
 template <int W>
-__device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, int t0, int t1,
-                     bool conv, bool lens, int& nc, int& nb, int& ct, int& ce) {
+__device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const CandSetup* ws, bool lens, int& nc,
+                     int& nb, int& ct, int& ce) {
   const Group<W> g;
   const int lane = g.gl;
   const unsigned lt_mask = (1u << lane) - 1u;
+  const int t0 = ws->t0, t1 = ws->t1;
   int k = 1, b = 0;
   if (lane == 0) {
     wc[0] = t0;
@@ -895,18 +978,21 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
     for (int base = 3 * lb; base < 3 * le; base += W) {
       const int slot = base + lane;
       const bool act = slot < 3 * le;
-      int e = 0, ref = -1, cons = 0, u = -1, v = -1, tn = -1, t = -1;
+      // the tuple as its boundary record would be: u, v, outside ref,
+      // subsegment bit << 31 | t << 2 | e
+      int tn = -1;
+      bool cons = false;
+      int4 rec = make_int4(-1, -1, -1, 0);
       if (act) {
         const int q = slot / 3;
-        e = slot - 3 * q;
-        t = wc[q];
+        const int e = slot - 3 * q;
+        const int t = wc[q];
         const int4 T4 = P.T[t];
-        const int4 N4 = P.N[t];
-        ref = comp(N4, e);
+        const int ref = comp(P.N[t], e);
         cons = (T4.w >> e) & 1;
-        u = comp(T4, mod3(e + 1));
-        v = comp(T4, mod3(e + 2));
         tn = ref >= 0 ? ref >> 2 : -1;
+        rec = make_int4(comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), ref,
+                        (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
       }
       bool member = false;
       for (int j = 0; j < k; ++j) member |= (wc[j] == tn);
@@ -917,7 +1003,7 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
       bool in = false;
       if (test && lane == leader) {
         const int4 Tn = P.T[tn];
-        in = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
+        in = incircle_cs(P, Tn.x, Tn.y, Tn.z, ws) > 0;
       }
       in = g.shfl(in, leader);
       const unsigned adders = g.ballot(test && lane == leader && in);
@@ -928,7 +1014,7 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
       int ev = 0;
       if (act && !member) {
         if (test) ev = (lane == leader && in) ? 1 : (in ? 0 : 2);
-        else if (cons && conv && encroaches(pt(P, u), pt(P, v), p, lens)) ev = 3;
+        else if (cons && ws->conv && encroaches(pt(P, rec.x), pt(P, rec.y), P2{ws->p, ws->pf}, lens)) ev = 3;
         else ev = 2;
       }
       const unsigned am = g.ballot(ev == 1);
@@ -939,8 +1025,9 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
       const int first_conv = cm ? __ffs(cm) - 1 : W;
       const int first_ovf = ovf ? __ffs(ovf) - 1 : W;
       if (first_conv < first_ovf) {
-        ct = g.shfl(t, first_conv);
-        ce = g.shfl(e, first_conv);
+        const int te = g.shfl(rec.w & 0x7fffffff, first_conv);
+        ct = te >> 2;
+        ce = te & 3;
         return G_CONV;
       }
       if (first_ovf < W) return G_OVF;
@@ -948,7 +1035,7 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
         wc[k + ar] = tn;
         cav[k + ar] = tn;
       } else if (ev == 2) {
-        bnd[b + rr] = make_int4(u, v, ref, (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
+        bnd[b + rr] = rec;
       }
       k += __popc(am);
       b += __popc(rm);
@@ -964,6 +1051,40 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const P2& p, i
 // One candidate grown by the group (all W lanes call it): splitting point,
 // walk and key by the group's first lane, then the cavity, the visibility
 // check of its boundary and the marks.  ws: the group's CandSetup slot.
+// The growth of candidate i whose setup is in ws (all W lanes call it): the
+// cavity, the visibility check of its boundary and the marks.
+template <int MODE, int W>
+__device__ __forceinline__ void group_grow_body(const Pool& P, int i, int* wc, CandSetup* ws, GrowAcc& acc) {
+  const Group<W> g;
+  int* cav = P.c_cav + (size_t)i * CMAX;
+  int4* bnd = P.c_bnd + (size_t)i * BMAX;
+  int nc = 0, nb = 0, ct = -1, ce = -1;
+  const bool lens = P.mi[ws->m].lens != 0;
+  int r = wgrow<W>(P, cav, bnd, wc, ws, lens, nc, nb, ct, ce);
+  if (r == G_CONV) {
+    if (g.gl == 0) cand_conv(P, i, *ws, ct, ce);   // clears ws->conv
+    g.sync();
+    r = wgrow<W>(P, cav, bnd, wc, ws, lens, nc, nb, ct, ce);
+  }
+  if (r == G_OVF) {
+    if (g.gl == 0) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+    g.sync();
+    return;
+  }
+  g.sync();
+  const int2 sub = ws->sub;
+  bool bad = false;
+  for (int q = g.gl; q < nb; q += W) {
+    const int4 rec = bnd[q];
+    if (!is_split_edge(rec, sub) && orient_cs(P, rec.x, rec.y, ws) <= 0) bad = true;
+  }
+  if (g.any(bad)) return;
+  const unsigned long long key = ws->key;
+  for (int j = g.gl; j < nc; j += W) atomicMax(&P.mark[cav[j]], key);
+  if (g.gl == 0) cand_record(P, i, *ws, nc, nb, acc);
+  g.sync();
+}
+
 template <int MODE, int W>
 __device__ __forceinline__ void group_grow_cand(const Pool& P, int i, int* wc, CandSetup* ws, GrowAcc& acc) {
   const Group<W> g;
@@ -974,34 +1095,7 @@ __device__ __forceinline__ void group_grow_cand(const Pool& P, int i, int* wc, C
   }
   g.sync();
   if (!g.shfl(ok, 0)) return;
-  CandSetup s = *ws;
-  int* cav = P.c_cav + (size_t)i * CMAX;
-  int4* bnd = P.c_bnd + (size_t)i * BMAX;
-  int nc = 0, nb = 0, ct = -1, ce = -1;
-  const bool lens = P.mi[s.m].lens != 0;
-  int r = wgrow<W>(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, s.conv, lens, nc, nb, ct, ce);
-  if (r == G_CONV) {
-    if (g.gl == 0) cand_conv(P, i, *ws, ct, ce);
-    g.sync();
-    s = *ws;
-    r = wgrow<W>(P, cav, bnd, wc, P2{s.p, s.pf}, s.t0, s.t1, false, lens, nc, nb, ct, ce);
-  }
-  if (r == G_OVF) {
-    if (g.gl == 0) atomicMin(&P.lane[i & (LANES_A - 1)], i);
-    g.sync();
-    return;
-  }
-  g.sync();
-  const P2 pp{s.p, s.pf};
-  bool bad = false;
-  for (int q = g.gl; q < nb; q += W) {
-    const int4 rec = bnd[q];
-    if (!is_split_edge(rec, s.sub) && orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) bad = true;
-  }
-  if (g.any(bad)) return;
-  for (int j = g.gl; j < nc; j += W) atomicMax(&P.mark[cav[j]], s.key);
-  if (g.gl == 0) cand_record(P, i, s, nc, nb, acc);
-  g.sync();
+  group_grow_body<MODE, W>(P, i, wc, ws, acc);
 }
 
 // Cavity growth of the candidates in their own slots of CMAX triangles
@@ -1027,10 +1121,11 @@ __global__ void __maxnreg__(128) k_grow_w(Pool P, int timed) {
   if (MODE == 0) acc_flush(P, acc, timed);
 }
 
-// The same above P.warp_max candidates, where the launch is throughput-bound:
-// a group of GROW_GROUP lanes per candidate (four candidates per warp), so that
-// a level's few tuples keep most lanes busy and the lanes of a warp run the
-// same instruction stream.  The grid covers the candidates in place.
+// The same above P.warp_max candidates, where the launch is throughput-bound.
+// A warp takes 32 candidates at a time: first their setups, one per lane (the
+// FP64 circumcentres and keys and the walks, with every lane busy), then their
+// cavities, a group of GROW_GROUP lanes per candidate (four at a time), so
+// that a level's few tuples keep most lanes busy.
 constexpr int GROW_GROUP = 8;
 #ifndef GDP_GROW_G_REGS
 #define GDP_GROW_G_REGS 64
@@ -1038,17 +1133,32 @@ constexpr int GROW_GROUP = 8;
 template <int MODE>
 __global__ void __maxnreg__(GDP_GROW_G_REGS) k_grow_g(Pool P, int timed) {
   constexpr int GPB = 128 / GROW_GROUP;   // groups per 128-thread block
+  constexpr int GPW = 32 / GROW_GROUP;    // groups per warp
   __shared__ int wcs[GPB][32];
-  __shared__ CandSetup ws[GPB];
+  __shared__ CandSetup ws[128];           // the setups of a round, one per thread
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gib = threadIdx.x / GROW_GROUP;
-  const int gg = (blockIdx.x * blockDim.x + threadIdx.x) / GROW_GROUP;
-  const int ng = (gridDim.x * blockDim.x) / GROW_GROUP;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const int n = P.ctrl->n_cand;
   if (n <= P.warp_max) return;   // k_grow_w's case
   GrowAcc acc;
-  for (int i0 = gg - (gg & (32 / GROW_GROUP - 1)); i0 < n; i0 += ng) {   // whole warps
-    const int i = i0 + (gg & (32 / GROW_GROUP - 1));
-    if (i < n) group_grow_cand<MODE, GROW_GROUP>(P, i, wcs[gib], &ws[gib], acc);
+  for (int i0 = gw * 32; i0 < n; i0 += nw * 32) {
+    // the setups of the warp's 32 candidates, one per lane, so that the FP64
+    // circumcentre and key arithmetic and the walks keep the lanes busy
+    const int i = i0 + lane;
+    bool ok = false;
+    if (i < n) {
+      P.c_big[CI(i, P.cap_cand, 113)] = -1;
+      ok = cand_setup<MODE>(P, i, ws[threadIdx.x], acc);
+    }
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    __syncwarp();
+    // then every group grows one of them at a time
+    for (int r = 0; r < 32; r += GPW) {
+      const int j = r + lane / GROW_GROUP;
+      if ((okm >> j) & 1) group_grow_body<MODE, GROW_GROUP>(P, i0 + j, wcs[gib], &ws[wib * 32 + j], acc);
+    }
+    __syncwarp();   // the next round's setups overwrite the slots
   }
   if (MODE == 0) acc_flush(P, acc, timed);
 }
@@ -1150,7 +1260,7 @@ __device__ int wgrow_h(const Pool& P, const CavBuf& B, const P2& p, int t0, int 
       bool in = false;
       if (test && lane == leader) {
         const int4 Tn = P.T[tn];
-        in = incircle(pt(P, Tn.x), pt(P, Tn.y), pt(P, Tn.z), p) > 0;
+        in = incircle_ids(P, Tn.x, Tn.y, Tn.z, p) > 0;
       }
       in = __shfl_sync(FULL, in, leader);
       const unsigned adders = __ballot_sync(FULL, test && lane == leader && in);
@@ -1245,7 +1355,7 @@ __global__ void __maxnreg__(128) k_grow_big(Pool P, int TIER) {
     bool bad = false;
     for (int r = lane; r < nb; r += 32) {
       const int4 rec = B.bnd[r];
-      if (!is_split_edge(rec, s.sub) && orient(pt(P, rec.x), pt(P, rec.y), pp) <= 0) bad = true;
+      if (!is_split_edge(rec, s.sub) && orient_ids(P, rec.x, rec.y, pp) <= 0) bad = true;
     }
     if (__any_sync(FULL, bad)) continue;
     for (int j = lane; j < nc; j += 32) atomicMax(&P.mark[B.cav[j]], s.key);
@@ -1332,7 +1442,7 @@ __global__ void __launch_bounds__(BS) k_depend(Pool P) {
         if (!mo) continue;
         const int j = (int)(unsigned)(mo & 0xffffffffull);
         if (j == i || j >= n || P.c_state[j] != C_SURV) continue;
-        if (incircle(p, pt(P, rec.x), pt(P, rec.y), P2{P.c_pt[j], P.c_ptf[j]}) > 0 &&
+        if (incircle_dep(P, p, rec.x, rec.y, j) > 0 &&
             key < P.c_key[j])
           fin = false;
       }
@@ -1558,6 +1668,7 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
       if (P.c_final[i] && ok) {
         base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
         vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
+        vid = CI(vid, P.n_verts, 217);
         P.c_base[i] = base;
         P.V[vid] = P.c_pt[i];
         P.Vf[vid] = P.c_ptf[i];
@@ -1567,7 +1678,7 @@ __global__ void __launch_bounds__(BS) k_insert_t(Pool P) {
         if (!big) {
           const int4* bnd = P.c_bnd + (size_t)i * BMAX;
           const int* cav = P.c_cav + (size_t)i * CMAX;
-          const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
+          const int nc = CI(P.c_ncav[i], CMAX + 1, 211), nb = CI(P.c_nbnd[i], BMAX + 1, 211);
           const int2 sub = P.c_sub[i];
           const bool is_mid = sub.x >= 0;
           int j = 0;
@@ -1746,6 +1857,7 @@ __global__ void __launch_bounds__(128) k_insert_g(Pool P) {
         vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
         if (g.gl == 0) {
           P.c_base[i] = base;
+          vid = CI(vid, P.n_verts, 207);
           P.V[vid] = P.c_pt[i];
           P.Vf[vid] = P.c_ptf[i];
           P.vseg[vid] = P.c_vseg[i];
@@ -1756,7 +1868,7 @@ __global__ void __launch_bounds__(128) k_insert_g(Pool P) {
         if (!big) {
           const int4* bnd = P.c_bnd + (size_t)i * BMAX;
           const int* cav = P.c_cav + (size_t)i * CMAX;
-          const int nc = P.c_ncav[i], nb = P.c_nbnd[i];
+          const int nc = CI(P.c_ncav[i], CMAX + 1, 201), nb = CI(P.c_nbnd[i], BMAX + 1, 201);
           const int2 sub = P.c_sub[i];
           const bool is_mid = sub.x >= 0;
           int4 rec[R];
@@ -1769,7 +1881,7 @@ __global__ void __launch_bounds__(128) k_insert_g(Pool P) {
             keep[h] = r < nb && !is_split_edge(rec[h], sub);
             const unsigned km = g.ballot(keep[h]);
             const int j = done + __popc(km & lt_mask);
-            slot[h] = j < nc ? cav[j] : base + (j - nc);
+            slot[h] = j < nc ? cav[CI(j, CMAX, 202)] : base + (j - nc);
             done += __popc(km);
           }
           // fan neighbours: the record starting where mine ends (edge 2) and
@@ -1800,16 +1912,16 @@ __global__ void __launch_bounds__(128) k_insert_g(Pool P) {
             if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
             int n0 = rec[h].z;
             if (n0 >= 0) {
-              if (replaced(P, n0, n)) n0 = -1;   // linked by k_link
-              else *comp_ptr(&P.N[n0 >> 2], n0 & 3) = s << 2;
+              if (replaced(P, CI(n0, 4ll * P.n_slots, 203), n)) n0 = -1;   // linked by k_link
+              else *comp_ptr(&P.N[CI(n0 >> 2, P.n_slots, 203)], n0 & 3) = s << 2;
             }
-            P.T[s] = make_int4(vid, u, v, (m << 4) | cb);
-            P.N[s] = make_int4(n0, n1[h], n2[h], 0);
-            P.newref[rec[h].w & 0x7fffffff] = s << 2;
-            new_tri_code<MODE>(P, s);
-            P.vtri[u] = s;
-            P.vtri[v] = s;
-            P.vtri[vid] = s;
+            P.T[CI(s, P.n_slots, 204)] = make_int4(vid, u, v, (m << 4) | cb);
+            P.N[CI(s, P.n_slots, 204)] = make_int4(n0, n1[h], n2[h], 0);
+            P.newref[CI(rec[h].w & 0x7fffffff, 4ll * P.n_slots, 205)] = s << 2;
+            new_tri_code<MODE>(P, CI(s, P.n_slots, 204));
+            P.vtri[CI(u, P.n_verts, 206)] = s;
+            P.vtri[CI(v, P.n_verts, 206)] = s;
+            P.vtri[CI(vid, P.n_verts, 206)] = s;
           }
         }
       }
