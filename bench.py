@@ -385,7 +385,10 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region"""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+    The sampler is started before the warm-up steps and the timed steps wait
+    for its first sample: starting nvidia-smi initialises NVML, which can stall
+    the CUDA calls of other processes for tens of milliseconds."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -410,7 +413,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append([time.perf_counter()] + [x.strip() for x in line.split(",")])
+
+    def wait_first(self, timeout=15.0):
+        t0 = time.perf_counter()
+        while self.proc and not self.rows and time.perf_counter() - t0 < timeout:
+            time.sleep(0.05)
 
     def __exit__(self, *a):
         if self.proc:
@@ -420,18 +428,25 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+    def summary(self, t_lo=None, t_hi=None):
+        """the samples taken in [t_lo, t_hi] (plus the last one before t_lo,
+        the state when the window opened); all samples without a window"""
+        rows = self.rows
+        if t_lo is not None:
+            before = [r for r in rows if r[0] < t_lo]
+            rows = before[-1:] + [r for r in rows if t_lo <= r[0] <= t_hi]
+        rows = [r[1:] for r in rows]
+        sm = [float(r[1]) for r in rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             for k, n in enumerate(names):
                 if len(r) > 5 + k and r[5 + k].lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(self.rows)}
+                "samples": len(rows)}
 
 
 def load_workload(name):
@@ -571,10 +586,12 @@ def main():
         s = m.refine(args.B, flags=flags, **refine_kwargs(args))
         return m, s
 
+    clk = ClockSampler(local).__enter__()   # started early: see ClockSampler
     warmup = max(args.warmup, 3)
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
+    clk.wait_first()
 
     def barrier():
         if world > 1:
@@ -585,20 +602,23 @@ def main():
     times, steiner, launches = [], 0, 0
     stats = None
     barrier()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)              # L2 flush, outside the timed region
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            m, stats = step()
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1))
-            steiner += stats["n_steiner"]
-            launches += stats["launches"]
-            del m
-        barrier()
+    t_lo = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)              # L2 flush, outside the timed region
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m, stats = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        steiner += stats["n_steiner"]
+        launches += stats["launches"]
+        del m
+    barrier()
+    t_hi = time.perf_counter()
+    clk.__exit__()
+    clocks = clk.summary(t_lo, t_hi)
     tot_ms, steiner_all = replica_totals(sum(times), steiner, world, dev)
     value = steiner_all / (tot_ms / 1000.0)
 
@@ -718,7 +738,8 @@ def main():
             "steiner_per_step": stats["n_steiner"], "iterations": stats["iterations"],
             "cdt_rounds": stats["cdt_rounds"],
             "refine_only_steiner_per_s": stats["n_steiner"] / (stats["refine_ms"] / 1000.0),
-            "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clk.summary(),
+            "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clocks,
+            "step_ms": [round(t, 3) for t in times],
             "flipflop": flipflop,
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kt.items(), key=lambda kv: -kv[1][0])}}
     if not args.no_cpu_baseline:

@@ -138,16 +138,21 @@ __device__ __forceinline__ uint32_t pick_measure(const Pool& P, const MeshInfo& 
 
 // split: points on an edge of their triangle take no part in the pick (the
 // split rounds insert only points strictly inside a triangle)
-__global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int stop_cons, int split) {
+// resident blocks per SM the register allocation of k_cdt_locate aims at (the
+// walks are latency-bound: more resident warps hide more of it)
+#ifndef GDP_LOCATE_BLOCKS
+#define GDP_LOCATE_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(BS, GDP_LOCATE_BLOCKS) k_cdt_locate(Pool P, int stop_cons, int split) {
   const int n = P.ctrl->n_pts;
   const int round = P.ctrl->round;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (int k = gt; k < n; k += gs) {
     const int v = P.pts[k];
-    const double2 p = P.V[v];
+    const P2 pv = pt(P, v);
     int bt, be;
     int steps = 0;
-    const int t = walk(P, P.loc[v], pt(P, v), false, bt, be, steps);
+    const int t = walk(P, P.loc[v], pv, false, bt, be, steps);
     if (t < 0) {
       set_err(P.ctrl, t == -2 ? S_WALK : S_INTERNAL);
       continue;
@@ -155,16 +160,22 @@ __global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int stop_cons, int sp
     P.loc[v] = t;
     const int4 T4 = P.T[t];
     const int m = T4.w >> 4;
+    // a duplicate of a vertex of its triangle: equal points have equal
+    // two-float copies (the walk has just read them), so the FP64
+    // coordinates are compared only when those match
     bool dup = false;
     for (int e = 0; e < 3; ++e) {
-      const double2 q = P.V[comp(T4, e)];
-      dup |= (q.x == p.x && q.y == p.y);
+      const int w = comp(T4, e);
+      const float4 qf = P.Vf[w];
+      if (qf.x == pv.f.x && qf.y == pv.f.y && qf.z == pv.f.z && qf.w == pv.f.w) {
+        const double2 q = P.V[w];
+        dup |= (q.x == pv.d.x && q.y == pv.d.y);
+      }
     }
     if (stop_cons) {
       // inserted points must not lie on a subsegment
       for (int e = 0; e < 3; ++e)
-        if (((T4.w >> e) & 1) &&
-            orient(pt(P, comp(T4, mod3(e + 1))), pt(P, comp(T4, mod3(e + 2))), pt(P, v)) == 0)
+        if (((T4.w >> e) & 1) && orient_ids(P, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), pv) == 0)
           dup = true;
     }
     if (dup) {
@@ -173,10 +184,8 @@ __global__ void __launch_bounds__(BS) k_cdt_locate(Pool P, int stop_cons, int sp
       continue;
     }
     if (split) {
-      const P2 q = pt(P, v);
       bool edge = false;
-      for (int e = 0; e < 3; ++e)
-        edge |= orient(pt(P, comp(T4, mod3(e + 1))), pt(P, comp(T4, mod3(e + 2))), q) == 0;
+      for (int e = 0; e < 3; ++e) edge |= orient_ids(P, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), pv) == 0;
       if (edge) continue;
     }
     const unsigned long long key = ((unsigned long long)round << 52) |

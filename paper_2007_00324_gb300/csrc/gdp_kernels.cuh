@@ -1126,7 +1126,11 @@ __global__ void __maxnreg__(128) k_grow_w(Pool P, int timed) {
 // FP64 circumcentres and keys and the walks, with every lane busy), then their
 // cavities, a group of GROW_GROUP lanes per candidate (four at a time), so
 // that a level's few tuples keep most lanes busy.
-constexpr int GROW_GROUP = 8;
+#ifndef GDP_GROW_GROUP_W
+#define GDP_GROW_GROUP_W 8
+#endif
+constexpr int GROW_GROUP = GDP_GROW_GROUP_W;   // lanes per candidate: 4, 8 or 16
+static_assert(GROW_GROUP == 4 || GROW_GROUP == 8 || GROW_GROUP == 16, "a group is 4, 8 or 16 lanes");
 #ifndef GDP_GROW_G_REGS
 #define GDP_GROW_G_REGS 64
 #endif
