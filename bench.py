@@ -56,12 +56,15 @@ REF_SAMPLE = {"n_uniform": 125_000, "n_gauss": 75_000, "n_circle": 50_000, "n_se
 #   coordinates, (2k + 2) * 60 B, and each cavity triangle gets an 8 B mark
 #   written and read back, 16 k B:  120 B per grown candidate + 136 B per cavity
 #   triangle;
-#   per point-location walk step: one triangle and its neighbours, 76 B.
-GROW_BYTES = {"candidate": 120, "cavity_tri": 136, "walk_step": 76}
+#   per point-location walk step: one triangle and its neighbours, 76 B;
+#   per candidate set up by the pre-pass (k_pre): its own triangle, 12 B of ids
+#   + 48 B of coordinates, and its key put on its start triangles and their
+#   first ring (4 marks of 8 B on average), 92 B.
+GROW_BYTES = {"candidate": 120, "cavity_tri": 136, "walk_step": 76, "setup": 92}
 GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
 # the kernels of one refinement iteration (launched once per iteration, so an ncu
 # launch list counts them in every step and their shares compare directly)
-GROW_KERNELS = ("k_grow_w<0>", "k_grow_g<0>", "k_grow_t<0>")
+GROW_KERNELS = ("k_pre", "k_grow_w<0>", "k_grow_g<0>", "k_grow_t<0>")
 REFINE_KERNELS = ("k_scan_eval", "k_scan_count", "k_scan_write") + GROW_KERNELS + (
     "k_grow_big<0>", "k_survive", "k_depend", "k_offsets", "k_insert_w<0>", "k_insert_g<0>", "k_insert_t<0>",
     "k_link<0>")
@@ -72,7 +75,7 @@ COUNTERS_FILE = os.path.join(ROOT, "profiles", "cavity_growth_paper_shaped_count
 
 def grow_bytes(st) -> float:
     return (GROW_BYTES["candidate"] * st["grown"] + GROW_BYTES["cavity_tri"] * st["cavity_tris"] +
-            GROW_BYTES["walk_step"] * st["walk_steps"])
+            GROW_BYTES["walk_step"] * st["walk_steps"] + GROW_BYTES["setup"] * st.get("setups", 0))
 
 
 def grow_source_hash() -> str:
@@ -647,7 +650,7 @@ def main():
     # bracketed by CUDA events inside the graph (the events stall the graph,
     # which is why the timed steps above run without them)
     grow = {"grow_ms": 0.0, "grow_launches": 0, "timed_grown": 0, "timed_walk_steps": 0,
-            "timed_cavity_tris": 0, "timed_cavity_edges": 0}
+            "timed_cavity_tris": 0, "timed_cavity_edges": 0, "timed_setups": 0}
     for _ in range(max(1, args.roof_steps)):
         flush.fill_(1.0)
         m, rs = step(gdp.REFINE_TIME_GROW)
@@ -716,13 +719,14 @@ def main():
             "kernel": f"cavity growth: {grow_names}", "algorithmic_bytes_per_launch": by / n_l,
             "kernel_ms_per_launch": grow["grow_ms"] / n_l, "launches": grow["grow_launches"],
             "grown_candidates_per_launch": per_launch,
+            "setup_candidates_per_launch": timed["setups"] / n_l,
             "share_of_kernel_time": share / tot_k,
             "share_of_refine_kernel_time": share / max(sum(kt.get(k, (0.0, 0))[0] for k in REFINE_KERNELS), 1e-9),
             "largest_kernel": top[0],
             "peak_source": "measured (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "timed_launches": f"the first iteration of every graph replay, {args.roof_steps} instrumented steps",
             "mean_cavity_tris": timed["cavity_tris"] / max(timed["grown"], 1),
-            "mean_walk_steps": timed["walk_steps"] / max(timed["grown"], 1),
+            "mean_walk_steps": timed["walk_steps"] / max(timed["setups"], 1),
             "fp64": fp64, "l2": l2}
 
     if rank != 0:

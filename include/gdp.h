@@ -93,6 +93,11 @@ typedef struct {
     /* with GDP_REFINE_FLIPFLOP: flips, flops (point removals) and redundant
      * points removed, summed over the iterations */
     int64_t flips, flops, redundant_removed;
+    /* refinement candidates set up by the pre-pass that precedes cavity
+     * growth (splitting point, walk, first-ring marks); the ones that keep
+     * all their first-ring marks are grown.  All iterations / the timed
+     * launches. */
+    int64_t setups, timed_setups;
 } gdp_stats;
 
 /* gdp_refine_opts.flags */

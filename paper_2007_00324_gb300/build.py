@@ -9,7 +9,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgdp.so")
 SOURCES = ["gdp.cu", "gdp_noalloc.cu", "gdp_peak.cu"]
-HEADERS = ["gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh", "gdp_cdt.cuh", "gdp_server.cuh", "gdp_tune.cuh"]
+HEADERS = ["gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh", "gdp_cdt.cuh", "gdp_server.cuh", "gdp_tune.cuh",
+           "gdp_flipflop.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

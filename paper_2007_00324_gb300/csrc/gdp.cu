@@ -208,11 +208,13 @@ __global__ void k_drop_inactive(Pool P) {
     kern<<<(grid), (block), 0, (h).stream>>>(__VA_ARGS__);           \
     (h).prof_end();                                                  \
   } while (0)
-// candidate cavities: own slots, then the two spill tiers
+// candidate cavities (refinement: after the pre-pass k_pre): own slots,
+// then the two spill tiers
 // (above warp_max candidates: a group of lanes per candidate, or one thread
 // per candidate with GDP_GROW_GROUP=0)
 #define LAUNCH_GROW_PAIR(h, MODE, P, timed)                          \
   do {                                                               \
+    if (MODE == 0) LAUNCH_B(h, k_pre, (h).n_sm * 16, 128, P, timed); \
     LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P, timed);       \
     if ((h).grow_group)                                              \
       LAUNCH_B(h, k_grow_g<MODE>, (h).n_sm * 16, 128, P, timed);     \
@@ -583,6 +585,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   P.n_verts = (int)vb;
   P.cap_cand = (int)std::min<long long>(std::max<long long>(tb / 4, 65536), 1 << 23);
   P.warp_max = (int)env_double("GDP_WARP_GROW_MAX", WARP_GROW_MAX);
+  P.no_prepass = env_double("GDP_PREPASS", 1) == 0 ? 1 : 0;
   int st;
 #define AL(ptr, n, fill) \
   if ((st = alloc(&(ptr), (size_t)(n), fill)) != GDP_OK) return st;
@@ -594,6 +597,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   AL(P.T, tb, 0xff);
   AL(P.N, tb, 0xff);
   AL(P.mark, tb, 0);
+  AL(P.pmark, tb, 0);
   AL(P.newref, 4 * tb, 0xff);
   AL(P.dirty, tb, 0);
   AL(P.flag, tb, 0);
@@ -609,6 +613,7 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   AL(P.c_vseg, C, 0); AL(P.c_sub, C, 0); AL(P.c_pt, C, 0); AL(P.c_ptf, C, 0); AL(P.c_key, C, 0);
   AL(P.c_ncav, C, 0); AL(P.c_nbnd, C, 0); AL(P.c_cav, C * CMAX, 0); AL(P.c_bnd, C * BMAX, 0);
   AL(P.c_big, C, 0xff); AL(P.big_cav, BIG_ENTRIES, 0); AL(P.big_bnd, BIG_ENTRIES, 0);
+  AL(P.c_setup, C, 0); AL(P.c_pre, C * PRE_MAX, 0); AL(P.c_npre, C, 0);
   AL(P.big_hash, BIG_HASH, 0xff); AL(P.big_val, BIG_HASH, 0xff); AL(P.lane, LANES_A + LANES_B, 0x7f);
   AL(P.c_state, C, 0); AL(P.c_final, C, 0); AL(P.c_extra, C, 0); AL(P.c_offT, C, 0);
   AL(P.c_offV, C, 0); AL(P.c_base, C, 0);
@@ -917,6 +922,7 @@ int PoolHost::insert_rounds(int stop_cons, int* rounds_out, bool split) {
     if (parity) std::swap(P.pts, P.pts2);
     // the cavity rounds start from clean marks and an empty candidate list
     CK(cudaMemsetAsync(P.mark, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
+    CK(cudaMemsetAsync(P.pmark, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
     if (set_ctrl_field(offsetof(Ctrl, prev_cand), 0) != GDP_OK) return GDP_ERR_CUDA;
     if (sync_ctrl() != GDP_OK) return GDP_ERR_CUDA;
   }
@@ -1293,7 +1299,7 @@ int PoolHost::grow_meshes() {
   };
   take(&Q.V, vb, 0); take(&Q.Vf, vb, 0); take(&Q.vseg, vb, 0xff); take(&Q.vtri, vb, 0xff);
   take(&Q.apex, vb, 0); take(&Q.loc, vb, 0xff);
-  take(&Q.T, tb, 0xff); take(&Q.N, tb, 0xff); take(&Q.mark, tb, 0); take(&Q.newref, 4 * (size_t)tb, 0xff);
+  take(&Q.T, tb, 0xff); take(&Q.N, tb, 0xff); take(&Q.mark, tb, 0); take(&Q.pmark, tb, 0); take(&Q.newref, 4 * (size_t)tb, 0xff);
   take(&Q.dirty, tb, 0); take(&Q.flag, tb, 0); take(&Q.cbucket, tb, 0); take(&Q.tbest, tb, 0);
   int2* nb = nullptr;
   take(&nb, n_mesh, 0);
@@ -1322,7 +1328,7 @@ int PoolHost::grow_meshes() {
   LAUNCH(*this, k_regrow, dim3(std::min(256, (most + 1023) / 1024), std::min(n_mesh, 65535)), Q, P, nb);
   CK(cudaGetLastError());
   for (void* q : {(void*)P.V, (void*)P.Vf, (void*)P.vseg, (void*)P.vtri, (void*)P.apex, (void*)P.loc,
-                  (void*)P.T, (void*)P.N, (void*)P.mark, (void*)P.newref, (void*)P.dirty, (void*)P.flag,
+                  (void*)P.T, (void*)P.N, (void*)P.mark, (void*)P.pmark, (void*)P.newref, (void*)P.dirty, (void*)P.flag,
                   (void*)P.cbucket, (void*)P.tbest})
     release(q);
   release(nb);
@@ -1379,6 +1385,7 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   // a call that stopped with candidates (iteration limit, error) leaves their
   // marks behind: the next call starts from clean marks
   CK(cudaMemsetAsync(P.mark, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
+  CK(cudaMemsetAsync(P.pmark, 0, sizeof(unsigned long long) * (size_t)P.n_slots, stream));
   LAUNCH(*this, k_mark_all, G, P);
   int status = GDP_OK;
   time_grow = (d.flags & GDP_REFINE_TIME_GROW) != 0;
@@ -1471,6 +1478,8 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   stats.timed_cavity_tris = (int64_t)hctrl->t_cav;
   stats.timed_cavity_edges = (int64_t)hctrl->t_bnd;
   stats.timed_walk_steps = (int64_t)hctrl->t_walk;
+  stats.setups = (int64_t)hctrl->n_setup;
+  stats.timed_setups = (int64_t)hctrl->t_setup;
   stats.flips = (int64_t)hctrl->ff_flips;
   stats.flops = (int64_t)hctrl->ff_flops;
   stats.redundant_removed = (int64_t)hctrl->ff_removed;

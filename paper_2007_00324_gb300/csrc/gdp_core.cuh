@@ -5,6 +5,7 @@
 //                                     (edge e = (v[e+1], v[e+2]) is a subsegment) | DEAD bit 3
 //   N[t]   int4  (n0, n1, n2, -)      neighbour across edge e as (tri << 2 | edge), -1 none
 //   mark[t] u64                       cavity priority mark (Sec. 5.2 atomic marks)
+//   pmark[t] u64                      the same for the refinement pre-pass (first rings)
 //   newref[4t+e] int32                the new triangle that replaced edge e of t (this iteration)
 //   dirty[t] u8                       triangle not yet evaluated (construction, relocation)
 //   flag[t] u8                        its code: 0 good, 1-3 encroached edge + 1, 4 bad;
@@ -19,6 +20,10 @@
 //   then LANES_B lanes of CAP_B = CMAX_BIG; each lane has a hash set of twice
 //   its capacity in big_hash (cavity membership while growing; the fan map
 //   vertex -> boundary records, with big_val, while inserting).
+//   Refinement sets every candidate up in a pre-pass (k_pre): c_setup[i]
+//   holds its splitting point, key and start triangles, c_pre[i*PRE_MAX + j]
+//   the c_npre[i] triangles of its cavity known before growth (0: the set-up
+//   failed), on which it puts its key in pmark[].
 #pragma once
 #include <cstdint>
 
@@ -26,6 +31,7 @@ namespace gdp {
 
 constexpr int CMAX = 32;            // cavity triangles per splitting point
 constexpr int BMAX = CMAX + 2;      // boundary edges per cavity
+constexpr int PRE_MAX = 6;          // start triangles + their first ring (pre-pass)
 constexpr int CMAX_BIG = 1 << 16;   // largest cavity
 constexpr int LANES_A = 4096, CAP_A = 512;       // spill tier A (powers of two)
 constexpr int LANES_B = 16, CAP_B = CMAX_BIG;    // spill tier B
@@ -37,6 +43,8 @@ constexpr int WALK_MAX = 1 << 16;   // point-location steps
 constexpr int BS = 256;             // threads per block
 constexpr int INFO_DEAD = 8;
 constexpr unsigned long long KEY_MID = 1ull << 63;
+
+struct CandSetup;   // a candidate's splitting point, key and start triangles
 
 // candidate states
 enum : uint8_t { C_NONE = 0, C_GROWN = 1, C_LOST = 2, C_SURV = 3, C_FAIL = 4 };
@@ -94,6 +102,8 @@ struct Ctrl {
   unsigned long long n_grown, sum_cav, sum_bnd, sum_walk;
   // the same for the launches timed with CUDA events (GDP_REFINE_TIME_GROW)
   unsigned long long t_grown, t_cav, t_bnd, t_walk;
+  // candidates set up by the refinement pre-pass (all / in the timed launches)
+  unsigned long long n_setup, t_setup;
   int32_t grow_next;     // k_grow_t: next candidate to hand out
   int32_t need_eval;     // some triangles are marked dirty (construction, relocation)
   int32_t grow;          // some mesh asks for more slots (MeshInfo::need_grow)
@@ -112,6 +122,7 @@ struct Pool {
   int4* T;
   int4* N;
   unsigned long long* mark;
+  unsigned long long* pmark;   // pre-pass marks (first rings), cleared like mark
   int32_t* newref;
   uint8_t* dirty;
   uint8_t* flag;
@@ -126,6 +137,7 @@ struct Pool {
   // candidates
   int32_t cap_cand;
   int32_t warp_max;      // up to this many candidates, one warp grows each cavity
+  int32_t no_prepass;    // 1: the pre-pass sets candidates up but places no marks (ablation)
   int32_t* c_elem;
   int32_t* c_loc;
   int32_t* c_vid;
@@ -145,6 +157,9 @@ struct Pool {
   int32_t* cap_hist;
   int32_t* cap_thr;
   int32_t* c_big;        // offset of the cavity in the spill tiers, -1 = own slot
+  struct CandSetup* c_setup;   // refinement pre-pass: each candidate's set-up
+  int32_t* c_pre;        // PRE_MAX per candidate: its pre-marked triangles
+  int32_t* c_npre;       // how many (0: no set-up)
   int32_t* big_cav;      // BIG_ENTRIES
   int4* big_bnd;         // BIG_ENTRIES
   int32_t* big_hash;     // BIG_HASH

@@ -376,6 +376,12 @@ __device__ __forceinline__ void clear_prev_marks(const Pool& P) {
       const int* cav = cav_of(P, i);
       for (int j = 0; j < n; ++j) P.mark[cav[j]] = 0ull;
     }
+    // the refinement pre-pass's marks (entries 0 when the last iteration ran no pre-pass)
+    const int np = i < prev ? P.c_npre[i] : 0;
+    for (int j = 0; j < np; ++j) {
+      const int t = P.c_pre[(size_t)i * PRE_MAX + j];
+      if ((unsigned)t < (unsigned)P.n_slots) P.pmark[t] = 0ull;
+    }
     unsigned bm = __ballot_sync(FULL, big);
     while (bm) {
       const int src = __ffs(bm) - 1;
@@ -727,27 +733,30 @@ __device__ __forceinline__ bool is_split_edge(const int4& rec, int2 sub) {
 // (32-bit per thread: a thread's share of one launch stays far below 2^32;
 // the warp sums are taken in 64 bits)
 struct GrowAcc {
-  unsigned grown = 0, cav = 0, bnd = 0, walk = 0;
+  unsigned grown = 0, cav = 0, bnd = 0, walk = 0, setup = 0;
 };
 
 __device__ __forceinline__ void acc_flush(const Pool& P, const GrowAcc& a, int timed = 0) {
-  unsigned long long grown = a.grown, cav = a.cav, bnd = a.bnd, walk = a.walk;
+  unsigned long long grown = a.grown, cav = a.cav, bnd = a.bnd, walk = a.walk, setup = a.setup;
   for (int o = 16; o; o >>= 1) {
     grown += __shfl_xor_sync(0xffffffffu, grown, o);
     cav += __shfl_xor_sync(0xffffffffu, cav, o);
     bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
     walk += __shfl_xor_sync(0xffffffffu, walk, o);
+    setup += __shfl_xor_sync(0xffffffffu, setup, o);
   }
-  if ((threadIdx.x & 31) == 0 && grown + walk) {
+  if ((threadIdx.x & 31) == 0 && grown + walk + setup) {
     atomicAdd(&P.ctrl->n_grown, grown);
     atomicAdd(&P.ctrl->sum_cav, cav);
     atomicAdd(&P.ctrl->sum_bnd, bnd);
     atomicAdd(&P.ctrl->sum_walk, walk);
+    atomicAdd(&P.ctrl->n_setup, setup);
     if (timed) {
       atomicAdd(&P.ctrl->t_grown, grown);
       atomicAdd(&P.ctrl->t_cav, cav);
       atomicAdd(&P.ctrl->t_bnd, bnd);
       atomicAdd(&P.ctrl->t_walk, walk);
+      atomicAdd(&P.ctrl->t_setup, setup);
     }
   }
 }
@@ -797,6 +806,7 @@ __device__ __noinline__ bool cand_setup(const Pool& P, int i, CandSetup& s, Grow
   s.conv = false;
   s.sub = make_int2(-1, -1);
   if (MODE == 1) {
+    P.c_npre[i] = 0;   // no pre-marks (the pre-pass is refinement's)
     s.vid = CI(elem, P.n_verts, 126);
     s.t0 = CI(P.c_loc[i], P.n_slots, 125);
     s.m = P.T[s.t0].w >> 4;
@@ -884,13 +894,99 @@ __device__ void cand_record(const Pool& P, int i, const CandSetup& s, int nc, in
   acc.bnd += nb;
 }
 
+// ---------------------------------------------------------------- refinement pre-pass
+// Every refinement candidate is set up once, one per lane, before any cavity
+// grows: its splitting point, key, walk and start triangles go to c_setup[i].
+// The candidate then puts its key (atomicMax, Sec. 5.2) on the part of its
+// cavity that is known without growing it: the start triangles and, across
+// their non-subsegment edges, the neighbours whose circumcircles contain the
+// point -- the first level of the breadth-first growth, in the same order.
+// These marks go to their own array, pmark.  A candidate that finds a larger
+// key than its own on one of its pre-marked triangles shares a cavity
+// triangle with a candidate of higher priority, so it would lose that
+// triangle's growth mark as well; growth skips it (it stays a candidate for
+// the next iteration).  Skipped candidates place no growth marks, so the
+// lower-priority candidates near them are no longer blocked by candidates
+// that lose anyway: fewer cavities are grown and no fewer points inserted.
+// Growth reads pmark only after k_pre has finished, and pmark is never
+// written during growth, so which candidates grow depends only on the set of
+// keys: the outcome is deterministic and the same for a mesh alone and in a
+// batch.  (A candidate whose circumcentre gives way to a subsegment during
+// growth keeps the decision made for its circumcentre.)
+__global__ void __launch_bounds__(128) k_pre(Pool P, int timed) {
+  __shared__ CandSetup ws[128];
+  const int n = P.ctrl->n_cand;
+  GrowAcc acc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    P.c_big[i] = -1;
+    CandSetup& s = ws[threadIdx.x];
+    int np = 0;
+    if (cand_setup<0>(P, i, s, acc)) {
+      acc.setup += 1;
+      int pre[PRE_MAX];
+      pre[np++] = s.t0;
+      if (s.t1 >= 0 && s.t1 != s.t0) pre[np++] = s.t1;
+      const int ns = P.no_prepass ? 0 : np;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q >= ns) break;
+        const int t = CI(pre[q], P.n_slots, 140);
+        const int4 T4 = P.T[t];
+        const int4 N4 = P.N[t];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const int ref = comp(N4, e);
+          if (((T4.w >> e) & 1) || ref < 0) continue;
+          const int tn = ref >> 2;
+          bool dup = false;
+#pragma unroll
+          for (int r = 0; r < PRE_MAX; ++r) dup |= r < np && pre[r] == tn;
+          if (dup) continue;
+          const int4 Tn = P.T[CI(tn, P.n_slots, 141)];
+          if (incircle_cs(P, Tn.x, Tn.y, Tn.z, &s) > 0) {
+#pragma unroll
+            for (int r = 0; r < PRE_MAX; ++r)
+              if (r == np) pre[r] = tn;
+            ++np;
+          }
+        }
+      }
+      int* out = P.c_pre + (size_t)i * PRE_MAX;
+#pragma unroll
+      for (int r = 0; r < PRE_MAX; ++r)
+        if (r < np) {
+          out[r] = pre[r];
+          if (!P.no_prepass) atomicMax(&P.pmark[pre[r]], s.key);
+        }
+      P.c_setup[i] = s;
+    }
+    P.c_npre[i] = np;
+  }
+  acc_flush(P, acc, timed);
+}
+
+// The set-up of candidate i for growth: MODE 1 computes it; MODE 0 takes the
+// pre-pass's and is false when the candidate lost one of its pre-marks.
+template <int MODE>
+__device__ __forceinline__ bool cand_load(const Pool& P, int i, CandSetup& s, GrowAcc& acc) {
+  if (MODE == 1) return cand_setup<1>(P, i, s, acc);
+  const int np = P.c_npre[i];
+  if (np <= 0) return false;
+  s = P.c_setup[i];
+  if (P.no_prepass) return true;
+  const int* pre = P.c_pre + (size_t)i * PRE_MAX;
+  for (int r = 0; r < np; ++r)
+    if (P.pmark[pre[r]] != s.key) return false;
+  return true;
+}
+
 // One candidate, one thread (the spill tiers; any cavity size up to the
 // buffer's capacity).  Returns G_OVF when the cavity does not fit B, else
 // G_OK (c_state tells whether the candidate was grown).
 template <int MODE>
 __device__ int grow_cand(const Pool& P, int i, const CavBuf& B, GrowAcc& acc) {
   CandSetup s;
-  if (!cand_setup<MODE>(P, i, s, acc)) return G_OK;
+  if (!cand_load<MODE>(P, i, s, acc)) return G_OK;
   P2 pp{s.p, s.pf};
   int nc = 0, nb = 0, ct = -1, ce = -1;
 #ifdef GDP_DIAG
@@ -1091,7 +1187,7 @@ __device__ __forceinline__ void group_grow_cand(const Pool& P, int i, int* wc, C
   int ok = 1;
   if (g.gl == 0) {
     P.c_big[i] = -1;
-    ok = cand_setup<MODE>(P, i, *ws, acc) ? 1 : 0;
+    ok = cand_load<MODE>(P, i, *ws, acc) ? 1 : 0;
   }
   g.sync();
   if (!g.shfl(ok, 0)) return;
@@ -1153,7 +1249,7 @@ __global__ void __maxnreg__(GDP_GROW_G_REGS) k_grow_g(Pool P, int timed) {
     bool ok = false;
     if (i < n) {
       P.c_big[CI(i, P.cap_cand, 113)] = -1;
-      ok = cand_setup<MODE>(P, i, ws[threadIdx.x], acc);
+      ok = cand_load<MODE>(P, i, ws[threadIdx.x], acc);
     }
     const unsigned okm = __ballot_sync(0xffffffffu, ok);
     __syncwarp();
@@ -1445,7 +1541,7 @@ __global__ void __launch_bounds__(BS) k_depend(Pool P) {
         const unsigned long long mo = P.mark[rec.z >> 2];
         if (!mo) continue;
         const int j = (int)(unsigned)(mo & 0xffffffffull);
-        if (j == i || j >= n || P.c_state[j] != C_SURV) continue;
+        if (j == i || j >= n || P.c_state[j] != C_SURV || P.c_key[j] != mo) continue;
         if (incircle_dep(P, p, rec.x, rec.y, j) > 0 &&
             key < P.c_key[j])
           fin = false;
@@ -1497,7 +1593,7 @@ __device__ __forceinline__ bool replaced(const Pool& P, int ref, int n) {
   const unsigned long long mo = P.mark[ref >> 2];
   if (!mo) return false;
   const int j = (int)(unsigned)(mo & 0xffffffffull);
-  return j < n && P.c_final[j];
+  return j < n && P.c_final[j] && P.c_key[j] == mo;
 }
 
 // A triangle made by an insertion: refinement evaluates it at once (the

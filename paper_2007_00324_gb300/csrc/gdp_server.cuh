@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(BS) k_relocate(Pool D, Pool S, int ms, int md,
     D.dirty[dt + t] = 1;
     D.flag[dt + t] = 0;
     D.mark[dt + t] = 0ull;
+    D.pmark[dt + t] = 0ull;
   }
   for (int v = gt; v < Ms.vert_count; v += gs) {
     D.V[dv + v] = S.V[sv0 + v];
@@ -216,6 +217,7 @@ static int server_setup(gdp_server* s, long long tb, long long vb, long long sb,
   h.P.n_verts = (int)vb;
   h.P.cap_cand = (int)std::min<long long>(std::max<long long>(tb / 4, 65536), 1 << 23);
   h.P.warp_max = (int)env_double("GDP_WARP_GROW_MAX", WARP_GROW_MAX);
+  h.P.no_prepass = env_double("GDP_PREPASS", 1) == 0 ? 1 : 0;
   const long long ab = vb + nm;   // adjacency rows: at most one per vertex plus one per mesh
   int st;
 #define AL(ptr, n, fill) \
@@ -229,6 +231,7 @@ static int server_setup(gdp_server* s, long long tb, long long vb, long long sb,
   AL(H.P.T, tb, 0xff);
   AL(H.P.N, tb, 0xff);
   AL(H.P.mark, tb, 0);
+  AL(H.P.pmark, tb, 0);
   AL(H.P.newref, 4 * tb, 0xff);
   AL(H.P.dirty, tb, 0);
   AL(H.P.flag, tb, 0);
@@ -245,6 +248,7 @@ static int server_setup(gdp_server* s, long long tb, long long vb, long long sb,
   AL(H.P.c_key, C, 0); AL(H.P.c_ncav, C, 0); AL(H.P.c_nbnd, C, 0);
   AL(H.P.c_cav, C * CMAX, 0); AL(H.P.c_bnd, C * BMAX, 0);
   AL(H.P.c_big, C, 0xff); AL(H.P.big_cav, BIG_ENTRIES, 0); AL(H.P.big_bnd, BIG_ENTRIES, 0);
+  AL(H.P.c_setup, C, 0); AL(H.P.c_pre, C * PRE_MAX, 0); AL(H.P.c_npre, C, 0);
   AL(H.P.big_hash, BIG_HASH, 0xff); AL(H.P.big_val, BIG_HASH, 0xff); AL(H.P.lane, LANES_A + LANES_B, 0x7f);
   AL(H.P.c_state, C, 0); AL(H.P.c_final, C, 0); AL(H.P.c_extra, C, 0); AL(H.P.c_offT, C, 0);
   AL(H.P.c_offV, C, 0); AL(H.P.c_base, C, 0);

@@ -42,7 +42,8 @@ class Stats(C.Structure):
                 ("grow_ms", C.c_double), ("grow_launches", C.c_int64), ("timed_grown", C.c_int64),
                 ("timed_cavity_tris", C.c_int64), ("timed_cavity_edges", C.c_int64),
                 ("timed_walk_steps", C.c_int64), ("grow_steps", C.c_int64), ("flips", C.c_int64),
-                ("flops", C.c_int64), ("redundant_removed", C.c_int64)]
+                ("flops", C.c_int64), ("redundant_removed", C.c_int64), ("setups", C.c_int64),
+                ("timed_setups", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
