@@ -16,6 +16,9 @@ segments plus 20 fans of 8 segments 5 degrees apart, B = sqrt 2.
             algorithmic bytes per launch / launch time vs the HBM peak, plus its
             FP64 rate vs the measured FP64 peak and its L2 traffic
   cpu_baseline  the sequential C oracle on the machine's host cores
+  batched / served  (N=1) the 4,096-PSLG batch and a 10 s Poisson request
+            trace, each against the plain per-mesh loop on the same GPU, run
+            after the headline step and summarised in its line
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -124,7 +127,10 @@ def parse():
                          "(the command the ncu counter captures run)")
     ap.add_argument("--count", type=int, default=4096, help="batched: number of PSLGs")
     ap.add_argument("--rate", type=float, default=200.0, help="served: requests per second")
-    ap.add_argument("--duration", type=float, default=2.0, help="served: seconds of arrivals")
+    ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of arrivals")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="paper_shaped at N=1: skip the batched and served runs that follow the "
+                         "headline step (sub-objects 'batched' and 'served' of its line)")
     ap.add_argument("--cand-cap", type=int, default=0, help="per-mesh candidate cap (Rule 2), 0 = none")
     ap.add_argument("--cand-block", type=int, default=0, help="threads per block of the per-candidate kernels")
     ap.add_argument("--graph-iters", type=int, default=0, help="iterations per graph replay, -1 = no graph")
@@ -257,7 +263,7 @@ def run_batched(args):
             "generate_s": t_gen}
     if cpu:
         line["cpu_baseline"] = cpu
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_served(args):
@@ -375,7 +381,24 @@ def run_served(args):
             "generate_s": t_gen}
     if cpu:
         line["cpu_baseline"] = cpu
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def systems_summary(args):
+    """The batched and served configurations run after the headline step, in
+    the same process, summarised as sub-objects of the headline line."""
+    out = {}
+    b = run_batched(args)
+    out["batched"] = {"config": b["config"]["workload"], "meshes_per_s": b["value"],
+                      "batched_tuned": b["batched_tuned"], "batched_default": b["batched_default"],
+                      "plain_loop": b["plain_loop"], "speedup_vs_plain_loop": b["speedup_vs_plain_loop"],
+                      "autotune_best": b["autotune"]["best"], "cpu_baseline": b.get("cpu_baseline")}
+    v = run_served(args)
+    out["served"] = {"config": v["config"]["workload"], "meshes_per_s": v["value"], "served": v["served"],
+                     "plain_loop": v["plain_loop"], "p99_speedup_vs_plain": v["p99_speedup_vs_plain"],
+                     "throughput_speedup_vs_plain": v["throughput_speedup_vs_plain"],
+                     "cpu_baseline": v.get("cpu_baseline")}
+    return out
 
 
 def peaks():
@@ -551,7 +574,8 @@ def run_measure_step(args):
     stream = torch.cuda.current_stream()
     m = gdp.Mesh(p.xy, p.seg, stream=stream)
     s = m.refine(args.B, **refine_kwargs(args))
-    keys = ("n_steiner", "iterations", "candidates", "grown", "cavity_tris", "cavity_edges", "walk_steps")
+    keys = ("n_steiner", "iterations", "candidates", "setups", "grown", "cavity_tris", "cavity_edges",
+            "walk_steps")
     print(json.dumps({"workload": args.workload, "source_hash": grow_source_hash(),
                       **{k: s[k] for k in keys}}), flush=True)
 
@@ -560,10 +584,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batched":
-        return run_batched(args)
-    if args.workload == "served":
-        return run_served(args)
+    if args.workload in ("batched", "served"):
+        line = (run_batched if args.workload == "batched" else run_served)(args)
+        print(json.dumps(line), flush=True)
+        return
     if args.measure_step:
         return run_measure_step(args)
     import torch
@@ -742,6 +766,8 @@ def main():
             "steiner_per_step": stats["n_steiner"], "iterations": stats["iterations"],
             "cdt_rounds": stats["cdt_rounds"],
             "refine_only_steiner_per_s": stats["n_steiner"] / (stats["refine_ms"] / 1000.0),
+            "work_per_step": {"candidates": stats["candidates"], "set_up": stats["setups"],
+                              "grown": stats["grown"], "inserted": stats["inserted"]},
             "gpu_launches": launches, "e2e": e2e, "roofline": roof, "clocks": clocks,
             "step_ms": [round(t, 3) for t in times],
             "flipflop": flipflop,
@@ -749,6 +775,9 @@ def main():
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(p, args.B, 1 if args.workload == "paper_shaped" else 3,
                                             args.max_len, args.workload)
+    if args.workload == "paper_shaped" and world == 1 and not args.no_systems:
+        torch.cuda.empty_cache()
+        line.update(systems_summary(args))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
