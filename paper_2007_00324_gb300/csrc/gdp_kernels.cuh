@@ -913,7 +913,10 @@ __device__ void cand_record(const Pool& P, int i, const CandSetup& s, int nc, in
 // keys: the outcome is deterministic and the same for a mesh alone and in a
 // batch.  (A candidate whose circumcentre gives way to a subsegment during
 // growth keeps the decision made for its circumcentre.)
-__global__ void __launch_bounds__(128) k_pre(Pool P, int timed) {
+#ifndef GDP_PRE_MINB
+#define GDP_PRE_MINB 1
+#endif
+__global__ void __launch_bounds__(128, GDP_PRE_MINB) k_pre(Pool P, int timed) {
   __shared__ CandSetup ws[128];
   const int n = P.ctrl->n_cand;
   GrowAcc acc;
@@ -1218,10 +1221,12 @@ __global__ void __maxnreg__(128) k_grow_w(Pool P, int timed) {
 }
 
 // The same above P.warp_max candidates, where the launch is throughput-bound.
-// A warp takes 32 candidates at a time: first their setups, one per lane (the
-// FP64 circumcentres and keys and the walks, with every lane busy), then their
-// cavities, a group of GROW_GROUP lanes per candidate (four at a time), so
-// that a level's few tuples keep most lanes busy.
+// A warp takes 32 candidates at a time: first their set-ups, one per lane
+// (loaded from the pre-pass, with the first-ring check), then the cavities of
+// the candidates that passed, a group of GROW_GROUP lanes per candidate, so
+// that a level's few tuples keep most lanes busy.  The candidates that passed
+// are dealt to the groups in turn (a list in shared memory), so that the
+// groups of a warp have equal shares whatever the pattern of skipped ones.
 #ifndef GDP_GROW_GROUP_W
 #define GDP_GROW_GROUP_W 8
 #endif
@@ -1236,6 +1241,7 @@ __global__ void __maxnreg__(GDP_GROW_G_REGS) k_grow_g(Pool P, int timed) {
   constexpr int GPW = 32 / GROW_GROUP;    // groups per warp
   __shared__ int wcs[GPB][32];
   __shared__ CandSetup ws[128];           // the setups of a round, one per thread
+  __shared__ int widx[4][32];             // per warp: the lanes whose candidate grows
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gib = threadIdx.x / GROW_GROUP;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -1252,11 +1258,16 @@ __global__ void __maxnreg__(GDP_GROW_G_REGS) k_grow_g(Pool P, int timed) {
       ok = cand_load<MODE>(P, i, ws[threadIdx.x], acc);
     }
     const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    if (ok) widx[wib][__popc(okm & ((1u << lane) - 1u))] = lane;
     __syncwarp();
     // then every group grows one of them at a time
-    for (int r = 0; r < 32; r += GPW) {
-      const int j = r + lane / GROW_GROUP;
-      if ((okm >> j) & 1) group_grow_body<MODE, GROW_GROUP>(P, i0 + j, wcs[gib], &ws[wib * 32 + j], acc);
+    const int na = __popc(okm);
+    for (int r = 0; r < na; r += GPW) {
+      const int k = r + lane / GROW_GROUP;
+      if (k < na) {
+        const int j = widx[wib][k];
+        group_grow_body<MODE, GROW_GROUP>(P, i0 + j, wcs[gib], &ws[wib * 32 + j], acc);
+      }
     }
     __syncwarp();   // the next round's setups overwrite the slots
   }
@@ -1921,116 +1932,131 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
 }
 
 // The same above P.warp_max candidates by groups of GROW_GROUP lanes (four
-// candidates per warp): a group takes its cavity's boundary records (up to
-// BMAX, ceil(BMAX / 8) per lane), finds the fan neighbours by shuffles within
-// the group and writes and evaluates the new triangles in parallel.  A
+// candidates per warp at a time): a warp takes 32 candidates, one per lane for
+// the room check, the slot bases and the new vertices, then deals the final
+// ones to its groups in turn.  A group takes its cavity's boundary records (up
+// to BMAX, ceil(BMAX / 8) per lane), finds the fan neighbours by shuffles
+// within the group and writes and evaluates the new triangles in parallel.  A
 // spill-tier cavity is written by the whole warp (fan_big) after the groups.
 // Identical output to k_insert_t.
 template <int MODE>
 __global__ void __launch_bounds__(128) k_insert_g(Pool P) {
   constexpr int W = GROW_GROUP;
+  constexpr int GPW = 32 / W;
   constexpr int R = (BMAX + W - 1) / W;   // records per lane
   const unsigned FULL = 0xffffffffu;
+  __shared__ int4 wq[4][32];   // per warp: the final candidates of a round (i, mesh, base, vid)
   const int n = P.ctrl->n_cand;
   if (n <= P.warp_max) return;   // k_insert_w's case
   const Group<W> g;
   const unsigned lt_mask = (1u << g.gl) - 1u;
-  const int gg = (blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int ng = (gridDim.x * blockDim.x) / W;
-  for (int i0 = gg - (gg & (32 / W - 1)); i0 < n; i0 += ng) {   // whole warps: spill tiers below
-    const int i = i0 + (gg & (32 / W - 1));
-    bool big = false;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i0 = gw * 32; i0 < n; i0 += nw * 32) {
+    // one candidate per lane: room check, slots and the new vertex
+    const int i0l = i0 + lane;
+    bool fin = false, big = false;
     int m = 0, base = 0, vid = 0;
-    if (i < n) {
-      m = P.c_mesh[i];
+    if (i0l < n) {
+      m = P.c_mesh[i0l];
       const MeshInfo& M = P.mi[m];
       const int f = M.first_cand, l = M.last_cand;
       int totE, totV;
       mesh_totals(P, f, l, totE, totV);
       const bool ok = M.tri_count + totE <= M.tri_cap && M.vert_count + totV <= M.vert_cap;
-      if (g.gl == 0 && i == f) {
+      if (i0l == f) {
         P.mi[m].ins_ok = ok ? 1 : 0;
         if (!ok) no_room<MODE>(P, m);
       }
-      if (P.c_final[i] && ok) {
-        base = M.tri_base + M.tri_count + (P.c_offT[i] - P.c_offT[f]);
-        vid = (MODE == 1) ? P.c_vid[i] : M.vert_base + M.vert_count + (P.c_offV[i] - P.c_offV[f]);
-        if (g.gl == 0) {
-          P.c_base[i] = base;
-          vid = CI(vid, P.n_verts, 207);
-          P.V[vid] = P.c_pt[i];
-          P.Vf[vid] = P.c_ptf[i];
-          P.vseg[vid] = P.c_vseg[i];
-          if (MODE == 1) P.loc[vid] = -1;
+      if (P.c_final[i0l] && ok) {
+        fin = true;
+        base = M.tri_base + M.tri_count + (P.c_offT[i0l] - P.c_offT[f]);
+        vid = (MODE == 1) ? P.c_vid[i0l] : M.vert_base + M.vert_count + (P.c_offV[i0l] - P.c_offV[f]);
+        vid = CI(vid, P.n_verts, 207);
+        P.c_base[i0l] = base;
+        P.V[vid] = P.c_pt[i0l];
+        P.Vf[vid] = P.c_ptf[i0l];
+        P.vseg[vid] = P.c_vseg[i0l];
+        if (MODE == 1) P.loc[vid] = -1;
+        big = P.c_big[i0l] >= 0;
+      }
+    }
+    const unsigned fm = __ballot_sync(FULL, fin && !big);
+    if (fin && !big) wq[wib][__popc(fm & ((1u << lane) - 1u))] = make_int4(i0l, m, base, vid);
+    __syncwarp();   // the new vertices (read by new_tri_code) and the list
+    // then the groups write the small cavities' fans, the finals dealt in turn
+    const int nf = __popc(fm);
+    for (int r0 = 0; r0 < nf; r0 += GPW) {
+      const int k = r0 + lane / W;
+      if (k < nf) {
+        const int4 e = wq[wib][k];
+        const int i = e.x;
+        const int mm = e.y, base = e.z, vid = e.w;
+        const int4* bnd = P.c_bnd + (size_t)i * BMAX;
+        const int* cav = P.c_cav + (size_t)i * CMAX;
+        const int nc = CI(P.c_ncav[i], CMAX + 1, 201), nb = CI(P.c_nbnd[i], BMAX + 1, 201);
+        const int2 sub = P.c_sub[i];
+        const bool is_mid = sub.x >= 0;
+        int4 rec[R];
+        bool keep[R];
+        int slot[R];
+        int done = 0;   // kept records before chunk h
+        for (int h = 0; h < R; ++h) {
+          const int r = g.gl + W * h;
+          rec[h] = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
+          keep[h] = r < nb && !is_split_edge(rec[h], sub);
+          const unsigned km = g.ballot(keep[h]);
+          const int j = done + __popc(km & lt_mask);
+          slot[h] = j < nc ? cav[CI(j, CMAX, 202)] : base + (j - nc);
+          done += __popc(km);
         }
-        g.sync();   // the new vertex is read by every lane (new_tri_code)
-        big = P.c_big[i] >= 0;
-        if (!big) {
-          const int4* bnd = P.c_bnd + (size_t)i * BMAX;
-          const int* cav = P.c_cav + (size_t)i * CMAX;
-          const int nc = CI(P.c_ncav[i], CMAX + 1, 201), nb = CI(P.c_nbnd[i], BMAX + 1, 201);
-          const int2 sub = P.c_sub[i];
-          const bool is_mid = sub.x >= 0;
-          int4 rec[R];
-          bool keep[R];
-          int slot[R];
-          int done = 0;   // kept records before chunk h
+        // fan neighbours: the record starting where mine ends (edge 2) and
+        // the one ending where mine starts (edge 1); the last match wins
+        int n1[R], n2[R];
+        for (int h = 0; h < R; ++h) n1[h] = n2[h] = -1;
+        for (int q = 0; q < nb; ++q) {
+          const int hq = q / W, src = q - W * hq;
+          int qx = -1, qy = -1, qs = -1, qk = 0;
+          for (int h = 0; h < R; ++h)
+            if (h == hq) { qx = rec[h].x; qy = rec[h].y; qs = slot[h]; qk = keep[h] ? 1 : 0; }
+          qx = g.shfl(qx, src);
+          qy = g.shfl(qy, src);
+          qs = g.shfl(qs, src);
+          qk = g.shfl(qk, src);
+          if (!qk) continue;
           for (int h = 0; h < R; ++h) {
-            const int r = g.gl + W * h;
-            rec[h] = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
-            keep[h] = r < nb && !is_split_edge(rec[h], sub);
-            const unsigned km = g.ballot(keep[h]);
-            const int j = done + __popc(km & lt_mask);
-            slot[h] = j < nc ? cav[CI(j, CMAX, 202)] : base + (j - nc);
-            done += __popc(km);
+            if (qx == rec[h].y) n1[h] = (qs << 2) | 2;
+            if (qy == rec[h].x) n2[h] = (qs << 2) | 1;
           }
-          // fan neighbours: the record starting where mine ends (edge 2) and
-          // the one ending where mine starts (edge 1); the last match wins
-          int n1[R], n2[R];
-          for (int h = 0; h < R; ++h) n1[h] = n2[h] = -1;
-          for (int q = 0; q < nb; ++q) {
-            const int hq = q / W, src = q - W * hq;
-            int qx = -1, qy = -1, qs = -1, qk = 0;
-            for (int h = 0; h < R; ++h)
-              if (h == hq) { qx = rec[h].x; qy = rec[h].y; qs = slot[h]; qk = keep[h] ? 1 : 0; }
-            qx = g.shfl(qx, src);
-            qy = g.shfl(qy, src);
-            qs = g.shfl(qs, src);
-            qk = g.shfl(qk, src);
-            if (!qk) continue;
-            for (int h = 0; h < R; ++h) {
-              if (qx == rec[h].y) n1[h] = (qs << 2) | 2;
-              if (qy == rec[h].x) n2[h] = (qs << 2) | 1;
-            }
+        }
+        for (int h = 0; h < R; ++h) {
+          if (!keep[h]) continue;
+          const int s = slot[h];
+          const int u = rec[h].x, v = rec[h].y;
+          int cb = rec[h].w < 0 ? 1 : 0;
+          if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
+          if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
+          int n0 = rec[h].z;
+          if (n0 >= 0) {
+            if (replaced(P, CI(n0, 4ll * P.n_slots, 203), n)) n0 = -1;   // linked by k_link
+            else *comp_ptr(&P.N[CI(n0 >> 2, P.n_slots, 203)], n0 & 3) = s << 2;
           }
-          for (int h = 0; h < R; ++h) {
-            if (!keep[h]) continue;
-            const int s = slot[h];
-            const int u = rec[h].x, v = rec[h].y;
-            int cb = rec[h].w < 0 ? 1 : 0;
-            if (is_mid && (v == sub.x || v == sub.y)) cb |= 2;
-            if (is_mid && (u == sub.x || u == sub.y)) cb |= 4;
-            int n0 = rec[h].z;
-            if (n0 >= 0) {
-              if (replaced(P, CI(n0, 4ll * P.n_slots, 203), n)) n0 = -1;   // linked by k_link
-              else *comp_ptr(&P.N[CI(n0 >> 2, P.n_slots, 203)], n0 & 3) = s << 2;
-            }
-            P.T[CI(s, P.n_slots, 204)] = make_int4(vid, u, v, (m << 4) | cb);
-            P.N[CI(s, P.n_slots, 204)] = make_int4(n0, n1[h], n2[h], 0);
-            P.newref[CI(rec[h].w & 0x7fffffff, 4ll * P.n_slots, 205)] = s << 2;
-            new_tri_code<MODE>(P, CI(s, P.n_slots, 204));
-            P.vtri[CI(u, P.n_verts, 206)] = s;
-            P.vtri[CI(v, P.n_verts, 206)] = s;
-            P.vtri[CI(vid, P.n_verts, 206)] = s;
-          }
+          P.T[CI(s, P.n_slots, 204)] = make_int4(vid, u, v, (mm << 4) | cb);
+          P.N[CI(s, P.n_slots, 204)] = make_int4(n0, n1[h], n2[h], 0);
+          P.newref[CI(rec[h].w & 0x7fffffff, 4ll * P.n_slots, 205)] = s << 2;
+          new_tri_code<MODE>(P, CI(s, P.n_slots, 204));
+          P.vtri[CI(u, P.n_verts, 206)] = s;
+          P.vtri[CI(v, P.n_verts, 206)] = s;
+          P.vtri[CI(vid, P.n_verts, 206)] = s;
         }
       }
     }
-    unsigned bm = __ballot_sync(FULL, big && g.gl == 0);
+    __syncwarp();   // wq is rewritten by the next round
+    unsigned bm = __ballot_sync(FULL, fin && big);
     while (bm) {
       const int src = __ffs(bm) - 1;
       bm &= bm - 1;
-      fan_big<MODE>(P, __shfl_sync(FULL, i, src), __shfl_sync(FULL, m, src), __shfl_sync(FULL, base, src),
+      fan_big<MODE>(P, __shfl_sync(FULL, i0l, src), __shfl_sync(FULL, m, src), __shfl_sync(FULL, base, src),
                     __shfl_sync(FULL, vid, src), n);
     }
   }
