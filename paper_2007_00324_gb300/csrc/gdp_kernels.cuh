@@ -1475,6 +1475,9 @@ __global__ void __maxnreg__(128) k_grow_big(Pool P, int TIER) {
   }
 }
 
+// lanes per survivor in k_depend and per final cavity in k_link
+constexpr int DEP_W = 8;
+
 // a point survives iff it still owns the mark of every cavity triangle
 __global__ void __launch_bounds__(BS) k_survive(Pool P) {
   const unsigned FULL = 0xffffffffu;
@@ -1527,42 +1530,66 @@ __global__ void __launch_bounds__(BS) k_survive(Pool P) {
 // non-subsegment edge uv would need the edge pq if q lies inside the circle of
 // p's new triangle (p,u,v); the lower priority one is dropped.  The test is
 // symmetric (same four points), so both sides agree.
+// A block takes its chunk BS candidates at a time; the survivors among them are
+// listed in shared memory and each is checked by a group of DEP_W lanes, one
+// boundary record per lane, so that the dependent loads of the records (mark,
+// owner state and key, coordinates) overlap instead of running one after
+// another in one thread.
 __global__ void __launch_bounds__(BS) k_depend(Pool P) {
   __shared__ int sm[33];
+  __shared__ int slist[BS];
+  __shared__ int scount;
   const int n = P.ctrl->n_cand;
   const Chunk ch = chunk_of(n);
+  const int gl = threadIdx.x & (DEP_W - 1);
+  const int grp = threadIdx.x / DEP_W;
+  const unsigned gmask = ((1u << DEP_W) - 1u) << ((threadIdx.x & 31) & ~(DEP_W - 1));
   int se = 0, sv = 0;
-  for (int base = ch.b0; base < ch.b1; base += BS) {
-    const int i = base + threadIdx.x;
-    if (i >= ch.b1) continue;
-    bool fin = false;
-    int extra = 0;
-    if (P.c_state[i] == C_SURV) {
-      fin = true;
-      const unsigned long long key = P.c_key[i];
-      const P2 p{P.c_pt[i], P.c_ptf[i]};
-      const int nb = P.c_nbnd[i];
-      const int4* bnd = bnd_of(P, i);
-      const int2 sub = P.c_sub[i];
+  for (int b0 = ch.b0; b0 < ch.b1; b0 += BS) {
+    if (threadIdx.x == 0) scount = 0;
+    __syncthreads();
+    const int i = b0 + threadIdx.x;
+    if (i < ch.b1) {
+      if (P.c_state[i] == C_SURV) {
+        slist[atomicAdd(&scount, 1)] = i;
+      } else {
+        P.c_final[i] = 0;
+        P.c_extra[i] = 0;
+      }
+    }
+    __syncthreads();
+    const int ns = scount;
+    for (int q = grp; q < ns; q += BS / DEP_W) {
+      const int c = slist[q];
+      const unsigned long long key = P.c_key[c];
+      const P2 p{P.c_pt[c], P.c_ptf[c]};
+      const int nb = P.c_nbnd[c];
+      const int4* bnd = bnd_of(P, c);
+      const int2 sub = P.c_sub[c];
       int eff = 0;
-      for (int r = 0; r < nb; ++r) {
+      bool lose = false;
+      for (int r = gl; r < nb; r += DEP_W) {
         const int4 rec = bnd[r];
         if (!is_split_edge(rec, sub)) ++eff;
-        if (rec.w < 0 || rec.z < 0 || !fin) continue;
+        if (rec.w < 0 || rec.z < 0) continue;
         const unsigned long long mo = P.mark[rec.z >> 2];
         if (!mo) continue;
         const int j = (int)(unsigned)(mo & 0xffffffffull);
-        if (j == i || j >= n || P.c_state[j] != C_SURV || P.c_key[j] != mo) continue;
-        if (incircle_dep(P, p, rec.x, rec.y, j) > 0 &&
-            key < P.c_key[j])
-          fin = false;
+        if (j == c || j >= n || P.c_state[j] != C_SURV || P.c_key[j] != mo) continue;
+        if (key < mo && incircle_dep(P, p, rec.x, rec.y, j) > 0) lose = true;
       }
-      if (fin) extra = eff - P.c_ncav[i];
+#pragma unroll
+      for (int o = DEP_W / 2; o; o >>= 1) eff += __shfl_xor_sync(gmask, eff, o);
+      lose = __ballot_sync(gmask, lose) != 0u;
+      if (gl == 0) {
+        const int extra = lose ? 0 : eff - P.c_ncav[c];
+        P.c_final[c] = lose ? 0 : 1;
+        P.c_extra[c] = extra;
+        se += extra;
+        sv += (!lose && P.c_vid[c] < 0) ? 1 : 0;
+      }
     }
-    P.c_final[i] = fin;
-    P.c_extra[i] = extra;
-    se += extra;
-    sv += (fin && P.c_vid[i] < 0) ? 1 : 0;
+    __syncthreads();   // slist and scount are rewritten by the next step
   }
   se = block_sum(se, sm);
   sv = block_sum(sv, sm);
@@ -2070,10 +2097,15 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  __shared__ int wl[BS / 32][32];
+  const int wib = threadIdx.x >> 5;
+  const int gl = lane & (DEP_W - 1);
+  const unsigned gmask = ((1u << DEP_W) - 1u) << (lane & ~(DEP_W - 1));
+  const unsigned glt = (1u << gl) - 1u;
   int ins = 0;
   for (int i0 = gt - lane; i0 < n; i0 += gs) {   // whole warps: spill-tier cavities below
     const int i = i0 + lane;
-    bool big = false;
+    bool big = false, small = false;
     if (i < n) {
       const int m = P.c_mesh[i];
       const MeshInfo& M = P.mi[m];
@@ -2081,22 +2113,7 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
       if (P.c_final[i] && ok) {
         ++ins;
         big = P.c_big[i] >= 0;
-        if (!big) {
-          const int4* bnd = P.c_bnd + (size_t)i * BMAX;
-          const int* cav = P.c_cav + (size_t)i * CMAX;
-          const int nc = P.c_ncav[i], nb = P.c_nbnd[i], base = P.c_base[i];
-          const int2 sub = P.c_sub[i];
-          int j = 0;
-          for (int r = 0; r < nb; ++r) {
-            const int4 rec = bnd[r];
-            if (is_split_edge(rec, sub)) continue;
-            if (rec.z >= 0 && replaced(P, rec.z, n)) {
-              const int s = j < nc ? cav[j] : base + (j - nc);
-              P.N[s].x = P.newref[rec.z];
-            }
-            ++j;
-          }
-        }
+        small = !big;
       }
       if (i == M.last_cand && ok) {
         int totE, totV;
@@ -2114,6 +2131,36 @@ __global__ void __launch_bounds__(BS) k_link(Pool P) {
         }
       }
     }
+    // the small cavities' links, a group of DEP_W lanes per cavity (records in
+    // parallel; the j-th kept record owns the j-th new slot)
+    const unsigned sm_ = __ballot_sync(FULL, small);
+    if (small) wl[wib][__popc(sm_ & lt_mask)] = i;
+    __syncwarp();
+    const int ns = __popc(sm_);
+    for (int r0 = 0; r0 < ns; r0 += 32 / DEP_W) {
+      const int k = r0 + lane / DEP_W;
+      if (k < ns) {
+        const int c = wl[wib][k];
+        const int4* bnd = P.c_bnd + (size_t)c * BMAX;
+        const int* cav = P.c_cav + (size_t)c * CMAX;
+        const int nc = P.c_ncav[c], nb = P.c_nbnd[c], base = P.c_base[c];
+        const int2 sub = P.c_sub[c];
+        int done = 0;
+        for (int h = 0; h < nb; h += DEP_W) {
+          const int r = h + gl;
+          const int4 rec = r < nb ? bnd[r] : make_int4(-1, -1, -1, 0);
+          const bool keep = r < nb && !is_split_edge(rec, sub);
+          const unsigned km = __ballot_sync(gmask, keep) >> (lane & ~(DEP_W - 1));
+          if (keep && rec.z >= 0 && replaced(P, rec.z, n)) {
+            const int j = done + __popc(km & glt);
+            const int s = j < nc ? cav[j] : base + (j - nc);
+            P.N[s].x = P.newref[rec.z];
+          }
+          done += __popc(km);
+        }
+      }
+    }
+    __syncwarp();   // wl is rewritten by the next round
     unsigned bm = __ballot_sync(FULL, big);
     while (bm) {
       const int src = __ffs(bm) - 1;
