@@ -144,54 +144,67 @@ __device__ __forceinline__ uint32_t pick_measure(const Pool& P, const MeshInfo& 
 #define GDP_LOCATE_BLOCKS 2
 #endif
 __global__ void __launch_bounds__(BS, GDP_LOCATE_BLOCKS) k_cdt_locate(Pool P, int stop_cons, int split) {
+  const unsigned FULL = 0xffffffffu;
   const int n = P.ctrl->n_pts;
   const int round = P.ctrl->round;
+  const int lane = threadIdx.x & 31;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (int k = gt; k < n; k += gs) {
-    const int v = P.pts[k];
-    const P2 pv = pt(P, v);
-    int bt, be;
-    int steps = 0;
-    const int t = walk(P, P.loc[v], pv, false, bt, be, steps);
-    if (t < 0) {
-      set_err(P.ctrl, t == -2 ? S_WALK : S_INTERNAL);
-      continue;
-    }
-    P.loc[v] = t;
-    const int4 T4 = P.T[t];
-    const int m = T4.w >> 4;
-    // a duplicate of a vertex of its triangle: equal points have equal
-    // two-float copies (the walk has just read them), so the FP64
-    // coordinates are compared only when those match
-    bool dup = false;
-    for (int e = 0; e < 3; ++e) {
-      const int w = comp(T4, e);
-      const float4 qf = P.Vf[w];
-      if (qf.x == pv.f.x && qf.y == pv.f.y && qf.z == pv.f.z && qf.w == pv.f.w) {
-        const double2 q = P.V[w];
-        dup |= (q.x == pv.d.x && q.y == pv.d.y);
+  for (int k0 = gt - lane; k0 < n; k0 += gs) {   // whole warps: the bids are combined per warp
+    const int k = k0 + lane;
+    bool bid = false;
+    int t = -1;
+    unsigned long long key = 0ull;
+    if (k < n) {
+      const int v = P.pts[k];
+      const P2 pv = pt(P, v);
+      int bt, be;
+      int steps = 0;
+      t = walk(P, P.loc[v], pv, false, bt, be, steps);
+      if (t < 0) {
+        set_err(P.ctrl, t == -2 ? S_WALK : S_INTERNAL);
+      } else {
+        P.loc[v] = t;
+        const int4 T4 = P.T[t];
+        const int m = T4.w >> 4;
+        // a duplicate of a vertex of its triangle: equal points have equal
+        // two-float copies (the walk has just read them), so the FP64
+        // coordinates are compared only when those match
+        bool dup = false;
+        for (int e = 0; e < 3; ++e) {
+          const int w = comp(T4, e);
+          const float4 qf = P.Vf[w];
+          if (qf.x == pv.f.x && qf.y == pv.f.y && qf.z == pv.f.z && qf.w == pv.f.w) {
+            const double2 q = P.V[w];
+            dup |= (q.x == pv.d.x && q.y == pv.d.y);
+          }
+        }
+        if (stop_cons) {
+          // inserted points must not lie on a subsegment
+          for (int e = 0; e < 3; ++e)
+            if (((T4.w >> e) & 1) && orient_ids(P, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), pv) == 0)
+              dup = true;
+        }
+        bool edge = false;
+        if (dup) {
+          P.mi[m].status = S_INPUT;
+          set_err(P.ctrl, S_INPUT);
+        } else if (split) {
+          for (int e = 0; e < 3; ++e) edge |= orient_ids(P, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), pv) == 0;
+        }
+        if (!dup && !edge) {
+          bid = true;
+          key = ((unsigned long long)round << 52) |
+                ((unsigned long long)pick_measure(P, P.mi[m], v, T4) << 32) | (unsigned)v;
+        }
       }
     }
-    if (stop_cons) {
-      // inserted points must not lie on a subsegment
-      for (int e = 0; e < 3; ++e)
-        if (((T4.w >> e) & 1) && orient_ids(P, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), pv) == 0)
-          dup = true;
-    }
-    if (dup) {
-      P.mi[m].status = S_INPUT;
-      set_err(P.ctrl, S_INPUT);
-      continue;
-    }
-    if (split) {
-      bool edge = false;
-      for (int e = 0; e < 3; ++e) edge |= orient_ids(P, comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), pv) == 0;
-      if (edge) continue;
-    }
-    const unsigned long long key = ((unsigned long long)round << 52) |
-                                   ((unsigned long long)pick_measure(P, P.mi[m], v, T4) << 32) |
-                                   (unsigned)v;
-    atomicMax(&P.tbest[t], key);
+    // the largest bid per triangle among the warp's lanes, then one atomic per
+    // triangle: in the first rounds a million points bid for a few triangles,
+    // and same-address atomics serialise
+    const unsigned peers = __match_any_sync(FULL, bid ? t : -1 - lane);
+    const unsigned hi = __reduce_max_sync(peers, (unsigned)(key >> 32));
+    const unsigned lo = __reduce_max_sync(peers, (unsigned)(key >> 32) == hi ? (unsigned)key : 0u);
+    if (bid && lane == __ffs(peers) - 1) atomicMax(&P.tbest[t], ((unsigned long long)hi << 32) | lo);
   }
 }
 

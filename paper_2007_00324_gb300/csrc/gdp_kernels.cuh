@@ -1958,17 +1958,22 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
   }
 }
 
-// The same above P.warp_max candidates by groups of GROW_GROUP lanes (four
+// The same above P.warp_max candidates by groups of INSERT_GROUP lanes (eight
 // candidates per warp at a time): a warp takes 32 candidates, one per lane for
 // the room check, the slot bases and the new vertices, then deals the final
 // ones to its groups in turn.  A group takes its cavity's boundary records (up
-// to BMAX, ceil(BMAX / 8) per lane), finds the fan neighbours by shuffles
+// to BMAX, ceil(BMAX / 4) per lane), finds the fan neighbours by shuffles
 // within the group and writes and evaluates the new triangles in parallel.  A
 // spill-tier cavity is written by the whole warp (fan_big) after the groups.
 // Identical output to k_insert_t.
+#ifndef GDP_INSERT_GROUP_W
+#define GDP_INSERT_GROUP_W 4
+#endif
+constexpr int INSERT_GROUP = GDP_INSERT_GROUP_W;   // lanes per cavity: 4 or 8 (4 measured faster)
+static_assert(INSERT_GROUP == 4 || INSERT_GROUP == 8, "an insertion group is 4 or 8 lanes");
 template <int MODE>
 __global__ void __launch_bounds__(128) k_insert_g(Pool P) {
-  constexpr int W = GROW_GROUP;
+  constexpr int W = INSERT_GROUP;
   constexpr int GPW = 32 / W;
   constexpr int R = (BMAX + W - 1) / W;   // records per lane
   const unsigned FULL = 0xffffffffu;

@@ -1,9 +1,10 @@
 """The cavity-growth and insertion kernels come in three forms that must give
 the same mesh bit for bit (Sec. 5.3, the tuple-list expansion, and Sec. 4.3,
 the retriangulation): one warp per candidate (k_grow_w / k_insert_w, the
-default up to GDP_WARP_GROW_MAX candidates), four candidates per warp in
-lockstep groups of eight lanes (k_grow_g / k_insert_g, above it) and one
-thread per candidate (k_grow_t / k_insert_t, GDP_GROW_GROUP=0).  Setting
+default up to GDP_WARP_GROW_MAX candidates), groups of lanes above it (four
+cavities per warp grown by groups of eight lanes, k_grow_g, and eight written
+by groups of four, k_insert_g) and one thread per candidate (k_grow_t /
+k_insert_t, GDP_GROW_GROUP=0).  Setting
 GDP_WARP_GROW_MAX=1 sends every iteration to the group or thread kernels, so
 the small inputs here cover all of their paths: spill tiers, circumcentres
 that give way to a subsegment's split point, Chew's lenses and Flip-Flop.
@@ -17,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 KERNELS = (
     {},                                                   # warp per candidate
-    {"GDP_WARP_GROW_MAX": "1"},                           # lockstep groups of 8
+    {"GDP_WARP_GROW_MAX": "1"},                           # lane groups
     {"GDP_WARP_GROW_MAX": "1", "GDP_GROW_GROUP": "0"},    # thread per candidate
 )
 
