@@ -627,7 +627,7 @@ __device__ int walk(const Pool& P, int t, const P2& p, bool stop_cons, int& bt, 
   return -2;
 }
 
-enum { G_OK = 0, G_OVF = 1, G_CONV = 2 };
+enum { G_OK = 0, G_OVF = 1, G_CONV = 2, G_LOSE = 3 };
 
 // Bowyer-Watson cavity of p from t0 (and t1): breadth-first over triangles
 // whose circumcircle holds p (exact incircle with simulation of simplicity),
@@ -1327,8 +1327,15 @@ __device__ __forceinline__ void hash_put(const CavBuf& B, int t) {
   }
 }
 
+// key > 0 (refinement): the growth gives up (G_LOSE) once it has taken a
+// triangle on which the pre-pass put a larger key than its own (pmark).
+// Such a triangle lies in the first ring of a candidate of higher priority,
+// so this cavity would be lost unless that candidate was itself skipped;
+// spill-tier cavities are large and seldom win, and their growth is the
+// longest dependent chain of an iteration.  pmark is not written during
+// growth, so the outcome is deterministic.
 __device__ int wgrow_h(const Pool& P, const CavBuf& B, const P2& p, int t0, int t1, bool conv, bool lens,
-                       int& nc, int& nb, int& ct, int& ce) {
+                       unsigned long long key, int& nc, int& nb, int& ct, int& ce) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -1396,15 +1403,18 @@ __device__ int wgrow_h(const Pool& P, const CavBuf& B, const P2& p, int t0, int 
         return G_CONV;
       }
       if (first_ovf < 32) return G_OVF;
+      bool lose = false;
       if (ev == 1) {
         B.cav[k + ar] = tn;
         hash_put(B, tn);
+        lose = key && P.pmark[tn] > key;
       } else if (ev == 2) {
         B.bnd[b + rr] = make_int4(u, v, ref, (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
       }
       k += __popc(am);
       b += __popc(rm);
       __syncwarp();
+      if (__any_sync(FULL, lose)) return G_LOSE;
     }
     lb = le;
   }
@@ -1445,12 +1455,18 @@ __global__ void __maxnreg__(128) k_grow_big(Pool P, int TIER) {
     CandSetup s = ws[wib];
     int nc = 0, nb = 0, ct = -1, ce = -1;
     const bool lens = P.mi[s.m].lens != 0;
-    int g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, s.conv, lens, nc, nb, ct, ce);
+    const unsigned long long lk = (MODE == 0 && !P.no_prepass) ? s.key : 0ull;
+    int g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, s.conv, lens, lk, nc, nb, ct, ce);
     if (g == G_CONV) {
       if (lane == 0) cand_conv(P, i, ws[wib], ct, ce);
       __syncwarp();
       s = ws[wib];
-      g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, false, lens, nc, nb, ct, ce);
+      g = wgrow_h(P, B, P2{s.p, s.pf}, s.t0, s.t1, false, lens, lk ? s.key : 0ull, nc, nb, ct, ce);
+    }
+    if (g == G_LOSE) {   // not grown: no marks, no record
+      if (lane == 0) P.c_big[i] = -1;
+      __syncwarp();
+      continue;
     }
     if (g == G_OVF) {
       if (lane == 0) {
