@@ -421,7 +421,8 @@ struct PoolHost {
     }
     allocs.push_back(q);
     *p = reinterpret_cast<X*>(q);
-    if (cudaMemsetAsync(q, fill, std::max<size_t>(n, 1) * sizeof(X), stream) != cudaSuccess)
+    // fill < 0: scratch that every reader finds written first (no memset)
+    if (fill >= 0 && cudaMemsetAsync(q, fill, std::max<size_t>(n, 1) * sizeof(X), stream) != cudaSuccess)
       return GDP_ERR_CUDA;
     return GDP_OK;
   }
@@ -611,9 +612,11 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   const size_t C = (size_t)P.cap_cand;
   AL(P.c_elem, C, 0); AL(P.c_loc, C, 0); AL(P.c_vid, C, 0); AL(P.c_mesh, C, 0);
   AL(P.c_vseg, C, 0); AL(P.c_sub, C, 0); AL(P.c_pt, C, 0); AL(P.c_ptf, C, 0); AL(P.c_key, C, 0);
-  AL(P.c_ncav, C, 0); AL(P.c_nbnd, C, 0); AL(P.c_cav, C * CMAX, 0); AL(P.c_bnd, C * BMAX, 0);
-  AL(P.c_big, C, 0xff); AL(P.big_cav, BIG_ENTRIES, 0); AL(P.big_bnd, BIG_ENTRIES, 0);
-  AL(P.c_setup, C, 0); AL(P.c_pre, C * PRE_MAX, 0); AL(P.c_npre, C, 0);
+  // cavity lists, boundary records and set-ups are written by the growth
+  // kernels before any kernel reads them (only the counts start at zero)
+  AL(P.c_ncav, C, 0); AL(P.c_nbnd, C, 0); AL(P.c_cav, C * CMAX, -1); AL(P.c_bnd, C * BMAX, -1);
+  AL(P.c_big, C, 0xff); AL(P.big_cav, BIG_ENTRIES, -1); AL(P.big_bnd, BIG_ENTRIES, -1);
+  AL(P.c_setup, C, -1); AL(P.c_pre, C * PRE_MAX, -1); AL(P.c_npre, C, 0);
   AL(P.big_hash, BIG_HASH, 0xff); AL(P.big_val, BIG_HASH, 0xff); AL(P.lane, LANES_A + LANES_B, 0x7f);
   AL(P.c_state, C, 0); AL(P.c_final, C, 0); AL(P.c_extra, C, 0); AL(P.c_offT, C, 0);
   AL(P.c_offV, C, 0); AL(P.c_base, C, 0);

@@ -771,6 +771,10 @@ struct CandSetup {
   unsigned long long key;
   int t0, t1, m, vid;
   int2 sub;
+  // the first level of the growth as the pre-pass found it: bit 3q + e says
+  // that the neighbour across edge e of start triangle q has the point in
+  // its circumcircle (for the tuples the growth tests); -1: not known
+  int pre_in;
   bool conv;
 };
 
@@ -803,6 +807,7 @@ __device__ __noinline__ bool cand_setup(const Pool& P, int i, CandSetup& s, Grow
   const int elem = P.c_elem[i];
   s.t1 = -1;
   s.vid = -1;
+  s.pre_in = -1;
   s.conv = false;
   s.sub = make_int2(-1, -1);
   if (MODE == 1) {
@@ -875,6 +880,7 @@ __device__ void cand_conv(const Pool& P, int i, CandSetup& s, int ct, int ce) {
   const int nr = comp(P.N[ct], ce);
   s.t0 = ct;
   s.t1 = nr >= 0 ? nr >> 2 : -1;
+  s.pre_in = -1;
   s.conv = false;
 }
 
@@ -930,6 +936,7 @@ __global__ void __launch_bounds__(128, GDP_PRE_MINB) k_pre(Pool P, int timed) {
       pre[np++] = s.t0;
       if (s.t1 >= 0 && s.t1 != s.t0) pre[np++] = s.t1;
       const int ns = P.no_prepass ? 0 : np;
+      int pin = 0;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (q >= ns) break;
@@ -951,9 +958,11 @@ __global__ void __launch_bounds__(128, GDP_PRE_MINB) k_pre(Pool P, int timed) {
             for (int r = 0; r < PRE_MAX; ++r)
               if (r == np) pre[r] = tn;
             ++np;
+            pin |= 1 << (3 * q + e);
           }
         }
       }
+      s.pre_in = P.no_prepass ? -1 : pin;
       int* out = P.c_pre + (size_t)i * PRE_MAX;
 #pragma unroll
       for (int r = 0; r < PRE_MAX; ++r)
@@ -1058,6 +1067,7 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const CandSetu
   const int lane = g.gl;
   const unsigned lt_mask = (1u << lane) - 1u;
   const int t0 = ws->t0, t1 = ws->t1;
+  const int pin = ws->pre_in;   // the first level's incircle results, when the pre-pass has them
   int k = 1, b = 0;
   if (lane == 0) {
     wc[0] = t0;
@@ -1101,8 +1111,12 @@ __device__ int wgrow(const Pool& P, int* cav, int4* bnd, int* wc, const CandSetu
       const int leader = __ffs(same) - 1;
       bool in = false;
       if (test && lane == leader) {
-        const int4 Tn = P.T[tn];
-        in = incircle_cs(P, Tn.x, Tn.y, Tn.z, ws) > 0;
+        if (lb == 0 && pin >= 0) {
+          in = (pin >> slot) & 1;
+        } else {
+          const int4 Tn = P.T[tn];
+          in = incircle_cs(P, Tn.x, Tn.y, Tn.z, ws) > 0;
+        }
       }
       in = g.shfl(in, leader);
       const unsigned adders = g.ballot(test && lane == leader && in);
