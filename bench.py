@@ -52,7 +52,8 @@ WORKLOAD_NAMES = {
 REF_SAMPLE = {"n_uniform": 125_000, "n_gauss": 75_000, "n_circle": 50_000, "n_seg": 2_500, "n_fans": 5}
 
 # Algorithmic bytes of the dominant step of the refinement, cavity growth
-# (k_grow_w<0>, or k_grow_g<0> above 32,768 candidates; Sec. 5.2-5.3), per unit of
+# (the pre-pass k_pre, then k_grow_w<0>, or k_grow_b above 32,768 candidates;
+# Sec. 5.2-5.3), per unit of
 # work the library counts on the device:
 #   per cavity of k triangles: the k cavity triangles and the k + 2 triangles
 #   across its boundary edges are read, each 12 B of vertex ids + 48 B of FP64
@@ -67,7 +68,7 @@ GROW_BYTES = {"candidate": 120, "cavity_tri": 136, "walk_step": 76, "setup": 92}
 GROW_SOURCES = ("gdp_core.cuh", "gdp_pred.cuh", "gdp_kernels.cuh")
 # the kernels of one refinement iteration (launched once per iteration, so an ncu
 # launch list counts them in every step and their shares compare directly)
-GROW_KERNELS = ("k_pre", "k_grow_w<0>", "k_grow_g<0>", "k_grow_t<0>")
+GROW_KERNELS = ("k_pre", "k_grow_w<0>", "k_grow_b", "k_grow_g<0>", "k_grow_t<0>")
 REFINE_KERNELS = ("k_scan_eval", "k_scan_count", "k_scan_write") + GROW_KERNELS + (
     "k_grow_big<0>", "k_survive", "k_depend", "k_offsets", "k_insert_w<0>", "k_insert_g<0>", "k_insert_t<0>",
     "k_link<0>")

@@ -216,7 +216,9 @@ __global__ void k_drop_inactive(Pool P) {
   do {                                                               \
     if (MODE == 0) LAUNCH_B(h, k_pre, (h).n_sm * 16, 128, P, timed); \
     LAUNCH_B(h, k_grow_w<MODE>, (h).n_sm * 16, 128, P, timed);       \
-    if ((h).grow_group)                                              \
+    if ((h).grow_group == 2 && MODE == 0)                            \
+      LAUNCH_B(h, k_grow_b, (h).n_sm * 16, 128, P, timed);           \
+    else if ((h).grow_group)                                         \
       LAUNCH_B(h, k_grow_g<MODE>, (h).n_sm * 16, 128, P, timed);     \
     else                                                             \
       LAUNCH_C(h, k_grow_t<MODE>, P, timed);                         \
@@ -530,7 +532,7 @@ struct PoolHost {
   int launch_iteration(int k);
   dim3 mesh_grid = dim3(1, 1);    // per-mesh kernels: (blocks per mesh, meshes)
   int bs_cand = 64;               // per-candidate kernels: threads per block
-  bool grow_group = true;         // above warp_max candidates: k_grow_g (else k_grow_t)
+  int grow_group = 2;   // above warp_max candidates: 2 k_grow_b (refinement), 1 k_grow_g, 0 k_grow_t
   bool capped = false;            // some mesh has a per-iteration candidate cap
   void set_cand_block(int b) {
     bs_cand = (b == 32 || b == 128 || b == 256) ? b : 64;
@@ -553,7 +555,8 @@ int PoolHost::setup(const double* xy, const long long* pt_off, const int32_t* se
   G = 4 * n_sm;
   set_cand_block(64);
   prof = std::getenv("GDP_PROFILE") != nullptr;
-  grow_group = env_double("GDP_GROW_GROUP", 1.0) != 0.0;
+  grow_group = (int)env_double("GDP_GROW_GROUP", 2.0);
+  if (grow_group < 0 || grow_group > 2) grow_group = 1;
   grow_limit = (int)env_double("GDP_GROW_LIMIT", 20.0);
   if (!(hctrl = ctrl_get())) return GDP_ERR_NOMEM;
   CK(cudaEventCreate(&ev0));

@@ -1288,6 +1288,239 @@ __global__ void __maxnreg__(GDP_GROW_G_REGS) k_grow_g(Pool P, int timed) {
   if (MODE == 0) acc_flush(P, acc, timed);
 }
 
+// ---------------------------------------------------------------- warp-batched growth
+// The same above P.warp_max candidates with GDP_GROW_GROUP=2: a warp grows the
+// cavities of the (up to 32) candidates of a round together, level by level.
+// The tuples of one level of every growing candidate form one list that the
+// lanes take 32 at a time, so a lane's tuple may belong to any of them;
+// matches, ballots and prefix counts are taken within each candidate's run of
+// lanes.  Every lane runs every warp-wide step: the candidates share one
+// instruction stream, where the four groups of k_grow_g diverge.  Per
+// candidate the cavity list, the record order, the first encroached
+// subsegment and the overflow point are those of the sequential
+// breadth-first growth (the chunking does not matter, as in wgrow).
+// Lane c keeps candidate c's set-up in ws and its cavity so far in cv[c]
+// (shared memory); its counts, level start and state are in shared arrays that
+// every lane reads for the candidate of its tuple.
+#ifndef GDP_GROW_B_REGS
+#define GDP_GROW_B_REGS 64
+#endif
+enum : int { B_NONE = 0, B_RUN = 1, B_OK = 2, B_CONV = 3, B_OVF = 4 };
+
+__global__ void __maxnreg__(GDP_GROW_B_REGS) k_grow_b(Pool P, int timed) {
+  const unsigned FULL = 0xffffffffu;
+  __shared__ CandSetup ws[128];
+  __shared__ int wcav[4][32][CMAX];
+  __shared__ int sk[4][32], sb[4][32], slb[4][32], sst[4][32], sce[4][32];
+  __shared__ int soff[4][33];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int n = P.ctrl->n_cand;
+  if (n <= P.warp_max) return;   // k_grow_w's case
+  GrowAcc acc;
+  CandSetup* W = ws + wib * 32;
+  int (*cv)[CMAX] = wcav[wib];
+  for (int i0 = gw * 32; i0 < n; i0 += nw * 32) {
+    const int i = i0 + lane;   // lane c owns candidate i0 + c
+    bool ok = false;
+    if (i < n) {
+      P.c_big[CI(i, P.cap_cand, 114)] = -1;
+      ok = cand_load<0>(P, i, W[lane], acc);
+    }
+    int st = ok ? B_RUN : B_NONE;
+    sce[wib][lane] = 0;
+    // pass 0: every candidate; pass 1: the ones whose circumcentre gave way to
+    // a subsegment's split point (grown again from the subsegment's sides)
+    for (int pass = 0; pass < 2; ++pass) {
+      if (!__any_sync(FULL, st == B_RUN)) break;
+      if (st == B_RUN) {
+        const int t0 = W[lane].t0, t1 = W[lane].t1;
+        cv[lane][0] = t0;
+        P.c_cav[(size_t)i * CMAX] = t0;
+        int k = 1;
+        if (t1 >= 0 && t1 != t0) {
+          cv[lane][1] = t1;
+          P.c_cav[(size_t)i * CMAX + 1] = t1;
+          k = 2;
+        }
+        sk[wib][lane] = k;
+        sb[wib][lane] = 0;
+        slb[wib][lane] = 0;
+      }
+      sst[wib][lane] = st;
+      __syncwarp();
+      while (__any_sync(FULL, sst[wib][lane] == B_RUN)) {
+        // this level: tuples [3 lb, 3 le) of every running candidate
+        const bool run = sst[wib][lane] == B_RUN;
+        const int le = sk[wib][lane];
+        const int T = run ? 3 * (le - slb[wib][lane]) : 0;
+        int incl = T;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += y;
+        }
+        soff[wib][lane] = incl - T;
+        if (lane == 31) soff[wib][32] = incl;
+        __syncwarp();
+        const int TT = soff[wib][32];
+        for (int base = 0; base < TT; base += 32) {
+          const int x = base + lane;
+          bool act = x < TT;
+          int c = 0;
+          if (act) {   // the candidate of tuple x: the last c with soff[c] <= x
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (soff[wib][mid] <= x) lo = mid;
+              else hi = mid - 1;
+            }
+            c = lo;
+            act = sst[wib][c] == B_RUN;   // stopped earlier in this level: no more tuples
+          }
+          int slot = 0, t = -1, e = 0, tn = -1, kc = 0, bc = 0, lbc = 0;
+          bool cons = false;
+          int4 rec = make_int4(-1, -1, -1, 0);
+          if (act) {
+            lbc = slb[wib][c];
+            kc = sk[wib][c];
+            bc = sb[wib][c];
+            slot = 3 * lbc + (x - soff[wib][c]);
+            const int q = slot / 3;
+            e = slot - 3 * q;
+            t = cv[c][q];
+            const int4 T4 = P.T[CI(t, P.n_slots, 115)];
+            const int ref = comp(P.N[CI(t, P.n_slots, 115)], e);
+            cons = (T4.w >> e) & 1;
+            tn = ref >= 0 ? ref >> 2 : -1;
+            rec = make_int4(comp(T4, mod3(e + 1)), comp(T4, mod3(e + 2)), ref,
+                            (int)(((unsigned)cons << 31) | (unsigned)((t << 2) | e)));
+          }
+          bool member = false;
+          for (int j = 0; j < kc; ++j) member |= (cv[c][j] == tn);
+          const bool test = act && !member && tn >= 0 && !cons;
+          // (candidate, neighbour) pairs; lane-unique values match nothing
+          const unsigned long long uk = (unsigned long long)(64 + lane) << 32;
+          const unsigned long long ck = ((unsigned long long)c << 32) | (unsigned)tn;
+          const unsigned same = __match_any_sync(FULL, test ? ck : uk);
+          const int leader = __ffs(same) - 1;
+          bool in = false;
+          if (test && lane == leader) {
+            const CandSetup* sc = &W[c];
+            if (lbc == 0 && sc->pre_in >= 0) {
+              in = (sc->pre_in >> slot) & 1;
+            } else {
+              const int4 Tn = P.T[CI(tn, P.n_slots, 116)];
+              in = incircle_cs(P, Tn.x, Tn.y, Tn.z, sc) > 0;
+            }
+          }
+          in = __shfl_sync(FULL, in, leader);
+          const unsigned adders = __ballot_sync(FULL, test && lane == leader && in);
+          const unsigned same_all = __match_any_sync(FULL, (act && tn >= 0) ? ck : uk);
+          if (act && tn >= 0 && (same_all & adders & lt_mask)) member = true;
+          // 1 add, 2 boundary record, 3 encroached subsegment (the circumcentre gives way)
+          int ev = 0;
+          if (act && !member) {
+            if (test) {
+              ev = (lane == leader && in) ? 1 : (in ? 0 : 2);
+            } else if (cons && W[c].conv &&
+                       encroaches(pt(P, rec.x), pt(P, rec.y), P2{W[c].p, W[c].pf}, P.mi[W[c].m].lens != 0)) {
+              ev = 3;
+            } else {
+              ev = 2;
+            }
+          }
+          const unsigned seg = __match_any_sync(FULL, act ? c : 32 + lane);   // this candidate's lanes
+          const unsigned am = __ballot_sync(FULL, ev == 1) & seg;
+          const unsigned rm = __ballot_sync(FULL, ev == 2) & seg;
+          const unsigned cm = __ballot_sync(FULL, ev == 3) & seg;
+          const int ar = __popc(am & lt_mask), rr = __popc(rm & lt_mask);
+          const unsigned ovf =
+              __ballot_sync(FULL, (ev == 1 && kc + ar >= CMAX) || (ev == 2 && bc + rr >= BMAX)) & seg;
+          const int first_conv = cm ? __ffs(cm) - 1 : 32;
+          const int first_ovf = ovf ? __ffs(ovf) - 1 : 32;
+          const bool head = act && lane == __ffs(seg) - 1;
+          if (act) {
+            if (first_conv < first_ovf) {
+              if (lane == first_conv) {
+                sst[wib][c] = B_CONV;
+                sce[wib][c] = rec.w & 0x7fffffff;
+              }
+            } else if (first_ovf < 32) {
+              if (head) sst[wib][c] = B_OVF;
+            } else {
+              const size_t ic = (size_t)(i0 + c);
+              if (ev == 1) {
+                cv[c][kc + ar] = tn;
+                P.c_cav[ic * CMAX + kc + ar] = tn;
+              } else if (ev == 2) {
+                P.c_bnd[ic * BMAX + bc + rr] = rec;
+              }
+              if (head) {
+                sk[wib][c] = kc + __popc(am);
+                sb[wib][c] = bc + __popc(rm);
+              }
+            }
+          }
+          __syncwarp();
+        }
+        // the level is done; a level that added nothing ends the growth
+        if (sst[wib][lane] == B_RUN) {
+          slb[wib][lane] = le;
+          if (sk[wib][lane] == le) sst[wib][lane] = B_OK;
+        }
+        __syncwarp();
+      }
+      st = sst[wib][lane];
+      if (pass == 0 && st == B_CONV) {
+        const int te = sce[wib][lane];
+        cand_conv(P, i, W[lane], te >> 2, te & 3);
+        sce[wib][lane] = 0;
+        st = B_RUN;
+      }
+      __syncwarp();
+    }
+    if (st == B_OVF) atomicMin(&P.lane[i & (LANES_A - 1)], i);
+    // visibility of the cavity boundaries from the points, records in parallel
+    // (sce now flags a boundary edge that does not see the point)
+    const int nbc = st == B_OK ? sb[wib][lane] : 0;
+    int incl = nbc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    soff[wib][lane] = incl - nbc;
+    if (lane == 31) soff[wib][32] = incl;
+    __syncwarp();
+    const int TR = soff[wib][32];
+    for (int base = 0; base < TR; base += 32) {
+      const int x = base + lane;
+      if (x < TR) {
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (soff[wib][mid] <= x) lo = mid;
+          else hi = mid - 1;
+        }
+        const int c = lo;
+        const int4 rec = P.c_bnd[(size_t)(i0 + c) * BMAX + (x - soff[wib][c])];
+        if (!is_split_edge(rec, W[c].sub) && orient_cs(P, rec.x, rec.y, &W[c]) <= 0) sce[wib][c] = 1;
+      }
+    }
+    __syncwarp();
+    if (st == B_OK && sce[wib][lane] == 0) {
+      const int kc = sk[wib][lane];
+      const unsigned long long key = W[lane].key;
+      for (int j = 0; j < kc; ++j) atomicMax(&P.mark[cv[lane][j]], key);
+      cand_record(P, i, W[lane], kc, sb[wib][lane], acc);
+    }
+    __syncwarp();   // the next round rewrites the set-ups and cavities
+  }
+  acc_flush(P, acc, timed);
+}
+
 // the same, one thread per candidate, when there are more than
 // P.warp_max candidates (a separate kernel keeps each version's register
 // allocation to itself).  Warps take runs of 32 candidates from a counter

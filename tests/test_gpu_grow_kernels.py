@@ -4,7 +4,9 @@ the retriangulation): one warp per candidate (k_grow_w / k_insert_w, the
 default up to GDP_WARP_GROW_MAX candidates), groups of lanes above it (four
 cavities per warp grown by groups of eight lanes, k_grow_g, and eight written
 by groups of four, k_insert_g) and one thread per candidate (k_grow_t /
-k_insert_t, GDP_GROW_GROUP=0).  Setting
+k_insert_t, GDP_GROW_GROUP=0); the warp-batched growth (k_grow_b,
+GDP_GROW_GROUP=2) grows the cavities of a warp's 32 candidates from one
+shared tuple list.  Setting
 GDP_WARP_GROW_MAX=1 sends every iteration to the group or thread kernels, so
 the small inputs here cover all of their paths: spill tiers, circumcentres
 that give way to a subsegment's split point, Chew's lenses and Flip-Flop.
@@ -18,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 KERNELS = (
     {},                                                   # warp per candidate
-    {"GDP_WARP_GROW_MAX": "1"},                           # lane groups
+    {"GDP_WARP_GROW_MAX": "1"},                           # warp-batched growth (default)
+    {"GDP_WARP_GROW_MAX": "1", "GDP_GROW_GROUP": "1"},    # lane groups
     {"GDP_WARP_GROW_MAX": "1", "GDP_GROW_GROUP": "0"},    # thread per candidate
 )
 
