@@ -9,8 +9,8 @@ segments plus 20 fans of 8 segments 5 degrees apart, B = sqrt 2.
 
   value     Steiner points / (CDT + refine) device time, inputs resident in HBM,
             un-instrumented steps
-  e2e       the same through the C ABI with host buffers: create (H2D inside),
-            refine and export (D2H) all in the timed region
+  e2e       the same through the C ABI with pinned host buffers: create (H2D
+            inside), refine and export (D2H) all in the timed region
   roofline  the cavity-growth kernel (the largest refinement kernel), timed by
             CUDA events inside the graph in separate instrumented steps:
             algorithmic bytes per launch / launch time vs the HBM peak, plus its
@@ -650,9 +650,15 @@ def main():
     tot_ms, steiner_all = replica_totals(sum(times), steiner, world, dev)
     value = steiner_all / (tot_ms / 1000.0)
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers: the inputs, and
+    # the export's destination (allocated once, sized from the timed steps'
+    # counts with a margin, outside the timed region)
     xy_h = torch.from_numpy(p.xy).pin_memory()
     seg_h = torch.from_numpy(p.seg).pin_memory()
+    room = 1.25
+    out_h = (torch.empty((int(room * (p.n + stats["n_steiner"] + 16)), 2), dtype=torch.float64).pin_memory().numpy(),
+             torch.empty((int(room * stats["n_tris"]) + 64, 3), dtype=torch.int32).pin_memory().numpy(),
+             torch.empty((int(room * stats["n_subsegs"]) + 64, 3), dtype=torch.int32).pin_memory().numpy())
     e2e_ms, e2e_steiner, d2h = [], 0, 0
     for k in range(max(1, args.steps)):
         flush.fill_(1.0)
@@ -660,7 +666,7 @@ def main():
         t0 = time.perf_counter()
         m = gdp.Mesh(xy_h.numpy(), seg_h.numpy(), stream=stream)
         s2 = m.refine(args.B, **refine_kwargs(args))
-        xy_o, tri_o, sub_o = m.export()
+        xy_o, tri_o, sub_o = m.export(out=out_h)
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
         e2e_steiner += s2["n_steiner"]

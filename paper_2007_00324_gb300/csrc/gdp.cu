@@ -1467,6 +1467,11 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
     }
   }
   CK(cudaEventRecord(ev1, stream));
+  // the refined meshes' live triangles and subsegments (after the timed region)
+  CK(cudaMemsetAsync(&P.ctrl->live_tri, 0, 2 * sizeof(unsigned long long), stream));
+  LAUNCH(*this, k_count_live, mesh_grid, P);
+  CK(cudaMemcpyAsync(&hctrl->live_tri, &P.ctrl->live_tri, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                     stream));
   CK(cudaStreamSynchronize(stream));
   float ms = 0;
   CK(cudaEventElapsedTime(&ms, ev0, ev1));
@@ -1489,14 +1494,14 @@ int PoolHost::refine(const double* B, const gdp_refine_opts* o) {
   stats.flips = (int64_t)hctrl->ff_flips;
   stats.flops = (int64_t)hctrl->ff_flops;
   stats.redundant_removed = (int64_t)hctrl->ff_removed;
-  long long st = 0, nt = 0;
+  long long st = 0;
   for (auto& M : hmi) {
     st += M.steiner;
-    nt += M.tri_count;
     if (M.status != S_OK && status == GDP_OK) status = M.status;
   }
   stats.n_steiner = st;
-  stats.n_tris = nt;
+  stats.n_tris = (int64_t)hctrl->live_tri;
+  stats.n_subsegs = (int64_t)hctrl->live_sub;
   return status;
 }
 

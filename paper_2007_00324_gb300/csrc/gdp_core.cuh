@@ -104,6 +104,8 @@ struct Ctrl {
   unsigned long long t_grown, t_cav, t_bnd, t_walk;
   // candidates set up by the refinement pre-pass (all / in the timed launches)
   unsigned long long n_setup, t_setup;
+  // live triangles and subsegments of all meshes after a refine call (k_count_live)
+  unsigned long long live_tri, live_sub;
   int32_t grow_next;     // k_grow_t: next candidate to hand out
   int32_t need_eval;     // some triangles are marked dirty (construction, relocation)
   int32_t grow;          // some mesh asks for more slots (MeshInfo::need_grow)

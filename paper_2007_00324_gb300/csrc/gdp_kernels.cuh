@@ -2236,8 +2236,13 @@ __global__ void __launch_bounds__(128) k_insert_w(Pool P) {
 #endif
 constexpr int INSERT_GROUP = GDP_INSERT_GROUP_W;   // lanes per cavity: 4 or 8 (4 measured faster)
 static_assert(INSERT_GROUP == 4 || INSERT_GROUP == 8, "an insertion group is 4 or 8 lanes");
+#ifdef GDP_INSERT_REGS
+#define GDP_INSERT_G_BOUNDS __maxnreg__(GDP_INSERT_REGS)
+#else
+#define GDP_INSERT_G_BOUNDS __launch_bounds__(128)
+#endif
 template <int MODE>
-__global__ void __launch_bounds__(128) k_insert_g(Pool P) {
+__global__ void GDP_INSERT_G_BOUNDS k_insert_g(Pool P) {
   constexpr int W = INSERT_GROUP;
   constexpr int GPW = 32 / W;
   constexpr int R = (BMAX + W - 1) / W;   // records per lane
@@ -2496,6 +2501,31 @@ __global__ void __launch_bounds__(BS) k_export_count(Pool P, int m) {
   if (threadIdx.x == 0) {
     P.blk[blockIdx.x] = nt;
     P.blk[gridDim.x + blockIdx.x] = ns;
+  }
+}
+
+// live triangles and subsegments of every mesh (a subsegment counted once,
+// as the export emits it), for the statistics of a refine call; blocks on a
+// 2D grid (x: blocks of one mesh, y: meshes)
+__global__ void __launch_bounds__(BS) k_count_live(Pool P) {
+  unsigned long long nt = 0, ns = 0;
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    const MeshInfo& M = P.mi[m];
+    for (int k = blockIdx.x * BS + threadIdx.x; k < M.tri_count; k += gridDim.x * BS) {
+      const int t = M.tri_base + k;
+      const int4 T4 = P.T[t];
+      if (T4.w < 0 || (T4.w & INFO_DEAD)) continue;
+      ++nt;
+      for (int e = 0; e < 3; ++e) ns += ex_sub(P, t, T4, e) ? 1 : 0;
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    nt += __shfl_xor_sync(0xffffffffu, nt, o);
+    ns += __shfl_xor_sync(0xffffffffu, ns, o);
+  }
+  if ((threadIdx.x & 31) == 0 && nt + ns) {
+    atomicAdd(&P.ctrl->live_tri, nt);
+    atomicAdd(&P.ctrl->live_sub, ns);
   }
 }
 

@@ -224,21 +224,31 @@ class Mesh:
             i += 1
         return out
 
-    def export(self):
+    def export(self, out=None):
+        """(xy, tri, sub) as numpy arrays.  out: optional (xy, tri, sub) host
+        arrays of at least the mesh's sizes (C-contiguous float64 (n,2), int32
+        (t,3), int32 (s,3), e.g. views of pinned memory) to copy into; the
+        returned arrays are then views of their leading rows."""
         L = load()
         n_pts, n_tri, n_seg = C.c_int64(), C.c_int64(), C.c_int64()
-        st = L.gdp_mesh_export(self._h, None, 0, None, 0, None, 0, C.byref(n_pts), C.byref(n_tri),
-                               C.byref(n_seg))
-        if st != OK:
-            raise GdpError(st, "gdp_mesh_export")
-        xy = np.zeros((n_pts.value, 2), np.float64)
-        tri = np.zeros((n_tri.value, 3), np.int32)
-        sub = np.zeros((n_seg.value, 3), np.int32)
+        if out is not None:   # one call: the library checks the capacities
+            xy, tri, sub = out
+            for a, dt, w in ((xy, np.float64, 2), (tri, np.int32, 3), (sub, np.int32, 3)):
+                if a.dtype != dt or a.ndim != 2 or a.shape[1] != w or not a.flags.c_contiguous:
+                    raise ValueError(f"export: out array {a.dtype} {a.shape} is not a C-contiguous (n, {w}) {dt}")
+        else:
+            st = L.gdp_mesh_export(self._h, None, 0, None, 0, None, 0, C.byref(n_pts), C.byref(n_tri),
+                                   C.byref(n_seg))
+            if st != OK:
+                raise GdpError(st, "gdp_mesh_export")
+            xy = np.zeros((n_pts.value, 2), np.float64)
+            tri = np.zeros((n_tri.value, 3), np.int32)
+            sub = np.zeros((n_seg.value, 3), np.int32)
         st = L.gdp_mesh_export(self._h, _p(xy), len(xy), _p(tri), len(tri), _p(sub), len(sub),
                                C.byref(n_pts), C.byref(n_tri), C.byref(n_seg))
         if st != OK:
             raise GdpError(st, "gdp_mesh_export")
-        return xy, tri, sub
+        return xy[:n_pts.value], tri[:n_tri.value], sub[:n_seg.value]
 
     def insert_points(self, xy):
         xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)

@@ -124,3 +124,27 @@ def test_stopped_call_then_finished(oracle):
     g.refine(SQ2)
     xy, tri, sub = g.export()
     assert_valid(oracle.check(xy, tri, sub, p.seg, p.n, B=SQ2, brute=True), brute=True)
+
+
+def test_export_into_caller_buffers(oracle):
+    """Mesh.export(out=...) copies into the caller's host arrays (as the bench
+    does with pinned buffers) and gives the same mesh; arrays that are too
+    short are refused before anything is copied"""
+    gdp = need_gpu()
+    import torch
+    from paper_2007_00324_gb300 import workloads as W
+    p = W.tiny()
+    g = gdp.Mesh(p.xy, p.seg)
+    st = g.refine(SQ2)
+    xy, tri, sub = g.export()
+    # the refine statistics count the live triangles and subsegments the export gives
+    assert st["n_tris"] == len(tri) and st["n_subsegs"] == len(sub), (st["n_tris"], st["n_subsegs"])
+    assert st["n_steiner"] == len(xy) - p.n
+    out = (torch.empty((len(xy) + 7, 2), dtype=torch.float64).pin_memory().numpy(),
+           torch.empty((len(tri) + 5, 3), dtype=torch.int32).pin_memory().numpy(),
+           torch.empty((len(sub) + 3, 3), dtype=torch.int32).pin_memory().numpy())
+    xy2, tri2, sub2 = g.export(out=out)
+    assert np.array_equal(xy, xy2) and np.array_equal(tri, tri2) and np.array_equal(sub, sub2)
+    short = (out[0][:len(xy) - 1], out[1], out[2])
+    with pytest.raises(gdp.GdpError):
+        g.export(out=short)
