@@ -92,6 +92,90 @@ __global__ void __launch_bounds__(BS) k_iscan_write(int* a, int n, const int* bl
   }
 }
 
+// ---------------------------------------------------------------- spatial order of the construction's points
+// The construction inserts the pending points in the order of the pending list
+// (each triangle takes one per round, chosen by its own key), and new triangles
+// take slots in that order.  Listing each mesh's points by cell of a 2^L x 2^L
+// grid over its box -- cells in Morton order, the points of a cell by id --
+// puts triangles that are near in the plane near in memory, for the
+// construction's walks and for every kernel after it.  The order depends only
+// on the mesh's own points (a mesh is triangulated the same alone and in a
+// batch), and the CDT does not depend on the order at all.  A mesh with a cell
+// of more than CELL_SORT_MAX points (dense duplicates) keeps its input order.
+constexpr int CELL_SORT_MAX = 256;
+
+__device__ __forceinline__ uint32_t spread16(uint32_t v) {
+  v &= 0xffffu;
+  v = (v | (v << 8)) & 0x00ff00ffu;
+  v = (v | (v << 4)) & 0x0f0f0f0fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+// the Morton index of p's cell; coordinates outside the box or not finite go
+// to the nearest edge cell (such a mesh is rejected later anyway)
+__device__ __forceinline__ int cell_of(const MeshInfo& M, double2 p, int L) {
+  const double w = fmax(M.hi.x - M.lo.x, M.hi.y - M.lo.y);
+  const int G = 1 << L;
+  const double fx = w > 0 ? (p.x - M.lo.x) / w * G : 0.0;
+  const double fy = w > 0 ? (p.y - M.lo.y) / w * G : 0.0;
+  const int cx = (fx >= 0.0 && fx < G) ? (int)fx : (fx >= G ? G - 1 : 0);
+  const int cy = (fy >= 0.0 && fy < G) ? (int)fy : (fy >= G ? G - 1 : 0);
+  return (int)(spread16((uint32_t)cx) | (spread16((uint32_t)cy) << 1));
+}
+
+__global__ void k_cell_count(Pool P, const int* cbase, const int* lev, int* cnt) {
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    const MeshInfo& M = P.mi[m];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M.n_in; k += gridDim.x * blockDim.x)
+      atomicAdd(&cnt[cbase[m] + cell_of(M, P.V[M.vert_base + k], lev[m])], 1);
+  }
+}
+
+// end: inclusive prefix sums of cnt (a cell's points end there)
+__global__ void k_cell_scatter(Pool P, const int* cbase, const int* lev, const int* end, const int* cnt,
+                               int* fill, int* tmp, int* crowded) {
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    const MeshInfo& M = P.mi[m];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M.n_in; k += gridDim.x * blockDim.x) {
+      const int c = cbase[m] + cell_of(M, P.V[M.vert_base + k], lev[m]);
+      if (cnt[c] > CELL_SORT_MAX) crowded[m] = 1;
+      tmp[end[c] - cnt[c] + atomicAdd(&fill[c], 1)] = M.vert_base + k;
+    }
+  }
+}
+
+// the points of each cell by id (insertion sort; crowded cells are skipped)
+__global__ void k_cell_sort(int ncell, const int* end, const int* cnt, int* tmp) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (int c = gt; c < ncell; c += gs) {
+    const int n = cnt[c];
+    if (n < 2 || n > CELL_SORT_MAX) continue;
+    int* a = tmp + (end[c] - n);
+    for (int i = 1; i < n; ++i) {
+      const int x = a[i];
+      int j = i - 1;
+      while (j >= 0 && a[j] > x) {
+        a[j + 1] = a[j];
+        --j;
+      }
+      a[j + 1] = x;
+    }
+  }
+}
+
+__global__ void k_cell_put(Pool P, const int* cbase, const int* end, const int* cnt, const int* tmp,
+                           const int* crowded) {
+  for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
+    const MeshInfo& M = P.mi[m];
+    if (crowded[m]) continue;
+    const int first = end[cbase[m]] - cnt[cbase[m]];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M.n_in; k += gridDim.x * blockDim.x)
+      P.pts[M.pts_base + k] = tmp[first + k];
+  }
+}
+
 // input vertices where two segments meet at less than 60 degrees
 __global__ void k_apex(Pool P) {
   for (int m = blockIdx.y; m < P.n_mesh; m += gridDim.y) {
@@ -465,6 +549,7 @@ struct PoolHost {
   int setup(const double* xy, const long long* pt_off, const int32_t* seg, const long long* seg_off,
             int nm, bool on_device, void* s);
   int build_cdt();
+  int spatial_order();
   bool cdt_done = false;          // build_cdt ran to the end (mesh statuses are final)
   int insert_rounds(int stop_cons, int* rounds_out, bool split);
   int launch_cdt_round(const Pool& Q, int stop_cons);
@@ -970,6 +1055,39 @@ int PoolHost::insert_rounds(int stop_cons, int* rounds_out, bool split) {
   return GDP_OK;
 }
 
+// the pending points of every mesh in cell (Morton) order, see k_cell_count
+int PoolHost::spatial_order() {
+  std::vector<int> lev(n_mesh), cbase(n_mesh + 1, 0);
+  for (int m = 0; m < n_mesh; ++m) {
+    int L = 0;   // 4^L >= n_in / 2: about two points per cell
+    while (L < 15 && (1ll << (2 * L)) * 2 < (long long)hmi[m].n_in) ++L;
+    lev[m] = L;
+    cbase[m + 1] = cbase[m] + (1 << (2 * L));
+  }
+  const int ncell = cbase[n_mesh];
+  int *d_lev = nullptr, *d_cbase = nullptr, *cnt = nullptr, *end = nullptr, *fill = nullptr, *tmp = nullptr,
+      *crowded = nullptr;
+  int st;
+  if ((st = alloc(&d_lev, n_mesh)) != GDP_OK || (st = alloc(&d_cbase, n_mesh + 1)) != GDP_OK ||
+      (st = alloc(&cnt, ncell, 0)) != GDP_OK || (st = alloc(&end, ncell, -1)) != GDP_OK ||
+      (st = alloc(&fill, ncell, 0)) != GDP_OK || (st = alloc(&tmp, std::max<long long>(tot_in, 1), -1)) != GDP_OK ||
+      (st = alloc(&crowded, n_mesh, 0)) != GDP_OK)
+    return st;
+  CK(cudaMemcpyAsync(d_lev, lev.data(), sizeof(int) * n_mesh, cudaMemcpyHostToDevice, stream));
+  CK(cudaMemcpyAsync(d_cbase, cbase.data(), sizeof(int) * (n_mesh + 1), cudaMemcpyHostToDevice, stream));
+  LAUNCH(*this, k_cell_count, mesh_grid, P, d_cbase, d_lev, cnt);
+  CK(cudaMemcpyAsync(end, cnt, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, stream));
+  LAUNCH(*this, k_iscan_count, G, end, ncell, P.blk);
+  LAUNCH(*this, k_iscan_write, G, end, ncell, P.blk);
+  LAUNCH(*this, k_cell_scatter, mesh_grid, P, d_cbase, d_lev, end, cnt, fill, tmp, crowded);
+  LAUNCH(*this, k_cell_sort, G, ncell, end, cnt, tmp);
+  LAUNCH(*this, k_cell_put, mesh_grid, P, d_cbase, end, cnt, tmp, crowded);
+  CK(cudaGetLastError());
+  for (void* q : {(void*)d_lev, (void*)d_cbase, (void*)cnt, (void*)end, (void*)fill, (void*)tmp, (void*)crowded})
+    release(q);
+  return GDP_OK;
+}
+
 int PoolHost::build_cdt() {
   CK(cudaEventRecord(ev0, stream));
   double* part = nullptr;
@@ -981,6 +1099,10 @@ int PoolHost::build_cdt() {
   LAUNCH(*this, k_cdt_init, n_mesh, P, part, (int)mesh_grid.x, env_double("GDP_FRAME_MARGIN", 16.0));
   LAUNCH(*this, k_cdt_vf, mesh_grid, P);
   release(part);
+  if (env_double("GDP_SPATIAL_ORDER", 1) != 0) {
+    const int so = spatial_order();
+    if (so != GDP_OK) return so;
+  }
   CK(cudaGetLastError());
   std::memset(hctrl, 0, sizeof(Ctrl));
   hctrl->n_pts = (int)(tot_in + 4 * n_mesh);
