@@ -143,7 +143,10 @@ int gdp_mesh_create_device(const double* xy_device, int64_t n_pts, const int32_t
  * still a valid CDT that can be exported. */
 int gdp_mesh_refine(gdp_mesh* mesh, const gdp_refine_opts* opts, gdp_stats* stats);
 
-/* Copy the mesh out.  Call with NULL buffers to get the sizes only.
+/* Copy the mesh out: the result of Algorithm 1 (the refined constrained
+ * Delaunay triangulation) or, before gdp_mesh_refine, the initial CDT.  This
+ * is the boundary's output side; the paper defines no interface for it.
+ * Call with NULL buffers to get the sizes only.
  *   xy:     2*cap_pts doubles: input points keep ids 0..n_in-1, Steiner points follow
  *   tri:    3*cap_tri int32, CCW
  *   subseg: 3*cap_seg int32: (u, v, input segment id)
@@ -206,6 +209,8 @@ int gdp_mesh_profile(gdp_mesh* mesh, int enable);
 int gdp_mesh_kernel_time(gdp_mesh* mesh, int32_t i, char* name, int64_t name_cap, double* total_ms,
                          int64_t* count);
 
+/* Free the mesh and every device allocation it holds (stream-ordered on its
+ * stream).  NULL is ignored.  Housekeeping with no counterpart in the paper. */
 void gdp_mesh_destroy(gdp_mesh* mesh);
 
 /* ---------------- batches: many independent PSLGs in one pool ----------------
@@ -345,6 +350,9 @@ int gdp_scan_noalloc(const double* xy_device, int64_t n_vert, const int32_t* tri
  * GDP_ERR_CUDA. */
 int gdp_measure_fp64_peak(void* cuda_stream, double* tflops);
 
+/* A static, human-readable name of a status code ("ok", "invalid input", ...);
+ * unknown codes give "unknown".  Housekeeping with no counterpart in
+ * the paper. */
 const char* gdp_status_str(int status);
 
 #ifdef __cplusplus
